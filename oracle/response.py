@@ -1,0 +1,254 @@
+"""Oracle: pair densities, Adler-Wiser chi0, Dyson, S(q,w) and F(q,tau).
+
+Test infrastructure only (see oracle/__init__.py).
+
+Definitions (Hartree atomic units, spin factor 2, Omega = cell volume, N_k = k points):
+  pair p = (k, n, n'),  Delta_p = eps_nk - eps_n'k+q,  df_p = f_nk - f_n'k+q
+  rho_p(G) = <nk| e^{-i(q+G).r} |n'k+q> = sum_G1 c*_nk(G1) c_n'k+q(G1+G)      (direct
+             G-space correlation; no FFT)
+  w_p(w)   = df_p / (w + Delta_p + i eta)
+  chi0_GG'(q,w) = (2/(N_k Omega)) sum_p rho_p(G) rho_p*(G') w_p(w)            (Adler-Wiser)
+  K_GG = 4 pi/|q+G|^2 + f_xc                                                    (diagonal)
+  chi = (1 - chi0 K)^{-1} chi0; only chi_{G,0} is solved for.
+  S(q,w) = -Im chi_00(q,w) / (pi n (1 - e^{-beta w}))          fluctuation-dissipation, Eq. 8
+           (hbar = 1; the 1/pi makes int w S dw = q^2/2, the f-sum rule)
+  S(q,0) = -Im chi_00(q,h) / (pi n beta h), h = 1e-6 Ha    (the w -> 0 limit; Im chi_00 is odd)
+  F(q,tau) = int dw S(q,w) e^{-tau w}                        two-sided Laplace transform, Eq. 1
+           = int_0^wmax S(w) [e^{-tau w} + e^{-(beta-tau) w}] dw   using detailed balance
+             S(-w) = e^{-beta w} S(w) (FOLD mode, trapezoid over the w >= 0 samples)
+  F-tilde(tau) = F(tau) - F(0)                                                    Eq. 2
+  metrics: F(beta/2), int_0^beta F dtau, F-tilde(beta/2), int_0^beta F-tilde dtau and the static
+  response chi(q) = -n int_0^beta F dtau (Sec. 2).  The tau integral is done exactly per w:
+  int_0^beta [e^{-tau w} + e^{-(beta-tau) w}] dtau = 2 (1 - e^{-beta w}) / w.
+
+Pinned by (tests/test_oracle_response.py): the discrete and continuum Lindhard functions at
+zero potential, the exact discrete f-sum rule, detailed balance to rounding on time-reversal
+symmetric meshes, the analytic Laplace transform of a model spectrum, the scalar and K = 0
+limits of Dyson, the Dyson residual, pair-density orthonormality and completeness, and a
+brute-force chi0 built by real-space FFT products on a tiny cell.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import crystal, occupations, xc
+
+H_ZERO = 1e-6     # Ha; frequency used for the w -> 0 limit of S
+
+
+def _lookup(basis: np.ndarray):
+    lo = basis.min(axis=0)
+    shape = basis.max(axis=0) - lo + 1
+    lut = -np.ones(tuple(shape), dtype=np.int64)
+    idx = basis - lo
+    lut[idx[:, 0], idx[:, 1], idx[:, 2]] = np.arange(len(basis))
+    return lo, shape, lut
+
+
+def pair_density(Ck, basis_k, Ckq, basis_kq, gset) -> np.ndarray:
+    """rho[n, n', iG] = sum_G1 conj(Ck[G1, n]) Ckq[G1+G, n'] over G1 with G1+G in basis_kq."""
+    lo, shape, lut = _lookup(basis_kq)
+    nb = Ck.shape[1]
+    rho = np.zeros((nb, Ckq.shape[1], len(gset)), dtype=np.complex128)
+    for ig, G in enumerate(gset):
+        t = basis_k + G[None, :] - lo[None, :]
+        ok = np.all((t >= 0) & (t < shape[None, :]), axis=1)
+        j = -np.ones(len(basis_k), dtype=np.int64)
+        j[ok] = lut[t[ok, 0], t[ok, 1], t[ok, 2]]
+        v = j >= 0
+        rho[:, :, ig] = Ck[v].conj().T @ Ckq[j[v]]
+    return rho
+
+
+def basis_for(wl, k):
+    if wl.basis == "fixed":
+        return crystal.sphere_basis(wl.lattice, np.zeros(3), wl.ecut)
+    return crystal.sphere_basis(wl.lattice, k, wl.ecut)
+
+
+def density(wl) -> float:
+    return wl.Z * wl.natoms / crystal.volume(wl.lattice)
+
+
+def ground_state(wl, iq: int):
+    """Eigenpairs on the k and k+q meshes of q index iq, the occupations and mu."""
+    q = wl.q[iq]
+    kpts, kqpts = crystal.pair_meshes(wl.lattice, wl.kmesh, q, wl.kscheme)
+    out = {"k": kpts, "kq": kqpts, "eps_k": [], "eps_kq": [], "C_k": [], "C_kq": [],
+           "basis_k": [], "basis_kq": []}
+    for tag, pts in (("k", kpts), ("kq", kqpts)):
+        for kv in pts:
+            b = basis_for(wl, kv)
+            e, C = crystal.eigenstates(wl.lattice, wl.positions, wl.Z, wl.r_c, kv, b, wl.nbands,
+                                       wl.potential)
+            out["eps_" + tag].append(e)
+            out["C_" + tag].append(C)
+            out["basis_" + tag].append(b)
+    out["eps_k"] = np.array(out["eps_k"])
+    out["eps_kq"] = np.array(out["eps_kq"])
+    nelec = wl.Z * wl.natoms
+    if wl.occupations is not None:
+        out["mu"] = float("nan")
+        out["f_k"] = np.asarray(wl.occupations[iq][0])
+        out["f_kq"] = np.asarray(wl.occupations[iq][1])
+    else:
+        mu = occupations.chemical_potential(out["eps_k"], wl.T, nelec, wl.nk)
+        out["mu"] = mu
+        out["f_k"] = occupations.fermi(out["eps_k"], mu, wl.T)
+        out["f_kq"] = occupations.fermi(out["eps_kq"], mu, wl.T)
+    return out
+
+
+def pair_densities(wl, gs, gset) -> np.ndarray:
+    """rho[k, n, n', G] for all k of the mesh."""
+    return np.array([pair_density(gs["C_k"][i], gs["basis_k"][i], gs["C_kq"][i], gs["basis_kq"][i], gset)
+                     for i in range(wl.nk)])
+
+
+def pair_weights(gs):
+    """Delta_p and df_p flattened in (k, n, n') order."""
+    d = gs["eps_k"][:, :, None] - gs["eps_kq"][:, None, :]
+    df = gs["f_k"][:, :, None] - gs["f_kq"][:, None, :]
+    return d.reshape(-1), df.reshape(-1)
+
+
+def internal_frequencies(omega: np.ndarray):
+    """The frequencies chi is evaluated at: the grid, with an exact 0 replaced by H_ZERO,
+    plus H_ZERO appended when 0 is not on the grid.  Returns (freqs, index of the h column)."""
+    w = np.array(omega, dtype=np.float64)
+    zero = np.where(w == 0.0)[0]
+    if len(zero):
+        w[zero[0]] = H_ZERO
+        return w, int(zero[0])
+    return np.concatenate([w, [H_ZERO]]), len(w)
+
+
+def chi0(rho_flat, delta, df, freqs, eta, nk, omega_cell) -> np.ndarray:
+    """chi0[w, G, G'] = (2/(N_k Omega)) sum_p rho_p(G) rho_p*(G') df_p/(w + Delta_p + i eta)."""
+    out = np.zeros((len(freqs), rho_flat.shape[1], rho_flat.shape[1]), dtype=np.complex128)
+    pref = 2.0 / (nk * omega_cell)
+    for iw, w in enumerate(freqs):
+        wt = df / (w + delta + 1j * eta)
+        out[iw] = pref * ((rho_flat * wt[:, None]).T @ rho_flat.conj())
+    return out
+
+
+def kernel_diag(wl, q, gset) -> np.ndarray:
+    """K_GG = 4 pi/|q+G|^2 + f_xc for the workload's kernel choice."""
+    B = crystal.reciprocal(wl.lattice)
+    qg = q[None, :] + gset @ B
+    qg2 = np.einsum("ij,ij->i", qg, qg)
+    K = 4.0 * math.pi / qg2
+    n = density(wl)
+    if wl.kernel == "rpa":
+        return K
+    if wl.kernel == "rpa_alda":
+        return K + xc.fxc_alda(n)
+    if wl.kernel == "fxc_model":
+        A, Bp, C = wl.fxc_params
+        return K + np.array([xc.fxc_model(math.sqrt(v), n, A, Bp, C) for v in qg2])
+    raise ValueError(wl.kernel)
+
+
+def solve_gauss(M: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Gaussian elimination with partial pivoting, vectorised over the leading batch axis.
+    M[batch, N, N], b[batch, N] -> x with M x = b."""
+    A = M.copy()
+    x = b.copy()
+    nb, N, _ = A.shape
+    rows = np.arange(nb)
+    for c in range(N):
+        piv = c + np.argmax(np.abs(A[:, c:, c]), axis=1)
+        if np.any(np.abs(A[rows, piv, c]) == 0.0):
+            raise np.linalg.LinAlgError("singular Dyson matrix")
+        tmp = A[rows, c, :].copy()
+        A[rows, c, :] = A[rows, piv, :]
+        A[rows, piv, :] = tmp
+        tb = x[rows, c].copy()
+        x[rows, c] = x[rows, piv]
+        x[rows, piv] = tb
+        for r in range(c + 1, N):
+            fac = A[:, r, c] / A[:, c, c]
+            A[:, r, c:] -= fac[:, None] * A[:, c, c:]
+            x[:, r] -= fac * x[:, c]
+    for c in range(N - 1, -1, -1):
+        x[:, c] = (x[:, c] - np.einsum("bj,bj->b", A[:, c, c + 1:], x[:, c + 1:])) / A[:, c, c]
+    return x
+
+
+def dyson_column0(chi0w: np.ndarray, K: np.ndarray) -> np.ndarray:
+    """chi_{G,0} from (1 - chi0 K) chi_{:,0} = chi0_{:,0}; returns [w, G]."""
+    N = chi0w.shape[1]
+    M = np.eye(N)[None, :, :] - chi0w * K[None, None, :]
+    return solve_gauss(M, chi0w[:, :, 0].copy())
+
+
+def dsf(chi00_int: np.ndarray, omega: np.ndarray, hcol: int, T: float, n: float) -> np.ndarray:
+    """S on the caller's grid from chi_00 at the internal frequencies (Eq. 8)."""
+    beta = 1.0 / T
+    S = np.zeros(len(omega))
+    for j, w in enumerate(omega):
+        if w == 0.0:
+            S[j] = -chi00_int[hcol].imag / (math.pi * n * beta * H_ZERO)
+        else:
+            S[j] = -chi00_int[j].imag / (math.pi * n * (-math.expm1(-beta * w)))
+    return S
+
+
+def s_zero(chi00_int, hcol, T, n) -> float:
+    return -chi00_int[hcol].imag / (math.pi * n * H_ZERO / T)
+
+
+def positive_branch(S, omega, S0):
+    """(w_j, S_j) over w >= 0 in ascending order, with w = 0 included (value S0 if the grid
+    lacks it)."""
+    w = np.asarray(omega)
+    pos = w >= 0.0
+    wp, Sp = w[pos], np.asarray(S)[pos]
+    if len(wp) == 0 or wp[0] != 0.0:
+        wp = np.concatenate([[0.0], wp])
+        Sp = np.concatenate([[S0], Sp])
+    return wp, Sp
+
+
+def trapezoid_weights(x: np.ndarray) -> np.ndarray:
+    w = np.zeros(len(x))
+    if len(x) < 2:
+        return w
+    dx = np.diff(x)
+    w[:-1] += 0.5 * dx
+    w[1:] += 0.5 * dx
+    return w
+
+
+def itcf_fold(wp, Sp, tau, T) -> np.ndarray:
+    """F(tau) = sum_j wt_j S_j [e^{-tau w_j} + e^{-(beta - tau) w_j}] (Eq. 1 + detailed balance)."""
+    beta = 1.0 / T
+    wt = trapezoid_weights(wp)
+    tau = np.asarray(tau)
+    ker = np.exp(-np.outer(tau, wp)) + np.exp(-np.outer(beta - tau, wp))
+    return ker @ (wt * Sp)
+
+
+def itcf_direct(omega, S, tau) -> np.ndarray:
+    """F(tau) = trapezoid over the full grid of S(w) e^{-tau w} (Eq. 1, no folding)."""
+    wt = trapezoid_weights(np.asarray(omega))
+    return np.exp(-np.outer(np.asarray(tau), omega)) @ (wt * S)
+
+
+def itcf_metrics(wp, Sp, T, n) -> np.ndarray:
+    """[F(beta/2), int_0^beta F, Ftilde(beta/2), int_0^beta Ftilde, -n int_0^beta F]."""
+    beta = 1.0 / T
+    wt = trapezoid_weights(wp)
+    Fhalf = float(itcf_fold(wp, Sp, [0.5 * beta], T)[0])
+    F0 = float(itcf_fold(wp, Sp, [0.0], T)[0])
+    tint = np.where(wp > 0.0, -2.0 * np.expm1(-beta * np.where(wp > 0, wp, 1.0)) / np.where(wp > 0, wp, 1.0),
+                    2.0 * beta)
+    Fint = float(np.sum(wt * Sp * tint))
+    return np.array([Fhalf, Fint, Fhalf - F0, Fint - beta * F0, -n * Fint])
+
+
+def tau_grid(T: float, ntau: int) -> np.ndarray:
+    return np.linspace(0.0, 0.5 / T, ntau)
