@@ -1,0 +1,227 @@
+/*
+ * lrtddft.h -- C ABI of the GB300 linear-response TDDFT response library (liblrtddft.so).
+ *
+ * The library computes, for a list of momentum transfers q, the dynamic structure factor
+ * S(q,w) and the imaginary-time correlation function F(q,tau) of a crystal with a fixed
+ * (non-self-consistent) empty-core pseudopotential, and the constraints-based attenuation
+ * of narrow-band fluctuations of S:
+ *
+ *   rho_p(G)      = <nk| e^{-i(q+G).r} |n'k+q>,  p = (k, n, n')            (pair densities)
+ *   chi0_GG'(q,w) = (2/(N_k Omega)) sum_p rho_p(G) rho_p*(G') (f_nk - f_n'k+q)
+ *                                              / (w + eps_nk - eps_n'k+q + i eta)
+ *                                                        (Adler-Wiser independent-particle)
+ *   chi           = (1 - chi0 K)^{-1} chi0,  K_GG' = delta_GG' (4 pi/|q+G|^2 + f_xc)  (Dyson)
+ *   S(q,w)        = -Im chi_00(q,w) / (pi n (1 - e^{-w/T}))   fluctuation-dissipation, Eq. 8
+ *   F(q,tau)      = int dw S(q,w) e^{-tau w}, with S(q,-w) = e^{-w/T} S(q,w)
+ *                                           two-sided Laplace transform + detailed balance, Eq. 1
+ *   F~(q,tau)     = F(q,tau) - F(q,0)                                                   Eq. 2
+ *   attenuation   Savitzky-Golay grid search scored by AICc + penalties, accepted under the
+ *                 imaginary-time constraints of Sec. 3, Eqs. 5-7.
+ * (Section, equation numbers: Moldabekov et al., "Enhancing the Efficiency of TDDFT
+ * Calculations of Dynamic Response Properties".  The chi0/Dyson engine itself is the
+ * textbook Adler-Wiser + Dyson form; the paper's own engine is Liouville-Lanczos.)
+ *
+ * Conventions for every entry point:
+ *  - Units: Hartree atomic units (Ha, bohr, 1/bohr); temperature T in Ha.
+ *  - Arrays are row-major, C order, with the sizes given in each comment.  Complex numbers
+ *    are (re, im) pairs of doubles.
+ *  - Ownership: inputs are read during the call and copied; the caller keeps them.  Outputs
+ *    go to caller-owned buffers.  Functions named *_device take device pointers and a
+ *    cudaStream_t (passed as void*) and return once the work is enqueued; the others take
+ *    host pointers and return after the results are on the host.  The library owns all of
+ *    its device workspace and frees it in lrtddft_destroy.
+ *  - Errors: every function returns an lrt_status; nothing throws or aborts across the ABI.
+ *    lrtddft_status_string gives a message and lrtddft_last_error the detail of the last
+ *    failure on the calling thread.  After LRT_ECUDA the context must be destroyed.
+ *  - One context is used from one host thread at a time.
+ */
+#ifndef LRTDDFT_H
+#define LRTDDFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRT_OK = 0,
+  LRT_EINVAL = 1,       /* invalid argument (sizes, grids, q equal to a lattice vector ...) */
+  LRT_ENOMEM = 2,       /* device or host allocation failed */
+  LRT_ECUDA = 3,        /* CUDA / cuSOLVER error */
+  LRT_ESINGULAR = 4,    /* a Dyson matrix 1 - chi0 K had a zero pivot */
+  LRT_ETIMEOUT = 5,     /* a bounded device-side wait ran out */
+  LRT_ESTATE = 6,       /* calls out of order (e.g. dsf before dyson_solve) */
+  LRT_EUNSUPPORTED = 7  /* option not available in this build / on this device */
+} lrt_status;
+
+typedef struct lrt_ctx lrt_ctx;
+
+enum { LRT_POT_EMPTY_CORE = 0, LRT_POT_ZERO = 1 };
+enum { LRT_BASIS_SPHERE = 0, LRT_BASIS_FIXED = 1 };
+enum { LRT_K_COMMENSURATE = 0, LRT_K_TR_SYMMETRIC = 1 };
+enum { LRT_KERNEL_RPA = 0, LRT_KERNEL_RPA_ALDA = 1, LRT_KERNEL_FXC_MODEL = 2 };
+/* Precision of the chi0 contraction (the Dyson solve, S and F are always FP64):
+ * FP64: FP64 products and sums;  FP16X3 / BF16X3: each operand split into a high and a low
+ * 16-bit part, three tensor-core products (hi*hi + hi*lo + lo*hi) accumulated in FP32 and
+ * flushed into FP64 partial sums. */
+enum { LRT_PREC_FP64 = 0, LRT_PREC_FP16X3 = 1, LRT_PREC_BF16X3 = 2 };
+enum { LRT_ITCF_FOLD = 0, LRT_ITCF_DIRECT = 1 };
+
+/* Crystal and plane-wave basis.  V(G) = sum_a v(|G|) e^{-i G.R_a},
+ * v(G) = -(4 pi Z/(Omega G^2)) cos(G r_c) (Ashcroft empty core), V(0) = 0.
+ * Basis per k: {G : |k+G|^2/2 <= ecut} (SPHERE) or {G : |G|^2/2 <= ecut} (FIXED). */
+typedef struct {
+  double lattice[3][3];     /* rows are the lattice vectors, bohr */
+  int natoms;
+  const double* positions;  /* [natoms][3] Cartesian, bohr */
+  double Z;                 /* ionic valence; N_e = Z * natoms */
+  double r_c;               /* empty-core radius, bohr */
+  double ecut;              /* Ha */
+  int potential;            /* LRT_POT_* */
+  int basis;                /* LRT_BASIS_* */
+} lrt_cell;
+
+/* k-mesh: Gamma-centred M = {sum_j (i_j/n_j) b_j}.  COMMENSURATE: k in M, k+q = k + q.
+ * TR_SYMMETRIC: k in M - q/2, k+q in M + q/2 (then -k-q lies in the k set modulo G, so
+ * chi0(-w)* = chi0(w)^T and detailed balance holds to rounding). */
+typedef struct {
+  int n[3];
+  int scheme;               /* LRT_K_* */
+} lrt_kmesh;
+
+/* Static kernel added to the Coulomb term: RPA (none), RPA_ALDA (f_xc of the mean density:
+ * Slater exchange + Perdew-Wang 1992 correlation), FXC_MODEL:
+ * f_xc(|q+G|) = A f_ALDA (1 + B |q+G|^2) exp(-C |q+G|^2). */
+typedef struct {
+  int kind;                 /* LRT_KERNEL_* */
+  double A, B, C;
+} lrt_kernel;
+
+/* flags: LRT_FLAG_HOST_ONLY builds only the host-side geometry (k meshes, bases, G-sets,
+ * K) and touches no GPU; compute calls on such a context return LRT_ESTATE. */
+enum { LRT_FLAG_HOST_ONLY = 1 };
+typedef struct {
+  int precision;            /* LRT_PREC_* */
+  int device;               /* CUDA device ordinal */
+  int flags;                /* LRT_FLAG_* */
+} lrt_options;
+
+/* Create a context: builds the k meshes, bases and response G-sets, diagonalises H(k) on
+ * the GPU (cuSOLVER, setup only), sets occupations and the Dyson kernel.
+ *   nbands        bands kept per k point (<= plane waves at every k)
+ *   T             electron temperature, Ha (> 0)
+ *   occupations   NULL for Fermi-Dirac with mu from (2/N_k) sum f = N_e on the k mesh of each
+ *                 q; else [nq][2][nk][nbands] (k mesh, then k+q mesh) overriding f
+ *   q             [nq][3] Cartesian, 1/bohr; no q may be a reciprocal-lattice vector
+ *   nG            [nq] response G-vectors per q: the nG of smallest |q+G| (ties: smaller |G|,
+ *                 then lexicographic Miller indices), ordered with G = 0 first
+ *   omega         [nw] strictly increasing real frequencies, Ha
+ *   eta           Lorentzian broadening, Ha (> 0)
+ * Errors: EINVAL (sizes, non-monotone omega, nbands too large, G = 0 not in the set),
+ * ENOMEM, ECUDA. */
+lrt_status lrtddft_create(const lrt_cell* cell, const lrt_kmesh* kmesh, int nbands, double T,
+                          const double* occupations, int nq, const double* q, const int* nG,
+                          int nw, const double* omega, double eta, const lrt_kernel* kernel,
+                          const lrt_options* opt, lrt_ctx** out);
+
+lrt_status lrtddft_destroy(lrt_ctx* ctx);
+
+const char* lrtddft_status_string(lrt_status s);
+/* Detail of the last failure on this thread (static storage; valid until the next call). */
+const char* lrtddft_last_error(void);
+
+/* Sizes of a context: out[0..7] = nq, nw, nk, nbands, max nG, plane waves (padded), number of
+ * internal frequencies (nw plus the w -> 0 column when 0 is not on the grid), precision. */
+lrt_status lrtddft_query(const lrt_ctx* ctx, int64_t out[8]);
+
+/* chi0 for q in [q_begin, q_end): pair densities (G-space correlation of the orbitals) and
+ * the Adler-Wiser contraction at every internal frequency, kept on the device.  Enqueued on
+ * `stream` (cudaStream_t; NULL = legacy default stream). */
+lrt_status lrtddft_chi0_assemble(lrt_ctx* ctx, int q_begin, int q_end, void* stream);
+
+/* Dyson for q in [q_begin, q_end): solves (1 - chi0 K) x = chi0_{:,0} by LU with partial
+ * pivoting per (q, w), FP64; x = chi_{G,0}.  Requires chi0_assemble on the same q.
+ * A zero pivot makes a later synchronising call return LRT_ESINGULAR. */
+lrt_status lrtddft_dyson_solve(lrt_ctx* ctx, int q_begin, int q_end, void* stream);
+
+/* S(q,w) (Eq. 8) on the caller's grid: S [nq][nw].  At w = 0 the limit
+ * -Im chi_00(h)/(pi n h / T), h = 1e-6 Ha, is used.  Requires dyson_solve for every q. */
+lrt_status lrtddft_dsf(lrt_ctx* ctx, double* S);
+lrt_status lrtddft_dsf_device(lrt_ctx* ctx, double* S_dev, void* stream);
+
+/* F(q,tau) at the caller's tau (each in [0, 1/T]):
+ *   FOLD   (Eq. 1 with detailed balance) trapezoid over the w >= 0 samples (plus w = 0) of
+ *          S(w)[e^{-tau w} + e^{-(1/T - tau) w}];
+ *   DIRECT trapezoid over the whole caller grid of S(w) e^{-tau w}.
+ * F [nq][ntau]; metrics [nq][5] (may be NULL) = F(beta/2), int_0^beta F dtau,
+ * F~(beta/2) (Eq. 2), int_0^beta F~ dtau and the static response -n int_0^beta F dtau
+ * (Sec. 2), the tau integrals done exactly per w (FOLD branch). */
+lrt_status lrtddft_itcf_laplace(lrt_ctx* ctx, int ntau, const double* tau, int mode, double* F,
+                                double* metrics);
+lrt_status lrtddft_itcf_laplace_device(lrt_ctx* ctx, int ntau, const double* tau_dev, int mode,
+                                       double* F_dev, double* metrics_dev, void* stream);
+
+/* Attenuation of narrow-band fluctuations (Sec. 3).  Defaults (fields <= 0) in brackets. */
+typedef struct {
+  int d_min, d_max;         /* polynomial degrees searched [1, 4] */
+  double w_min, w_max;      /* window grid, Ha, full widths [4 dw, quarter of the range] */
+  int n_w;                  /* windows in the grid [24]; m = 2 round(w/(2 dw)) + 1 points */
+  double lambda_f;          /* weight of ln(max(R_f, r0)/r0), R_f = target power kept [N] */
+  double lambda_c;          /* weight of the second-difference ratio [N] */
+  int n_targets;            /* strongest local maxima of the dS/dw periodogram [2] */
+  double feat_lo, feat_hi;  /* featureless range, Ha [central 90 % of the w >= 0 samples] */
+  double low_exclude;       /* lowest fraction of Fourier frequencies ignored [0.05] */
+  double accept_mean;       /* |Fbar_n| / F(beta/2) limit [4e-3] (Sec. 3) */
+  double accept_rms;        /* sigma_n / F(beta/2) limit [4.2e-5] (Sec. 3) */
+  int average;              /* 1: S_p = mean over accepted degrees (Sec. 4.1); 0: best [1] */
+  int ntau;                 /* tau points on [0, beta/2] for the constraints [64] */
+  double retain_floor;      /* r0 [1e-4] */
+} lrt_atten_params;
+
+#define LRT_ATTEN_MAX_DEG 8
+typedef struct {
+  int n_accepted;
+  int targets[4];           /* periodogram bins of the targets (-1 = none) */
+  int degree[LRT_ATTEN_MAX_DEG];       /* degree d of each row (-1 = unused) */
+  int window[LRT_ATTEN_MAX_DEG];       /* chosen window m (points) */
+  double score[LRT_ATTEN_MAX_DEG];
+  double mean_ratio[LRT_ATTEN_MAX_DEG];  /* |Fbar_n| / F(beta/2) */
+  double rms_ratio[LRT_ATTEN_MAX_DEG];   /* sigma_n / F(beta/2) */
+  int accepted[LRT_ATTEN_MAX_DEG];
+} lrt_atten_report;
+
+/* Sp [nq][nw] (samples with w < 0 are copied from S unchanged); report [nq] (may be NULL).
+ * Requires dyson_solve for every q and at least 8 uniformly spaced samples with w >= 0. */
+lrt_status lrtddft_attenuate(lrt_ctx* ctx, const lrt_atten_params* params, double* Sp,
+                             lrt_atten_report* report);
+
+/* ---- test and debug hooks ---- */
+
+/* Replace the orbitals of q index iq: eps [2][nk][nbands] (k mesh then k+q mesh),
+ * coeff [2][nk][nbands][npw] complex on the context's padded basis order (see
+ * lrtddft_get_basis), occ [2][nk][nbands] or NULL (keep Fermi-Dirac with a new mu).
+ * Host pointers. */
+lrt_status lrtddft_set_orbitals(lrt_ctx* ctx, int iq, const double* eps, const double* coeff,
+                                const double* occ);
+/* Miller indices of the padded basis of q index iq: miller [2][nk][npw][3] (int32; padding
+ * rows hold INT32_MIN), npw_k [2][nk]. */
+lrt_status lrtddft_get_basis(const lrt_ctx* ctx, int iq, int32_t* miller, int32_t* npw_k);
+/* Eigenvalues [2][nk][nbands], occupations [2][nk][nbands] and mu of q index iq. */
+lrt_status lrtddft_get_ground_state(const lrt_ctx* ctx, int iq, double* eps, double* occ,
+                                    double* mu);
+/* Response G-set of q index iq: miller [nG][3] (G = 0 first) and K_GG [nG]. */
+lrt_status lrtddft_get_gset(const lrt_ctx* ctx, int iq, int32_t* miller, double* K);
+/* chi0 of q index iq: [nw_int][nG][nG] complex, at the internal frequencies
+ * (lrtddft_get_frequencies).  Requires chi0_assemble on iq. */
+lrt_status lrtddft_get_chi0(const lrt_ctx* ctx, int iq, double* chi0);
+/* chi_{G,0} of q index iq: [nw_int][nG] complex.  Requires dyson_solve on iq. */
+lrt_status lrtddft_get_chi_col0(const lrt_ctx* ctx, int iq, double* chi);
+/* Internal frequencies [nw_int] and the index of the w -> 0 column. */
+lrt_status lrtddft_get_frequencies(const lrt_ctx* ctx, double* freqs, int* hcol);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRTDDFT_H */

@@ -1,0 +1,279 @@
+"""Python binding of liblrtddft (C ABI in include/lrtddft.h): argument marshalling only.
+
+Every step of the response path runs in the CUDA library; this module converts a
+`workloads.Workload` into the C structs, allocates numpy output buffers and checks status
+codes.  `load()` raises if the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from .workloads import Workload
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblrtddft.so")
+
+LRT_OK, LRT_EINVAL, LRT_ENOMEM, LRT_ECUDA, LRT_ESINGULAR, LRT_ETIMEOUT, LRT_ESTATE, LRT_EUNSUPPORTED = range(8)
+POT = {"empty_core": 0, "zero": 1}
+BASIS = {"sphere": 0, "fixed": 1}
+KSCHEME = {"commensurate": 0, "tr_symmetric": 1}
+KERNEL = {"rpa": 0, "rpa_alda": 1, "fxc_model": 2}
+PREC = {"fp64": 0, "fp16x3": 1, "bf16x3": 2}
+ITCF = {"fold": 0, "direct": 1}
+
+
+class LrtError(RuntimeError):
+    def __init__(self, fn, status, detail):
+        super().__init__(f"{fn}: {status} ({detail})")
+        self.status = status
+
+
+class lrt_cell(C.Structure):
+    _fields_ = [("lattice", C.c_double * 9), ("natoms", C.c_int), ("positions", C.POINTER(C.c_double)),
+                ("Z", C.c_double), ("r_c", C.c_double), ("ecut", C.c_double), ("potential", C.c_int),
+                ("basis", C.c_int)]
+
+
+class lrt_kmesh(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("scheme", C.c_int)]
+
+
+class lrt_kernel(C.Structure):
+    _fields_ = [("kind", C.c_int), ("A", C.c_double), ("B", C.c_double), ("C", C.c_double)]
+
+
+class lrt_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("device", C.c_int), ("flags", C.c_int)]
+
+
+class lrt_atten_params(C.Structure):
+    _fields_ = [("d_min", C.c_int), ("d_max", C.c_int), ("w_min", C.c_double), ("w_max", C.c_double),
+                ("n_w", C.c_int), ("lambda_f", C.c_double), ("lambda_c", C.c_double),
+                ("n_targets", C.c_int), ("feat_lo", C.c_double), ("feat_hi", C.c_double),
+                ("low_exclude", C.c_double), ("accept_mean", C.c_double), ("accept_rms", C.c_double),
+                ("average", C.c_int), ("ntau", C.c_int), ("retain_floor", C.c_double)]
+
+
+MAXDEG = 8
+
+
+class lrt_atten_report(C.Structure):
+    _fields_ = [("n_accepted", C.c_int), ("targets", C.c_int * 4), ("degree", C.c_int * MAXDEG),
+                ("window", C.c_int * MAXDEG), ("score", C.c_double * MAXDEG),
+                ("mean_ratio", C.c_double * MAXDEG), ("rms_ratio", C.c_double * MAXDEG),
+                ("accepted", C.c_int * MAXDEG)]
+
+
+# name -> (restype, argtypes); every symbol include/lrtddft.h declares
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+SIGNATURES = {
+    "lrtddft_create": (C.c_int, [C.POINTER(lrt_cell), C.POINTER(lrt_kmesh), C.c_int, C.c_double, _D, C.c_int,
+                                 _D, C.POINTER(C.c_int), C.c_int, _D, C.c_double, C.POINTER(lrt_kernel),
+                                 C.POINTER(lrt_options), C.POINTER(_P)]),
+    "lrtddft_destroy": (C.c_int, [_P]),
+    "lrtddft_status_string": (C.c_char_p, [C.c_int]),
+    "lrtddft_last_error": (C.c_char_p, []),
+    "lrtddft_query": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "lrtddft_chi0_assemble": (C.c_int, [_P, C.c_int, C.c_int, _P]),
+    "lrtddft_dyson_solve": (C.c_int, [_P, C.c_int, C.c_int, _P]),
+    "lrtddft_dsf": (C.c_int, [_P, _D]),
+    "lrtddft_dsf_device": (C.c_int, [_P, _P, _P]),
+    "lrtddft_itcf_laplace": (C.c_int, [_P, C.c_int, _D, C.c_int, _D, _D]),
+    "lrtddft_itcf_laplace_device": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "lrtddft_attenuate": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D, C.POINTER(lrt_atten_report)]),
+    "lrtddft_set_orbitals": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "lrtddft_get_basis": (C.c_int, [_P, C.c_int, _I32, _I32]),
+    "lrtddft_get_ground_state": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "lrtddft_get_gset": (C.c_int, [_P, C.c_int, _I32, _D]),
+    "lrtddft_get_chi0": (C.c_int, [_P, C.c_int, _D]),
+    "lrtddft_get_chi_col0": (C.c_int, [_P, C.c_int, _D]),
+    "lrtddft_get_frequencies": (C.c_int, [_P, _D, C.POINTER(C.c_int)]),
+}
+
+_lib = None
+
+
+def load():
+    """Load liblrtddft.so; raises when it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built first")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _check(fn: str, st: int):
+    if st != LRT_OK:
+        lib = load()
+        raise LrtError(fn, lib.lrtddft_status_string(st).decode(), lib.lrtddft_last_error().decode())
+
+
+def atten_params(**kw) -> lrt_atten_params:
+    """An lrt_atten_params with library defaults for every field not given."""
+    p = lrt_atten_params()
+    for f, _ in lrt_atten_params._fields_:
+        setattr(p, f, 0)
+    p.average = 1
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One lrt_ctx built from a Workload."""
+
+    def __init__(self, wl: Workload, precision: str = "fp64", device: int = 0,
+                 occupations: Optional[np.ndarray] = None):
+        lib = load()
+        self.wl = wl
+        cell = lrt_cell()
+        cell.lattice[:] = [float(x) for x in np.asarray(wl.lattice).reshape(-1)]
+        self._pos = np.ascontiguousarray(wl.positions, dtype=np.float64)
+        cell.natoms = wl.natoms
+        cell.positions = _dp(self._pos)
+        cell.Z, cell.r_c, cell.ecut = wl.Z, wl.r_c, wl.ecut
+        cell.potential = POT[wl.potential]
+        cell.basis = BASIS[wl.basis]
+        km = lrt_kmesh()
+        km.n[:] = list(wl.kmesh)
+        km.scheme = KSCHEME[wl.kscheme]
+        kern = lrt_kernel(KERNEL[wl.kernel], *[float(x) for x in wl.fxc_params])
+        opt = lrt_options(PREC[precision], device, 0)
+        q = np.ascontiguousarray(wl.q, dtype=np.float64)
+        nG = np.ascontiguousarray(wl.nG, dtype=np.int32)
+        om = np.ascontiguousarray(wl.omega, dtype=np.float64)
+        occ = None if occupations is None else np.ascontiguousarray(occupations, dtype=np.float64)
+        h = _P()
+        st = lib.lrtddft_create(C.byref(cell), C.byref(km), wl.nbands, wl.T,
+                                None if occ is None else _dp(occ), wl.nq, _dp(q),
+                                nG.ctypes.data_as(C.POINTER(C.c_int)), wl.nw, _dp(om), wl.eta,
+                                C.byref(kern), C.byref(opt), C.byref(h))
+        _check("lrtddft_create", st)
+        self.h = h
+        sz = (C.c_int64 * 8)()
+        _check("lrtddft_query", lib.lrtddft_query(h, sz))
+        self.nq, self.nw, self.nk, self.nb, self.nGmax, self.npw, self.nwi, _ = list(sz)
+        self.lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lrtddft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- response steps ---
+    def chi0_assemble(self, q0=0, q1=None, stream: int = 0):
+        _check("lrtddft_chi0_assemble", self.lib.lrtddft_chi0_assemble(
+            self.h, q0, self.nq if q1 is None else q1, _P(stream)))
+
+    def dyson_solve(self, q0=0, q1=None, stream: int = 0):
+        _check("lrtddft_dyson_solve", self.lib.lrtddft_dyson_solve(
+            self.h, q0, self.nq if q1 is None else q1, _P(stream)))
+
+    def dsf(self) -> np.ndarray:
+        S = np.zeros((self.nq, self.nw))
+        _check("lrtddft_dsf", self.lib.lrtddft_dsf(self.h, _dp(S)))
+        return S
+
+    def dsf_device(self, S_ptr: int, stream: int = 0):
+        _check("lrtddft_dsf_device", self.lib.lrtddft_dsf_device(self.h, _P(S_ptr), _P(stream)))
+
+    def itcf(self, tau, mode: str = "fold"):
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        F = np.zeros((self.nq, len(tau)))
+        m = np.zeros((self.nq, 5))
+        _check("lrtddft_itcf_laplace", self.lib.lrtddft_itcf_laplace(
+            self.h, len(tau), _dp(tau), ITCF[mode], _dp(F), _dp(m)))
+        return F, m
+
+    def itcf_device(self, ntau: int, tau_ptr: int, F_ptr: int, metrics_ptr: int, mode="fold", stream: int = 0):
+        _check("lrtddft_itcf_laplace_device", self.lib.lrtddft_itcf_laplace_device(
+            self.h, ntau, _P(tau_ptr), ITCF[mode], _P(F_ptr), _P(metrics_ptr), _P(stream)))
+
+    def attenuate(self, params: Optional[lrt_atten_params] = None):
+        p = params if params is not None else atten_params()
+        Sp = np.zeros((self.nq, self.nw))
+        rep = (lrt_atten_report * self.nq)()
+        _check("lrtddft_attenuate", self.lib.lrtddft_attenuate(self.h, C.byref(p), _dp(Sp), rep))
+        return Sp, [report_dict(r) for r in rep]
+
+    # --- hooks ---
+    def set_orbitals(self, iq: int, eps: np.ndarray, coeff: np.ndarray, occ: Optional[np.ndarray] = None):
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        cf = np.ascontiguousarray(coeff, dtype=np.complex128)
+        oc = None if occ is None else np.ascontiguousarray(occ, dtype=np.float64)
+        _check("lrtddft_set_orbitals", self.lib.lrtddft_set_orbitals(
+            self.h, iq, _dp(eps), cf.ctypes.data_as(_D), None if oc is None else _dp(oc)))
+
+    def get_basis(self, iq: int):
+        m = np.zeros((2, self.nk, self.npw, 3), dtype=np.int32)
+        n = np.zeros((2, self.nk), dtype=np.int32)
+        _check("lrtddft_get_basis", self.lib.lrtddft_get_basis(
+            self.h, iq, m.ctypes.data_as(_I32), n.ctypes.data_as(_I32)))
+        return m, n
+
+    def get_ground_state(self, iq: int):
+        e = np.zeros((2, self.nk, self.nb))
+        f = np.zeros((2, self.nk, self.nb))
+        mu = C.c_double()
+        _check("lrtddft_get_ground_state", self.lib.lrtddft_get_ground_state(
+            self.h, iq, _dp(e), _dp(f), C.byref(mu)))
+        return e, f, mu.value
+
+    def get_gset(self, iq: int):
+        nG = int(self.wl.nG[iq])
+        m = np.zeros((nG, 3), dtype=np.int32)
+        K = np.zeros(nG)
+        _check("lrtddft_get_gset", self.lib.lrtddft_get_gset(self.h, iq, m.ctypes.data_as(_I32), _dp(K)))
+        return m, K
+
+    def get_chi0(self, iq: int) -> np.ndarray:
+        nG = int(self.wl.nG[iq])
+        out = np.zeros((self.nwi, nG, nG), dtype=np.complex128)
+        _check("lrtddft_get_chi0", self.lib.lrtddft_get_chi0(self.h, iq, out.ctypes.data_as(_D)))
+        return out
+
+    def get_chi_col0(self, iq: int) -> np.ndarray:
+        nG = int(self.wl.nG[iq])
+        out = np.zeros((self.nwi, nG), dtype=np.complex128)
+        _check("lrtddft_get_chi_col0", self.lib.lrtddft_get_chi_col0(self.h, iq, out.ctypes.data_as(_D)))
+        return out
+
+    def get_frequencies(self):
+        f = np.zeros(self.nwi)
+        h = C.c_int()
+        _check("lrtddft_get_frequencies", self.lib.lrtddft_get_frequencies(self.h, _dp(f), C.byref(h)))
+        return f, h.value
+
+
+def report_dict(r: lrt_atten_report) -> dict:
+    degs = []
+    for i in range(MAXDEG):
+        if r.degree[i] < 0:
+            continue
+        degs.append({"d": r.degree[i], "m": r.window[i], "score": r.score[i],
+                     "mean_ratio": r.mean_ratio[i], "rms_ratio": r.rms_ratio[i],
+                     "accepted": bool(r.accepted[i])})
+    return {"n_accepted": r.n_accepted, "targets": [t for t in r.targets if t >= 0], "degrees": degs}

@@ -1,0 +1,442 @@
+// C ABI entry points of liblrtddft (declared in include/lrtddft.h): validation, context
+// lifetime, the order of the response steps and host/device transfers.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "lrt_internal.h"
+
+namespace lrt {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error() { return g_last_error.c_str(); }
+
+namespace {
+
+lrt_status bad(const char* msg) {
+  set_error(msg);
+  return LRT_EINVAL;
+}
+
+void free_ctx(lrt_ctx* c) {
+  if (!c) return;
+  if (c->host_only) {
+    delete c;
+    return;
+  }
+  cudaSetDevice(c->device);
+  for (auto& q : c->qd) {
+    cudaFree(q.Kdev);
+    cudaFree(q.eps);
+    cudaFree(q.occ);
+    cudaFree(q.coeff);
+    cudaFree(q.gather);
+    cudaFree(q.chi0);
+    cudaFree(q.chi);
+  }
+  cudaFree(c->dw.rho);
+  cudaFree(c->dw.delta);
+  cudaFree(c->dw.df);
+  cudaFree(c->dw.freqs);
+  cudaFree(c->dw.omega);
+  cudaFree(c->dw.S);
+  cudaFree(c->dw.chi00);
+  cudaFree(c->dw.status);
+  cudaFree(c->dw.scratch);
+  delete c;
+}
+
+lrt_status check_status_word(lrt_ctx* c) {
+  int st = 0;
+  LRT_CUDA(cudaMemcpy(&st, c->dw.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & 2) {
+    set_error("a bounded device wait ran out");
+    return LRT_ETIMEOUT;
+  }
+  if (st & 1) {
+    set_error("zero pivot in a Dyson matrix");
+    return LRT_ESINGULAR;
+  }
+  return LRT_OK;
+}
+
+lrt_status ensure_rho(lrt_ctx* c) {
+  size_t elem = (c->precision == LRT_PREC_FP64) ? sizeof(double2) : sizeof(float2);
+  size_t need = (size_t)c->nGmax * c->np * elem;
+  if (c->dw.rho_bytes >= need) return LRT_OK;
+  cudaFree(c->dw.rho);
+  c->dw.rho = nullptr;
+  LRT_CUDA(cudaMalloc(&c->dw.rho, need));
+  c->dw.rho_bytes = need;
+  return LRT_OK;
+}
+
+}  // namespace
+}  // namespace lrt
+
+using namespace lrt;
+
+extern "C" const char* lrtddft_status_string(lrt_status s) {
+  switch (s) {
+    case LRT_OK: return "ok";
+    case LRT_EINVAL: return "invalid argument";
+    case LRT_ENOMEM: return "out of memory";
+    case LRT_ECUDA: return "CUDA error";
+    case LRT_ESINGULAR: return "singular Dyson matrix";
+    case LRT_ETIMEOUT: return "device wait timed out";
+    case LRT_ESTATE: return "calls out of order";
+    case LRT_EUNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* lrtddft_last_error(void) { return lrt::last_error(); }
+
+extern "C" lrt_status lrtddft_create(const lrt_cell* cell, const lrt_kmesh* kmesh, int nbands,
+                                     double T, const double* occupations, int nq, const double* q,
+                                     const int* nG, int nw, const double* omega, double eta,
+                                     const lrt_kernel* kernel, const lrt_options* opt,
+                                     lrt_ctx** out) {
+  if (!out) return bad("out is NULL");
+  *out = nullptr;
+  if (!cell || !kmesh || !q || !nG || !omega || !kernel) return bad("NULL argument");
+  if (cell->natoms < 1 || !cell->positions) return bad("natoms must be >= 1 with positions");
+  if (!(cell->Z > 0) || !(cell->ecut > 0) || !(cell->r_c >= 0)) return bad("Z, ecut, r_c");
+  if (cell->potential != LRT_POT_EMPTY_CORE && cell->potential != LRT_POT_ZERO)
+    return bad("unknown potential kind");
+  if (cell->basis != LRT_BASIS_SPHERE && cell->basis != LRT_BASIS_FIXED)
+    return bad("unknown basis kind");
+  for (int i = 0; i < 3; ++i)
+    if (kmesh->n[i] < 1 || kmesh->n[i] > 256) return bad("k mesh size");
+  if (kmesh->scheme != LRT_K_COMMENSURATE && kmesh->scheme != LRT_K_TR_SYMMETRIC)
+    return bad("unknown k scheme");
+  if (nbands < 1) return bad("nbands must be >= 1");
+  if (!(T > 0) || !std::isfinite(T)) return bad("T must be > 0");
+  if (!(eta > 0) || !std::isfinite(eta)) return bad("eta must be > 0");
+  if (nq < 1) return bad("nq must be >= 1");
+  if (nw < 2) return bad("nw must be >= 2");
+  for (int j = 0; j < nw; ++j)
+    if (!std::isfinite(omega[j]) || (j > 0 && !(omega[j] > omega[j - 1])))
+      return bad("omega must be finite and strictly increasing");
+  for (int i = 0; i < 3 * nq; ++i)
+    if (!std::isfinite(q[i])) return bad("q must be finite");
+  for (int i = 0; i < nq; ++i)
+    if (nG[i] < 1 || nG[i] > 4096) return bad("nG out of range");
+  if (kernel->kind < LRT_KERNEL_RPA || kernel->kind > LRT_KERNEL_FXC_MODEL)
+    return bad("unknown kernel kind");
+  lrt_options o{LRT_PREC_FP64, 0, 0};
+  if (opt) o = *opt;
+  if (o.precision < LRT_PREC_FP64 || o.precision > LRT_PREC_BF16X3) return bad("precision");
+
+  lrt_ctx* c = new (std::nothrow) lrt_ctx();
+  if (!c) {
+    set_error("host allocation");
+    return LRT_ENOMEM;
+  }
+  std::memcpy(c->lattice, cell->lattice, sizeof(c->lattice));
+  c->natoms = cell->natoms;
+  c->positions.assign(cell->positions, cell->positions + 3 * cell->natoms);
+  c->Z = cell->Z;
+  c->r_c = cell->r_c;
+  c->ecut = cell->ecut;
+  c->potential = cell->potential;
+  c->basis = cell->basis;
+  for (int i = 0; i < 3; ++i) c->kn[i] = kmesh->n[i];
+  c->kscheme = kmesh->scheme;
+  c->nk = c->kn[0] * c->kn[1] * c->kn[2];
+  c->nb = nbands;
+  c->T = T;
+  c->eta = eta;
+  c->nq = nq;
+  c->q.assign(q, q + 3 * nq);
+  c->nw = nw;
+  c->omega.assign(omega, omega + nw);
+  c->kernel = *kernel;
+  c->precision = o.precision;
+  c->device = o.device;
+  c->np = (int64_t)c->nk * c->nb * c->nb;
+  // internal frequencies: an exact 0 becomes h; otherwise h is appended
+  c->freqs = c->omega;
+  c->hcol = -1;
+  for (int j = 0; j < nw; ++j)
+    if (c->omega[j] == 0.0) {
+      c->freqs[j] = kHZero;
+      c->hcol = j;
+      break;
+    }
+  if (c->hcol < 0) {
+    c->freqs.push_back(kHZero);
+    c->hcol = nw;
+  }
+  c->nwi = (int)c->freqs.size();
+
+  c->host_only = (o.flags & LRT_FLAG_HOST_ONLY) != 0;
+  lrt_status st = [&]() -> lrt_status {
+    LRT_TRY(build_geometry(c, nG));
+    if (2.0 * c->nb < c->nelec) return bad("not enough bands to hold the electrons");
+    if (c->host_only) return LRT_OK;
+    LRT_CUDA(cudaSetDevice(c->device));
+    LRT_TRY(solve_ground_states(c, occupations));
+    for (auto& Q : c->qd) {
+      LRT_CUDA(cudaMalloc(&Q.Kdev, Q.nG * sizeof(double)));
+      LRT_CUDA(cudaMemcpy(Q.Kdev, Q.K.data(), Q.nG * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    LRT_CUDA(cudaMalloc(&c->dw.delta, c->np * sizeof(double)));
+    LRT_CUDA(cudaMalloc(&c->dw.df, c->np * sizeof(double)));
+    LRT_CUDA(cudaMalloc(&c->dw.freqs, c->nwi * sizeof(double)));
+    LRT_CUDA(cudaMalloc(&c->dw.omega, c->nw * sizeof(double)));
+    LRT_CUDA(cudaMalloc(&c->dw.S, (size_t)c->nq * c->nw * sizeof(double)));
+    LRT_CUDA(cudaMalloc(&c->dw.chi00, (size_t)c->nq * c->nwi * sizeof(double2)));
+    LRT_CUDA(cudaMalloc(&c->dw.status, sizeof(int)));
+    LRT_CUDA(cudaMemset(c->dw.status, 0, sizeof(int)));
+    LRT_CUDA(cudaMemcpy(c->dw.freqs, c->freqs.data(), c->nwi * sizeof(double),
+                        cudaMemcpyHostToDevice));
+    LRT_CUDA(cudaMemcpy(c->dw.omega, c->omega.data(), c->nw * sizeof(double),
+                        cudaMemcpyHostToDevice));
+    return LRT_OK;
+  }();
+  if (st != LRT_OK) {
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_destroy(lrt_ctx* ctx) {
+  free_ctx(ctx);
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_query(const lrt_ctx* c, int64_t out[8]) {
+  if (!c || !out) return bad("NULL argument");
+  out[0] = c->nq;
+  out[1] = c->nw;
+  out[2] = c->nk;
+  out[3] = c->nb;
+  out[4] = c->nGmax;
+  out[5] = c->npw;
+  out[6] = c->nwi;
+  out[7] = c->precision;
+  return LRT_OK;
+}
+
+static lrt_status need_device(const lrt_ctx* c) {
+  if (c->host_only) {
+    set_error("host-only context");
+    return LRT_ESTATE;
+  }
+  LRT_CUDA(cudaSetDevice(c->device));
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_chi0_assemble(lrt_ctx* c, int q_begin, int q_end, void* stream) {
+  if (!c) return bad("NULL context");
+  LRT_TRY(need_device(c));
+  if (q_begin < 0 || q_end > c->nq || q_begin >= q_end) return bad("q range");
+  cudaStream_t s = (cudaStream_t)stream;
+  LRT_CUDA(cudaSetDevice(c->device));
+  LRT_TRY(ensure_rho(c));
+  for (int iq = q_begin; iq < q_end; ++iq) {
+    QData& Q = c->qd[iq];
+    if (!Q.chi0) LRT_CUDA(cudaMalloc(&Q.chi0, (size_t)c->nwi * Q.nG * Q.nG * sizeof(double2)));
+    LRT_TRY(launch_pair_weights(c, Q, s));
+    LRT_TRY(launch_pair_density(c, Q, c->dw.rho, c->precision != LRT_PREC_FP64, s));
+    if (c->precision == LRT_PREC_FP64)
+      LRT_TRY(launch_chi0_fp64(c, Q, s));
+    else
+      LRT_TRY(launch_chi0_split(c, Q, s));
+    Q.have_chi0 = true;
+    Q.have_chi = false;
+  }
+  c->have_S = false;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_dyson_solve(lrt_ctx* c, int q_begin, int q_end, void* stream) {
+  if (!c) return bad("NULL context");
+  LRT_TRY(need_device(c));
+  if (q_begin < 0 || q_end > c->nq || q_begin >= q_end) return bad("q range");
+  cudaStream_t s = (cudaStream_t)stream;
+  LRT_CUDA(cudaSetDevice(c->device));
+  for (int iq = q_begin; iq < q_end; ++iq) {
+    QData& Q = c->qd[iq];
+    if (!Q.have_chi0) {
+      set_error("dyson_solve before chi0_assemble");
+      return LRT_ESTATE;
+    }
+    if (!Q.chi) LRT_CUDA(cudaMalloc(&Q.chi, (size_t)c->nwi * Q.nG * sizeof(double2)));
+    LRT_TRY(launch_dyson(c, Q, iq, s));
+    Q.have_chi = true;
+  }
+  c->have_S = false;
+  return LRT_OK;
+}
+
+static lrt_status need_all_chi(lrt_ctx* c) {
+  LRT_TRY(need_device(c));
+  for (auto& Q : c->qd)
+    if (!Q.have_chi) {
+      set_error("spectra requested before dyson_solve on every q");
+      return LRT_ESTATE;
+    }
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_dsf_device(lrt_ctx* c, double* S_dev, void* stream) {
+  if (!c || !S_dev) return bad("NULL argument");
+  LRT_TRY(need_all_chi(c));
+  LRT_TRY(launch_dsf(c, S_dev, (cudaStream_t)stream));
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_dsf(lrt_ctx* c, double* S) {
+  if (!c || !S) return bad("NULL argument");
+  LRT_TRY(need_all_chi(c));
+  LRT_TRY(launch_dsf(c, c->dw.S, 0));
+  LRT_CUDA(cudaMemcpy(S, c->dw.S, (size_t)c->nq * c->nw * sizeof(double), cudaMemcpyDeviceToHost));
+  LRT_TRY(check_status_word(c));
+  c->have_S = true;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_itcf_laplace_device(lrt_ctx* c, int ntau, const double* tau_dev,
+                                                  int mode, double* F_dev, double* metrics_dev,
+                                                  void* stream) {
+  if (!c || !tau_dev || !F_dev) return bad("NULL argument");
+  if (ntau < 1) return bad("ntau must be >= 1");
+  if (mode != LRT_ITCF_FOLD && mode != LRT_ITCF_DIRECT) return bad("unknown ITCF mode");
+  LRT_TRY(need_all_chi(c));
+  cudaStream_t s = (cudaStream_t)stream;
+  LRT_TRY(launch_dsf(c, c->dw.S, s));
+  LRT_TRY(launch_itcf(c, c->dw.S, ntau, tau_dev, mode, F_dev, metrics_dev, s));
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_itcf_laplace(lrt_ctx* c, int ntau, const double* tau, int mode,
+                                           double* F, double* metrics) {
+  if (!c || !tau || !F) return bad("NULL argument");
+  if (ntau < 1) return bad("ntau must be >= 1");
+  for (int i = 0; i < ntau; ++i)
+    if (!(tau[i] >= 0.0) || tau[i] > 1.0 / c->T * (1.0 + 1e-12)) return bad("tau outside [0, beta]");
+  LRT_TRY(need_device(c));
+  double *dtau = nullptr, *dF = nullptr, *dm = nullptr;
+  auto done = [&](lrt_status st) {
+    cudaFree(dtau);
+    cudaFree(dF);
+    cudaFree(dm);
+    return st;
+  };
+  if (cudaMalloc(&dtau, ntau * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dF, (size_t)c->nq * ntau * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dm, (size_t)c->nq * 5 * sizeof(double)) != cudaSuccess) {
+    set_error("device allocation");
+    return done(LRT_ENOMEM);
+  }
+  if (cudaMemcpy(dtau, tau, ntau * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return done(LRT_ECUDA);
+  lrt_status st = lrtddft_itcf_laplace_device(c, ntau, dtau, mode, dF, dm, 0);
+  if (st != LRT_OK) return done(st);
+  if (cudaMemcpy(F, dF, (size_t)c->nq * ntau * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return done(LRT_ECUDA);
+  if (metrics &&
+      cudaMemcpy(metrics, dm, (size_t)c->nq * 5 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return done(LRT_ECUDA);
+  return done(check_status_word(c));
+}
+
+extern "C" lrt_status lrtddft_attenuate(lrt_ctx* c, const lrt_atten_params* p, double* Sp,
+                                        lrt_atten_report* rep) {
+  if (!c || !Sp) return bad("NULL argument");
+  LRT_TRY(need_all_chi(c));
+  LRT_TRY(launch_dsf(c, c->dw.S, 0));
+  LRT_TRY(run_attenuation(c, p, c->dw.S, Sp, rep, 0));
+  return check_status_word(c);
+}
+
+extern "C" lrt_status lrtddft_set_orbitals(lrt_ctx* c, int iq, const double* eps,
+                                           const double* coeff, const double* occ) {
+  if (!c || !eps || !coeff) return bad("NULL argument");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  LRT_TRY(need_device(c));
+  LRT_CUDA(cudaSetDevice(c->device));
+  QData& Q = c->qd[iq];
+  size_t ne = (size_t)2 * c->nk * c->nb;
+  LRT_CUDA(cudaMemcpy(Q.eps, eps, ne * sizeof(double), cudaMemcpyHostToDevice));
+  LRT_CUDA(cudaMemcpy(Q.coeff, coeff, ne * c->npw * sizeof(double2), cudaMemcpyHostToDevice));
+  if (occ) {
+    Q.mu = NAN;
+    LRT_CUDA(cudaMemcpy(Q.occ, occ, ne * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    LRT_TRY(set_occupations_fd(c, iq, eps));
+  }
+  Q.have_chi0 = Q.have_chi = false;
+  c->have_S = false;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_basis(const lrt_ctx* c, int iq, int32_t* miller, int32_t* npw_k) {
+  if (!c || !miller || !npw_k) return bad("NULL argument");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  const QData& Q = c->qd[iq];
+  std::copy(Q.miller.begin(), Q.miller.end(), miller);
+  std::copy(Q.npw_k.begin(), Q.npw_k.end(), npw_k);
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_ground_state(const lrt_ctx* c, int iq, double* eps, double* occ,
+                                               double* mu) {
+  if (!c) return bad("NULL context");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  LRT_TRY(need_device(c));
+  const QData& Q = c->qd[iq];
+  size_t ne = (size_t)2 * c->nk * c->nb;
+  if (eps) LRT_CUDA(cudaMemcpy(eps, Q.eps, ne * sizeof(double), cudaMemcpyDeviceToHost));
+  if (occ) LRT_CUDA(cudaMemcpy(occ, Q.occ, ne * sizeof(double), cudaMemcpyDeviceToHost));
+  if (mu) *mu = Q.mu;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_gset(const lrt_ctx* c, int iq, int32_t* miller, double* K) {
+  if (!c) return bad("NULL context");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  const QData& Q = c->qd[iq];
+  if (miller) std::copy(Q.gset.begin(), Q.gset.end(), miller);
+  if (K) std::copy(Q.K.begin(), Q.K.end(), K);
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_chi0(const lrt_ctx* c, int iq, double* chi0) {
+  if (!c || !chi0) return bad("NULL argument");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  const QData& Q = c->qd[iq];
+  if (!Q.have_chi0) {
+    set_error("get_chi0 before chi0_assemble");
+    return LRT_ESTATE;
+  }
+  LRT_CUDA(cudaMemcpy(chi0, Q.chi0, (size_t)c->nwi * Q.nG * Q.nG * sizeof(double2),
+                      cudaMemcpyDeviceToHost));
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_chi_col0(const lrt_ctx* c, int iq, double* chi) {
+  if (!c || !chi) return bad("NULL argument");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  const QData& Q = c->qd[iq];
+  if (!Q.have_chi) {
+    set_error("get_chi_col0 before dyson_solve");
+    return LRT_ESTATE;
+  }
+  LRT_CUDA(cudaMemcpy(chi, Q.chi, (size_t)c->nwi * Q.nG * sizeof(double2), cudaMemcpyDeviceToHost));
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_frequencies(const lrt_ctx* c, double* freqs, int* hcol) {
+  if (!c) return bad("NULL context");
+  if (freqs) std::copy(c->freqs.begin(), c->freqs.end(), freqs);
+  if (hcol) *hcol = c->hcol;
+  return LRT_OK;
+}

@@ -1,0 +1,141 @@
+// Internal declarations of liblrtddft: the context, error plumbing and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lrtddft.h"
+
+namespace lrt {
+
+constexpr double kHZero = 1e-6;        // Ha; frequency standing in for w -> 0 in S(q,0)
+constexpr double kBasisTol = 1e-9;     // |k+G|^2 <= 2 ecut + kBasisTol
+constexpr double kShellTol = 1e-9;     // |q+G|^2 (and |G|^2) closer than this: same shell
+constexpr double kPadDiag = 1.0e6;     // Ha; diagonal of the padding rows of H(k)
+
+// Thread-local message of the last failure.
+void set_error(const std::string& msg);
+const char* last_error();
+
+// Per-q data.  Meshes are indexed s = 0 (k points) and s = 1 (k+q points).
+struct QData {
+  int nG = 0;
+  std::vector<int32_t> gset;      // [nG][3], G = 0 first
+  std::vector<double> K;          // [nG]
+  double* Kdev = nullptr;         // device [nG]
+  std::vector<double> kpts;       // [2][nk][3] Cartesian
+  std::vector<int32_t> miller;    // [2][nk][npw][3], padding INT32_MIN
+  std::vector<int32_t> npw_k;     // [2][nk]
+  double mu = 0.0;
+  double* eps = nullptr;          // device [2][nk][nb]
+  double* occ = nullptr;          // device [2][nk][nb]
+  double2* coeff = nullptr;       // device [2][nk][nb][npw]
+  int32_t* gather = nullptr;      // device [nk][nG][npw]: index into the k+q basis or -1
+  double2* chi0 = nullptr;        // device [nwi][nG][nG]
+  double2* chi = nullptr;         // device [nwi][nG]  (chi_{G,0})
+  bool have_chi0 = false;
+  bool have_chi = false;
+};
+
+struct DeviceWork {
+  void* rho = nullptr;            // [nGmax][np] complex (FP64 or FP32 by precision)
+  size_t rho_bytes = 0;
+  double* delta = nullptr;        // [np]
+  double* df = nullptr;           // [np]
+  double* freqs = nullptr;        // [nwi]
+  double* omega = nullptr;        // [nw]
+  double* S = nullptr;            // [nq][nw]
+  double* chi00 = nullptr;        // [nq][nwi][2] gather of chi_00 for the spectra kernels
+  int* status = nullptr;          // device status word (0 ok, bit 1 singular, bit 2 timeout)
+  double* scratch = nullptr;      // chi0 FP64 split-K partials (tensor path)
+  size_t scratch_bytes = 0;
+};
+
+}  // namespace lrt
+
+struct lrt_ctx {
+  // inputs
+  double lattice[3][3];
+  double recip[3][3];
+  double volume = 0.0;
+  std::vector<double> positions;  // [natoms][3]
+  int natoms = 0;
+  double Z = 0.0, r_c = 0.0, ecut = 0.0;
+  int potential = 0, basis = 0;
+  int kn[3] = {1, 1, 1};
+  int kscheme = 0;
+  int nk = 0;
+  int nb = 0;
+  double T = 0.0, eta = 0.0;
+  int nq = 0;
+  std::vector<double> q;          // [nq][3]
+  int nw = 0;
+  std::vector<double> omega;      // [nw]
+  std::vector<double> freqs;      // [nwi] internal frequencies
+  int nwi = 0;
+  int hcol = 0;
+  lrt_kernel kernel{};
+  int precision = 0;
+  int device = 0;
+  double density = 0.0;           // N_e / Omega
+  double nelec = 0.0;
+  double fxc = 0.0;               // f_ALDA at the mean density
+  int npw = 0;                    // padded plane-wave count (max over all k points)
+  int nGmax = 0;
+  int64_t np = 0;                 // pairs per q = nk nb^2
+  std::vector<lrt::QData> qd;
+  lrt::DeviceWork dw;
+  bool have_S = false;
+  bool host_only = false;
+};
+
+namespace lrt {
+
+// setup.cu
+lrt_status build_geometry(lrt_ctx* c, const int* nG);
+lrt_status solve_ground_states(lrt_ctx* c, const double* occupations);
+lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host);
+double fxc_alda(double n);
+double fxc_model(double qg, double n, double A, double B, double C);
+
+// pairdens.cu: rho[G][p] for one q (FP64 or FP32 storage)
+lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool fp32,
+                               cudaStream_t s);
+lrt_status launch_pair_weights(const lrt_ctx* c, const QData& q, cudaStream_t s);
+
+// chi0_fp64.cu
+lrt_status launch_chi0_fp64(const lrt_ctx* c, QData& q, cudaStream_t s);
+// chi0_tc.cu
+lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s);
+
+// dyson.cu
+lrt_status launch_dyson(const lrt_ctx* c, QData& q, int iq, cudaStream_t s);
+
+// spectra.cu
+lrt_status launch_dsf(const lrt_ctx* c, double* S_dev, cudaStream_t s);
+lrt_status launch_itcf(const lrt_ctx* c, const double* S_dev, int ntau, const double* tau_dev,
+                       int mode, double* F_dev, double* metrics_dev, cudaStream_t s);
+
+// attenuate.cu
+lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* p, const double* S_dev,
+                           double* Sp_host, lrt_atten_report* rep, cudaStream_t s);
+
+}  // namespace lrt
+
+#define LRT_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      lrt::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
+      return (e_ == cudaErrorMemoryAllocation) ? LRT_ENOMEM : LRT_ECUDA;                \
+    }                                                                                   \
+  } while (0)
+
+#define LRT_TRY(call)                                                                   \
+  do {                                                                                  \
+    lrt_status s_ = (call);                                                             \
+    if (s_ != LRT_OK) return s_;                                                        \
+  } while (0)
