@@ -147,7 +147,8 @@ lrt_status lrtddft_chi0_assemble(lrt_ctx* ctx, int q_begin, int q_end, void* str
 lrt_status lrtddft_dyson_solve(lrt_ctx* ctx, int q_begin, int q_end, void* stream);
 
 /* S(q,w) (Eq. 8) on the caller's grid: S [nq][nw].  At w = 0 the limit
- * -Im chi_00(h)/(pi n h / T), h = 1e-6 Ha, is used.  Requires dyson_solve for every q. */
+ * -Im chi_00(h)/(pi n h / T), h = 1e-4 Ha, is used (Im chi_00 is odd in w, so the step
+ * costs O((h/eta)^2)).  Requires dyson_solve for every q. */
 lrt_status lrtddft_dsf(lrt_ctx* ctx, double* S);
 lrt_status lrtddft_dsf_device(lrt_ctx* ctx, double* S_dev, void* stream);
 
@@ -175,7 +176,8 @@ typedef struct {
   double low_exclude;       /* lowest fraction of Fourier frequencies ignored [0.05] */
   double accept_mean;       /* |Fbar_n| / F(beta/2) limit [4e-3] (Sec. 3) */
   double accept_rms;        /* sigma_n / F(beta/2) limit [4.2e-5] (Sec. 3) */
-  int average;              /* 1: S_p = mean over accepted degrees (Sec. 4.1); 0: best [1] */
+  int average;              /* 0 or 1: S_p = mean over the accepted degrees (Sec. 4.1);
+                               2: the accepted degree with the lowest score */
   int ntau;                 /* tau points on [0, beta/2] for the constraints [64] */
   double retain_floor;      /* r0 [1e-4] */
 } lrt_atten_params;

@@ -12,7 +12,8 @@ Definitions (Hartree atomic units, spin factor 2, Omega = cell volume, N_k = k p
   chi = (1 - chi0 K)^{-1} chi0; only chi_{G,0} is solved for.
   S(q,w) = -Im chi_00(q,w) / (pi n (1 - e^{-beta w}))          fluctuation-dissipation, Eq. 8
            (hbar = 1; the 1/pi makes int w S dw = q^2/2, the f-sum rule)
-  S(q,0) = -Im chi_00(q,h) / (pi n beta h), h = 1e-6 Ha    (the w -> 0 limit; Im chi_00 is odd)
+  S(q,0) = -Im chi_00(q,h) / (pi n beta h), h = 1e-4 Ha    (the w -> 0 limit; Im chi_00 is odd,
+           so the step costs O((h/eta)^2); a smaller h amplifies the cancellation in Im chi(h))
   F(q,tau) = int dw S(q,w) e^{-tau w}                        two-sided Laplace transform, Eq. 1
            = int_0^wmax S(w) [e^{-tau w} + e^{-(beta-tau) w}] dw   using detailed balance
              S(-w) = e^{-beta w} S(w) (FOLD mode, trapezoid over the w >= 0 samples)
@@ -35,7 +36,7 @@ import numpy as np
 
 from . import crystal, occupations, xc
 
-H_ZERO = 1e-6     # Ha; frequency used for the w -> 0 limit of S
+H_ZERO = 1e-4     # Ha; frequency used for the w -> 0 limit of S
 
 
 def _lookup(basis: np.ndarray):

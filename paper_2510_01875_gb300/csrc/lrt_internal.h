@@ -11,7 +11,7 @@
 
 namespace lrt {
 
-constexpr double kHZero = 1e-6;        // Ha; frequency standing in for w -> 0 in S(q,0)
+constexpr double kHZero = 1e-4;        // Ha; frequency standing in for w -> 0 in S(q,0)
 constexpr double kBasisTol = 1e-9;     // |k+G|^2 <= 2 ecut + kBasisTol
 constexpr double kShellTol = 1e-9;     // |q+G|^2 (and |G|^2) closer than this: same shell
 constexpr double kPadDiag = 1.0e6;     // Ha; diagonal of the padding rows of H(k)

@@ -1,7 +1,7 @@
 // S(q,w) by the fluctuation-dissipation theorem (Eq. 8) and F(q,tau) by the two-sided
 // Laplace transform (Eq. 1), FP64, one warp per output with a shuffle reduction.
 //   S(q,w) = -Im chi_00(q,w) / (pi n (1 - e^{-w/T})), the denominator as -expm1(-w/T);
-//   S(q,0) = -Im chi_00(q,h) / (pi n h / T), h = 1e-6 Ha (Im chi_00 is odd in w).
+//   S(q,0) = -Im chi_00(q,h) / (pi n h / T), h = 1e-4 Ha (Im chi_00 is odd in w).
 //   FOLD:   F(tau) = sum_i wt_i S_i [e^{-tau w_i} + e^{-(beta - tau) w_i}] over the w >= 0
 //           samples plus w = 0 (detailed balance S(-w) = e^{-beta w} S(w)), trapezoid wt;
 //   DIRECT: F(tau) = sum_j wt_j S_j e^{-tau w_j} over the caller's grid.
