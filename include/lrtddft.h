@@ -132,7 +132,8 @@ const char* lrtddft_status_string(lrt_status s);
 /* Detail of the last failure on this thread (static storage; valid until the next call). */
 const char* lrtddft_last_error(void);
 
-/* Sizes of a context: out[0..7] = nq, nw, nk, nbands, max nG, plane waves (padded), number of
+/* Sizes of a context: out[0..7] = nq, nw, nk, nb (bands carried per k point: nbands plus the
+ * members of any degenerate multiplet split by the band cut), max nG, plane waves (padded), number of
  * internal frequencies (nw plus the w -> 0 column when 0 is not on the grid), precision. */
 lrt_status lrtddft_query(const lrt_ctx* ctx, int64_t out[8]);
 
@@ -201,18 +202,25 @@ lrt_status lrtddft_attenuate(lrt_ctx* ctx, const lrt_atten_params* params, doubl
 
 /* ---- test and debug hooks ---- */
 
-/* Replace the orbitals of q index iq: eps [2][nk][nbands] (k mesh then k+q mesh),
- * coeff [2][nk][nbands][npw] complex on the context's padded basis order (see
- * lrtddft_get_basis), occ [2][nk][nbands] or NULL (keep Fermi-Dirac with a new mu).
+/* Replace the orbitals of q index iq: eps [2][nk][nb] ascending per k point (k mesh then k+q
+ * mesh), coeff [2][nk][nb][npw] complex on the context's padded basis order (see
+ * lrtddft_get_basis), occ [2][nk][nb] or NULL (Fermi-Dirac with a new mu).  The band weights
+ * are recomputed from eps.
  * Host pointers. */
 lrt_status lrtddft_set_orbitals(lrt_ctx* ctx, int iq, const double* eps, const double* coeff,
                                 const double* occ);
 /* Miller indices of the padded basis of q index iq: miller [2][nk][npw][3] (int32; padding
  * rows hold INT32_MIN), npw_k [2][nk]. */
 lrt_status lrtddft_get_basis(const lrt_ctx* ctx, int iq, int32_t* miller, int32_t* npw_k);
-/* Eigenvalues [2][nk][nbands], occupations [2][nk][nbands] and mu of q index iq. */
+/* Eigenvalues [2][nk][nb], occupations [2][nk][nb], band weights [2][nk][nb] and mu of q
+ * index iq (each pointer may be NULL); nb = lrtddft_query out[3] >= nbands.  The weights are
+ * 1 for the lowest nbands bands and 0 above, except on a degenerate multiplet (eigenvalues
+ * within 1e-6 Ha of band nbands-1) that the band cut splits: there each of its m members
+ * carries j/m (j members below the cut), so that the kept band projector does not depend on
+ * the eigensolver's choice of basis inside the multiplet.  A pair enters chi0 with
+ * df_p = w_nk w_n'k+q (f_nk - f_n'k+q). */
 lrt_status lrtddft_get_ground_state(const lrt_ctx* ctx, int iq, double* eps, double* occ,
-                                    double* mu);
+                                    double* weights, double* mu);
 /* Response G-set of q index iq: miller [nG][3] (G = 0 first) and K_GG [nG]. */
 lrt_status lrtddft_get_gset(const lrt_ctx* ctx, int iq, int32_t* miller, double* K);
 /* chi0 of q index iq: [nw_int][nG][nG] complex, at the internal frequencies

@@ -18,20 +18,25 @@ def fermi(eps, mu: float, T: float):
     return expit(-(np.asarray(eps) - mu) / T)
 
 
-def electron_count(eps, mu: float, T: float, nk: int) -> float:
-    return 2.0 * float(np.sum(fermi(eps, mu, T))) / nk
+def electron_count(eps, mu: float, T: float, nk: int, weights=None) -> float:
+    f = fermi(eps, mu, T)
+    if weights is not None:
+        f = f * weights
+    return 2.0 * float(np.sum(f)) / nk
 
 
-def chemical_potential(eps, T: float, nelec: float, nk: int) -> float:
-    """Bisection for mu with 200 halvings of [min(eps) - 60 T, max(eps) + 60 T]."""
+def chemical_potential(eps, T: float, nelec: float, nk: int, weights=None) -> float:
+    """Bisection for mu with 200 halvings of [min(eps) - 60 T, max(eps) + 60 T]; `weights`
+    (band weights of a split degenerate multiplet, else 1) multiply each state's count."""
     eps = np.asarray(eps)
-    if 2.0 * eps.size / nk < nelec:
+    cap = eps.size if weights is None else float(np.sum(weights))
+    if 2.0 * cap / nk < nelec:
         raise ValueError("not enough bands to hold the electrons")
     lo = float(eps.min()) - 60.0 * T
     hi = float(eps.max()) + 60.0 * T
     for _ in range(200):
         mid = 0.5 * (lo + hi)
-        if electron_count(eps, mid, T, nk) < nelec:
+        if electron_count(eps, mid, T, nk, weights) < nelec:
             lo = mid
         else:
             hi = mid

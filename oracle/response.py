@@ -37,6 +37,8 @@ import numpy as np
 from . import crystal, occupations, xc
 
 H_ZERO = 1e-4     # Ha; frequency used for the w -> 0 limit of S
+DEGEN_TOL = 1e-6  # Ha; eigenvalues this close to the last kept band form one multiplet
+EXTRA_BANDS = 8   # eigenpairs computed beyond nbands to see a multiplet split by the cut
 
 
 def _lookup(basis: np.ndarray):
@@ -73,29 +75,61 @@ def density(wl) -> float:
     return wl.Z * wl.natoms / crystal.volume(wl.lattice)
 
 
+def band_weights(e, nbands: int) -> np.ndarray:
+    """Weights of the computed bands e (ascending): 1 for the lowest nbands, 0 above, except
+    that a degenerate multiplet (|e_n - e_{nbands-1}| <= DEGEN_TOL) split by the cut keeps
+    its share j/m on each of its m members (j of them below the cut).  The projector onto
+    "the lowest nbands states" is then gauge-invariant, which it is not when the cut runs
+    through a multiplet (e.g. at high-symmetry k of a Gamma-centred mesh)."""
+    e = np.asarray(e)
+    w = np.zeros(len(e))
+    w[:nbands] = 1.0
+    mem = np.where(np.abs(e - e[nbands - 1]) <= DEGEN_TOL)[0]
+    j, m = int(np.sum(mem < nbands)), len(mem)
+    if m > j:
+        if mem.max() >= len(e) - 1:
+            raise ValueError("degenerate multiplet at the band cut extends past the computed bands")
+        w[mem] = j / m
+    return w
+
+
 def ground_state(wl, iq: int):
-    """Eigenpairs on the k and k+q meshes of q index iq, the occupations and mu."""
+    """Eigenpairs on the k and k+q meshes of q index iq, band weights, occupations and mu.
+    Arrays carry nb >= nbands bands: nbands plus any members of a multiplet split by the cut."""
     q = wl.q[iq]
     kpts, kqpts = crystal.pair_meshes(wl.lattice, wl.kmesh, q, wl.kscheme)
     out = {"k": kpts, "kq": kqpts, "eps_k": [], "eps_kq": [], "C_k": [], "C_kq": [],
-           "basis_k": [], "basis_kq": []}
+           "basis_k": [], "basis_kq": [], "w_k": [], "w_kq": []}
     for tag, pts in (("k", kpts), ("kq", kqpts)):
         for kv in pts:
             b = basis_for(wl, kv)
-            e, C = crystal.eigenstates(wl.lattice, wl.positions, wl.Z, wl.r_c, kv, b, wl.nbands,
+            nfull = min(len(b), wl.nbands + EXTRA_BANDS)
+            e, C = crystal.eigenstates(wl.lattice, wl.positions, wl.Z, wl.r_c, kv, b, nfull,
                                        wl.potential)
             out["eps_" + tag].append(e)
             out["C_" + tag].append(C)
             out["basis_" + tag].append(b)
-    out["eps_k"] = np.array(out["eps_k"])
-    out["eps_kq"] = np.array(out["eps_kq"])
+            if wl.occupations is not None:
+                w = np.zeros(nfull)
+                w[:wl.nbands] = 1.0
+            else:
+                w = band_weights(e, wl.nbands)
+            out["w_" + tag].append(w)
+    nb = max(int(np.max(np.nonzero(w)[0])) + 1 for w in out["w_k"] + out["w_kq"])
+    for tag in ("k", "kq"):
+        out["eps_" + tag] = np.array([e[:nb] for e in out["eps_" + tag]])
+        out["C_" + tag] = [C[:, :nb] for C in out["C_" + tag]]
+        out["w_" + tag] = np.array([w[:nb] for w in out["w_" + tag]])
+    out["nb"] = nb
     nelec = wl.Z * wl.natoms
     if wl.occupations is not None:
         out["mu"] = float("nan")
-        out["f_k"] = np.asarray(wl.occupations[iq][0])
-        out["f_kq"] = np.asarray(wl.occupations[iq][1])
+        out["f_k"] = np.zeros((wl.nk, nb))
+        out["f_kq"] = np.zeros((wl.nk, nb))
+        out["f_k"][:, :wl.nbands] = np.asarray(wl.occupations[iq][0])
+        out["f_kq"][:, :wl.nbands] = np.asarray(wl.occupations[iq][1])
     else:
-        mu = occupations.chemical_potential(out["eps_k"], wl.T, nelec, wl.nk)
+        mu = occupations.chemical_potential(out["eps_k"], wl.T, nelec, wl.nk, out["w_k"])
         out["mu"] = mu
         out["f_k"] = occupations.fermi(out["eps_k"], mu, wl.T)
         out["f_kq"] = occupations.fermi(out["eps_kq"], mu, wl.T)
@@ -109,9 +143,11 @@ def pair_densities(wl, gs, gset) -> np.ndarray:
 
 
 def pair_weights(gs):
-    """Delta_p and df_p flattened in (k, n, n') order."""
+    """Delta_p and df_p = w_nk w_n'k+q (f_nk - f_n'k+q) flattened in (k, n, n') order (the band
+    weights w are 1 except on a multiplet split by the band cut)."""
     d = gs["eps_k"][:, :, None] - gs["eps_kq"][:, None, :]
     df = gs["f_k"][:, :, None] - gs["f_kq"][:, None, :]
+    df = df * gs["w_k"][:, :, None] * gs["w_kq"][:, None, :]
     return d.reshape(-1), df.reshape(-1)
 
 

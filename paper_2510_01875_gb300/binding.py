@@ -89,7 +89,7 @@ SIGNATURES = {
     "lrtddft_attenuate": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D, C.POINTER(lrt_atten_report)]),
     "lrtddft_set_orbitals": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "lrtddft_get_basis": (C.c_int, [_P, C.c_int, _I32, _I32]),
-    "lrtddft_get_ground_state": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "lrtddft_get_ground_state": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
     "lrtddft_get_gset": (C.c_int, [_P, C.c_int, _I32, _D]),
     "lrtddft_get_chi0": (C.c_int, [_P, C.c_int, _D]),
     "lrtddft_get_chi_col0": (C.c_int, [_P, C.c_int, _D]),
@@ -237,10 +237,11 @@ class Context:
     def get_ground_state(self, iq: int):
         e = np.zeros((2, self.nk, self.nb))
         f = np.zeros((2, self.nk, self.nb))
+        w = np.zeros((2, self.nk, self.nb))
         mu = C.c_double()
         _check("lrtddft_get_ground_state", self.lib.lrtddft_get_ground_state(
-            self.h, iq, _dp(e), _dp(f), C.byref(mu)))
-        return e, f, mu.value
+            self.h, iq, _dp(e), _dp(f), _dp(w), C.byref(mu)))
+        return e, f, mu.value, w
 
     def get_gset(self, iq: int):
         nG = int(self.wl.nG[iq])

@@ -32,6 +32,7 @@ void free_ctx(lrt_ctx* c) {
     cudaFree(q.Kdev);
     cudaFree(q.eps);
     cudaFree(q.occ);
+    cudaFree(q.wgt);
     cudaFree(q.coeff);
     cudaFree(q.gather);
     cudaFree(q.chi0);
@@ -147,6 +148,7 @@ extern "C" lrt_status lrtddft_create(const lrt_cell* cell, const lrt_kmesh* kmes
   for (int i = 0; i < 3; ++i) c->kn[i] = kmesh->n[i];
   c->kscheme = kmesh->scheme;
   c->nk = c->kn[0] * c->kn[1] * c->kn[2];
+  c->nbands = nbands;
   c->nb = nbands;
   c->T = T;
   c->eta = eta;
@@ -367,6 +369,7 @@ extern "C" lrt_status lrtddft_set_orbitals(lrt_ctx* c, int iq, const double* eps
   size_t ne = (size_t)2 * c->nk * c->nb;
   LRT_CUDA(cudaMemcpy(Q.eps, eps, ne * sizeof(double), cudaMemcpyHostToDevice));
   LRT_CUDA(cudaMemcpy(Q.coeff, coeff, ne * c->npw * sizeof(double2), cudaMemcpyHostToDevice));
+  LRT_TRY(reset_band_weights(c, iq, eps));
   if (occ) {
     Q.mu = NAN;
     LRT_CUDA(cudaMemcpy(Q.occ, occ, ne * sizeof(double), cudaMemcpyHostToDevice));
@@ -388,7 +391,7 @@ extern "C" lrt_status lrtddft_get_basis(const lrt_ctx* c, int iq, int32_t* mille
 }
 
 extern "C" lrt_status lrtddft_get_ground_state(const lrt_ctx* c, int iq, double* eps, double* occ,
-                                               double* mu) {
+                                               double* weights, double* mu) {
   if (!c) return bad("NULL context");
   if (iq < 0 || iq >= c->nq) return bad("q index");
   LRT_TRY(need_device(c));
@@ -396,6 +399,7 @@ extern "C" lrt_status lrtddft_get_ground_state(const lrt_ctx* c, int iq, double*
   size_t ne = (size_t)2 * c->nk * c->nb;
   if (eps) LRT_CUDA(cudaMemcpy(eps, Q.eps, ne * sizeof(double), cudaMemcpyDeviceToHost));
   if (occ) LRT_CUDA(cudaMemcpy(occ, Q.occ, ne * sizeof(double), cudaMemcpyDeviceToHost));
+  if (weights) std::copy(Q.wgt_h.begin(), Q.wgt_h.end(), weights);
   if (mu) *mu = Q.mu;
   return LRT_OK;
 }

@@ -555,7 +555,7 @@ lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const 
   size_t dw_sz = (size_t)nq * cfg.ncand * cfg.L;
   size_t bytes = (prep_sz + yf_sz + dw_sz + (size_t)nq * cfg.ntau + (size_t)nq * c->nw) * sizeof(double) +
                  nq * sizeof(AttQ) + (size_t)nq * cfg.ncand * sizeof(CandOut) +
-                 (size_t)nq * kMaxDegree * sizeof(DegOut) + cfg.ncand * sizeof(int2) + nq * sizeof(int) + 1024;
+                 (size_t)nq * kMaxDegree * sizeof(DegOut) + cfg.ncand * sizeof(int2) + nq * sizeof(int) + 16 * 256;
   char* buf = nullptr;
   LRT_CUDA(cudaMalloc(&buf, bytes));
   struct Free {

@@ -1,12 +1,583 @@
-// Split-precision chi0 on the tcgen05 tensor cores (see the kernel below).
+// Split-precision Adler-Wiser chi0 on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The contraction chi0_GG'(w) = pref sum_p rho_p(G) rho_p*(G') w_p(w) is run as one real GEMM
+//   C[r][c] = sum_p A[r][p] B[p][c]
+// with Hermitian-split rows r = (G <= G', Re|Im of P_p = rho_p(G) rho_p*(G')) and columns
+// c = (w, Re|Im of w_p(w) = df_p / (w + Delta_p + i eta)).  From RR, RI, IR, II of a row pair
+// and a column pair, chi0(G,G') = (RR - II) + i(RI + IR) and chi0(G',G) = (RR + II) + i(RI - IR).
+//
+// Both operands are generated inside the kernel and never stored in global memory: producer
+// warps read rho (FP32, [G][p]) and (Delta_p, df_p), form P and w in FP32, split every value
+// v into v_hi = round16(v) and v_lo = round16(v - v_hi) (FP16 with power-of-two scaling, or
+// BF16), and write the four tiles MN-major with the 128-byte swizzle (one lane per pair =
+// per K index; 16-byte vector stores of 8 consecutive rows or columns).  One thread issues
+// tcgen05.mma kind::f16 for A_hi B_hi + A_hi B_lo + A_lo B_hi into an FP32 accumulator in
+// tensor memory; every `flush` stages the accumulator is drained by four epilogue warps
+// (tcgen05.ld) into FP64 sums in global memory while the MMAs continue in the second
+// accumulator.  Units of work are (row tile, column tile, pair range), handed out round-robin
+// to one CTA per SM.  Every wait on an mbarrier is bounded; on expiry the kernel sets bit 2 of
+// the status word, stops issuing work, waits (bounded) for its own MMAs and frees its tensor
+// memory before returning.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "lrt_internal.h"
 
 namespace lrt {
+namespace {
+
+constexpr int TM = 128;            // GEMM rows per tile (64 row pairs)
+constexpr int TN = 256;            // GEMM columns per tile (128 frequencies)
+constexpr int KS = 32;             // pairs (K) per pipeline stage
+constexpr int NS = 4;              // pipeline stages
+constexpr int NPROD = 8;           // producer warps 0..7
+constexpr int WMMA = 8;            // MMA warp
+constexpr int NTHREADS = 13 * 32;
+constexpr int A_BYTES = TM * KS * 2;                 // 8 KB per 16-bit tile
+constexpr int B_BYTES = TN * KS * 2;                 // 16 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int A_SBO = (TM / 64) * 1024;              // bytes between 8-pair groups of A
+constexpr int B_SBO = (TN / 64) * 1024;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+struct Params {
+  const float2* rho;          // [nG][np]
+  const float4* pw;           // [np] {Delta_hi, Delta_lo, df, 0}
+  const int2* rowtab;         // [n_m * 64] (G, G') per row pair, (-1, -1) padding
+  const float2* wtab;         // [n_n * 128] frequency hi/lo per column pair
+  double* C;                  // [n_m * TM][ldc] FP64 sums
+  int* status;
+  long long np;
+  int ldc;                    // = n_n * TN
+  int rows_valid;             // 2 * row pairs
+  int cols_valid;             // 2 * nwi
+  int n_m, n_n, n_split;
+  long long k_per_split;      // multiple of KS
+  int flush;                  // stages per accumulator period
+  float eta, sA, sB;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when this CTA is aborting or the wait ran out (then it starts the abort).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                          int* status) {
+  unsigned long long t0 = 0;
+  uint32_t n = 0;
+  while (!mbar_try(b, parity)) {
+    if (*abort_flag) return false;
+    if ((++n & 255u) == 0) {
+      unsigned long long t = gtime();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        atomicOr(status, 2);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: start >> 4, LBO >> 4 at bit 16, SBO >> 4 at bit 32,
+// version 1 at bit 46, 128-byte swizzle (2) at bits 61-63.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(b))
+      : "memory");
+}
+
+// Offset of the 16-byte chunk holding MN elements [8c, 8c+8) of K index k in an MN-major,
+// 128-byte-swizzled tile: [k/8][mn/64][k%8][64 elements], chunk (mn%64)/8 XOR k%8.
+__device__ __forceinline__ uint32_t mn_chunk(int k, int c, int sbo) {
+  return (uint32_t)((k >> 3) * sbo + (c >> 3) * 1024 + (k & 7) * 128 + (((c & 7) ^ (k & 7)) << 4));
+}
+
+template <bool BF>
+struct Pack;
+template <>
+struct Pack<false> {
+  // 8 floats -> hi and lo as 8 x f16 each
+  __device__ __forceinline__ static void split(const float* v, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 a = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+      float2 af = __half22float2(a);
+      __half2 b = __floats2half2_rn(v[2 * i] - af.x, v[2 * i + 1] - af.y);
+      h[i] = *reinterpret_cast<uint32_t*>(&a);
+      l[i] = *reinterpret_cast<uint32_t*>(&b);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+};
+template <>
+struct Pack<true> {
+  __device__ __forceinline__ static void split(const float* v, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __nv_bfloat162 a = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      float2 af = __bfloat1622float2(a);
+      __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i] - af.x, v[2 * i + 1] - af.y);
+      h[i] = *reinterpret_cast<uint32_t*>(&a);
+      l[i] = *reinterpret_cast<uint32_t*>(&b);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+};
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
+
+struct Unit {
+  int mt, nt;
+  long long kb, ke;
+};
+__device__ __forceinline__ Unit unit_of(const Params& P, int u) {
+  Unit U;
+  int tile = u / P.n_split, ks = u % P.n_split;
+  U.mt = tile / P.n_n;
+  U.nt = tile % P.n_n;
+  U.kb = (long long)ks * P.k_per_split;
+  U.ke = min(P.np, U.kb + P.k_per_split);
+  return U;
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], final_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int2 rowtab_s[64];
+  __shared__ float2 wtab_s[128];
+  __shared__ volatile int abort_s;
+  __shared__ int unit_sync;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* base_gen = smem_raw + (base - smem_u32(smem_raw));
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], NPROD);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(&final_bar, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == WMMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(2 * TN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+  const int nunits = P.n_m * P.n_n * P.n_split;
+  const uint32_t idesc = (1u << 4) | ((BF ? 1u : 0u) << 7) | ((BF ? 1u : 0u) << 10) | (1u << 15) |
+                         (1u << 16) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+  uint32_t it = 0;   // stage counter (producers and MMA)
+  uint32_t pc = 0;   // accumulator period counter (MMA and epilogue)
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const Unit U = unit_of(P, u);
+    // per-unit tables (row pairs of the row tile, frequencies of the column tile)
+    __syncthreads();
+    if (threadIdx.x < 64) rowtab_s[threadIdx.x] = P.rowtab[U.mt * 64 + threadIdx.x];
+    if (threadIdx.x < 128) wtab_s[threadIdx.x] = P.wtab[U.nt * 128 + threadIdx.x];
+    __syncthreads();
+    if (abort_s) break;
+    const long long nstage = (U.ke - U.kb + KS - 1) / KS;
+    const long long nper = (nstage + P.flush - 1) / P.flush;
+
+    if (warp < NPROD) {
+      // ---------------- producers ----------------
+      for (long long st = 0; st < nstage; ++st, ++it) {
+        const int s = it % NS;
+        if (!mbar_wait(&empty[s], ((it / NS) & 1) ^ 1, &abort_s, P.status)) break;
+        const long long p = U.kb + st * KS + lane;
+        const bool valid = p < U.ke;
+        float4 pw = valid ? P.pw[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t sA_hi = base + s * STAGE_BYTES, sA_lo = sA_hi + A_BYTES;
+        const uint32_t sB_hi = sA_lo + A_BYTES, sB_lo = sB_hi + B_BYTES;
+#pragma unroll 1
+        for (int cc = 0; cc < 6; ++cc) {
+          const int c = warp * 6 + cc;   // 0..15 A chunks, 16..47 B chunks
+          float v[8];
+          if (c < 16) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              int2 g = rowtab_s[4 * c + i];
+              float pr = 0.f, pi = 0.f;
+              if (valid && g.x >= 0) {
+                float2 a = P.rho[(size_t)g.x * P.np + p];
+                float2 b = P.rho[(size_t)g.y * P.np + p];
+                pr = (a.x * b.x + a.y * b.y) * P.sA;
+                pi = (a.y * b.x - a.x * b.y) * P.sA;
+              }
+              v[2 * i] = pr;
+              v[2 * i + 1] = pi;
+            }
+            uint4 hi, lo;
+            Pack<BF>::split(v, hi, lo);
+            st_shared_v4(sA_hi + mn_chunk(lane, c, A_SBO), hi);
+            st_shared_v4(sA_lo + mn_chunk(lane, c, A_SBO), lo);
+          } else {
+            const int cb = c - 16;
+            const float dfs = pw.z * P.sB;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              float2 w = wtab_s[4 * cb + i];
+              float x = (w.x + pw.x) + (w.y + pw.y);
+              float d = fmaf(x, x, P.eta * P.eta);
+              float sc = __fdividef(dfs, d);
+              v[2 * i] = sc * x;
+              v[2 * i + 1] = -sc * P.eta;
+            }
+            uint4 hi, lo;
+            Pack<BF>::split(v, hi, lo);
+            st_shared_v4(sB_hi + mn_chunk(lane, cb, B_SBO), hi);
+            st_shared_v4(sB_lo + mn_chunk(lane, cb, B_SBO), lo);
+          }
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[s]);
+      }
+    } else if (warp == WMMA) {
+      // ---------------- MMA issuer ----------------
+      for (long long per = 0; per < nper; ++per, ++pc) {
+        const uint32_t b = pc & 1;
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(&acc_empty[b], ((pc >> 1) & 1) ^ 1, &abort_s, P.status);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t d = tmem + b * TN;
+        const long long s0 = per * P.flush, s1 = min(nstage, s0 + P.flush);
+        for (long long st = s0; st < s1; ++st, ++it) {
+          const int s = it % NS;
+          if (lane == 0) ok = mbar_wait(&full[s], (it / NS) & 1, &abort_s, P.status);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) break;
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t aH = base + s * STAGE_BYTES, aL = aH + A_BYTES;
+            const uint32_t bH = aL + A_BYTES, bL = bH + B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < KS / 16; ++kk) {
+              const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
+              const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
+              const uint64_t dBh = sdesc(bH + kk * 2 * B_SBO, 1024, B_SBO);
+              const uint64_t dBl = sdesc(bL + kk * 2 * B_SBO, 1024, B_SBO);
+              mma(d, dAh, dBh, idesc, (st > s0 || kk > 0) ? 1u : 0u);
+              mma(d, dAh, dBl, idesc, 1u);
+              mma(d, dAl, dBh, idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+          }
+          __syncwarp();
+        }
+        if (!ok) break;
+        if (lane == 0) mma_commit(&acc_full[b]);
+        __syncwarp();
+      }
+    } else {
+      // ---------------- epilogue ----------------
+      const int q = warp & 3;            // tensor-memory lane quadrant of this warp
+      const int row = q * 32 + lane;
+      const long long grow = (long long)U.mt * TM + row;
+      for (long long per = 0; per < nper; ++per, ++pc) {
+        const uint32_t b = pc & 1;
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(&acc_full[b], (pc >> 1) & 1, &abort_s, P.status);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        tc_fence_after();
+#pragma unroll 1
+        for (int c = 0; c < TN / 32; ++c) {
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + b * TN + c * 32;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (grow < P.rows_valid) {
+            double* crow = P.C + grow * P.ldc + (long long)U.nt * TN + c * 32;
+            const int col0 = U.nt * TN + c * 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (col0 + j < P.cols_valid) atomicAdd(crow + j, (double)__uint_as_float(r[j]));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[b]);
+      }
+    }
+    // keep every role on the same unit; an abort stops all of them
+    __syncthreads();
+  }
+  // drain: wait (bounded) for this CTA's MMAs before freeing tensor memory
+  if (warp == WMMA) {
+    if (lane == 0) {
+      mma_commit(&final_bar);
+      unsigned long long t0 = gtime();
+      while (!mbar_try(&final_bar, 0)) {
+        if (gtime() - t0 > kTimeoutNs) {
+          atomicOr(P.status, 2);
+          break;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == WMMA)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN));
+  (void)unit_sync;
+  (void)base_gen;
+}
+
+// chi0[w][G][G'] from the FP64 sums
+__global__ void chi0_unpack(const double* __restrict__ C, int ldc, const int* __restrict__ rp_of,
+                            int nG, int nwi, double scale, double2* __restrict__ chi0) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long total = (long long)nwi * nG * nG;
+  if (t >= total) return;
+  int Gp = (int)(t % nG);
+  int G = (int)((t / nG) % nG);
+  int w = (int)(t / ((long long)nG * nG));
+  int rp = rp_of[G * nG + Gp];
+  const double* re = C + (long long)(2 * rp) * ldc + 2 * w;
+  const double* im = C + (long long)(2 * rp + 1) * ldc + 2 * w;
+  double RR = re[0], RI = re[1], IR = im[0], II = im[1];
+  double2 v;
+  if (G <= Gp)
+    v = make_double2(RR - II, RI + IR);
+  else
+    v = make_double2(RR + II, RI - IR);
+  chi0[t] = make_double2(scale * v.x, scale * v.y);
+}
+
+// {Delta_hi, Delta_lo, df, 0} per pair (Delta split so that w + Delta keeps FP64-level
+// accuracy when it cancels in FP32)
+__global__ void pair_weights_split(const double* __restrict__ eps, const double* __restrict__ occ,
+                                   const double* __restrict__ wgt, int nk, int nb,
+                                   float4* __restrict__ pw) {
+  long long np = (long long)nk * nb * nb;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    int m = (int)(p % nb);
+    long long kn = p / nb;
+    int k = (int)(kn / nb);
+    size_t ikq = (size_t)(nk + k) * nb + m;
+    double d = eps[kn] - eps[ikq];
+    float dh = (float)d;
+    pw[p] = make_float4(dh, (float)(d - (double)dh),
+                        (float)(wgt[kn] * wgt[ikq] * (occ[kn] - occ[ikq])), 0.f);
+  }
+}
+
+struct Plan {
+  int nG = -1, nwi = -1;
+  int n_m = 0, n_n = 0, rows_valid = 0;
+  int* rowtab = nullptr;
+  int* rp_of = nullptr;
+  float2* wtab = nullptr;
+};
+
+}  // namespace
 
 lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
-  (void)c; (void)q; (void)s;
-  set_error("split-precision chi0 not built yet");
-  return LRT_EUNSUPPORTED;
+  const int nG = q.nG;
+  // row pairs (G <= G') in 8 x 8 blocks so that a tile touches few G
+  std::vector<int2> pairs;
+  const int nblk = (nG + 7) / 8;
+  for (int I = 0; I < nblk; ++I)
+    for (int J = I; J < nblk; ++J)
+      for (int a = I * 8; a < std::min(nG, I * 8 + 8); ++a)
+        for (int b = J * 8; b < std::min(nG, J * 8 + 8); ++b)
+          if (I < J || a <= b) pairs.push_back(make_int2(a, b));
+  const int npairs = (int)pairs.size();
+  const int n_m = (npairs + 63) / 64;
+  std::vector<int2> rowtab((size_t)n_m * 64, make_int2(-1, -1));
+  std::vector<int> rp_of((size_t)nG * nG);
+  for (int i = 0; i < npairs; ++i) {
+    rowtab[i] = pairs[i];
+    rp_of[pairs[i].x * nG + pairs[i].y] = i;
+    rp_of[pairs[i].y * nG + pairs[i].x] = i;
+  }
+  const int ncols = 2 * c->nwi;
+  const int n_n = (ncols + TN - 1) / TN;
+  std::vector<float2> wtab((size_t)n_n * 128, make_float2(0.f, 0.f));
+  for (int j = 0; j < c->nwi; ++j) {
+    float h = (float)c->freqs[j];
+    wtab[j] = make_float2(h, (float)(c->freqs[j] - (double)h));
+  }
+  const bool bf = c->precision == LRT_PREC_BF16X3;
+  const float sA = bf ? 1.0f : 16384.0f;
+  float sB = 1.0f;
+  if (!bf) sB = std::ldexp(1.0f, (int)std::floor(std::log2(16384.0 * c->eta)));
+  const int ldc = n_n * TN;
+
+  int dev = 0, nsm = 0;
+  LRT_CUDA(cudaGetDevice(&dev));
+  LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const long long tiles = (long long)n_m * n_n;
+  // pair splits: at least 4 units per SM, chosen to fill the last round
+  long long best_split = 1;
+  double best_eff = 0.0;
+  const long long max_split = std::max<long long>(1, c->np / (KS * 64));
+  for (long long sp = std::max<long long>(1, (4LL * nsm + tiles - 1) / tiles); sp <= 8LL * nsm / std::max<long long>(1, tiles) + 8 && sp <= max_split; ++sp) {
+    long long units = tiles * sp;
+    double eff = (double)units / (double)(((units + nsm - 1) / nsm) * nsm);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best_split = sp;
+    }
+  }
+  long long kps = (c->np + best_split - 1) / best_split;
+  kps = (kps + KS - 1) / KS * KS;
+  const int n_split = (int)((c->np + kps - 1) / kps);
+
+  // device tables and buffers
+  size_t need = (size_t)n_m * TM * ldc * sizeof(double);
+  DeviceWork& dw = const_cast<DeviceWork&>(c->dw);
+  if (dw.scratch_bytes < need) {
+    cudaFree(dw.scratch);
+    dw.scratch = nullptr;
+    dw.scratch_bytes = 0;
+    LRT_CUDA(cudaMalloc(&dw.scratch, need));
+    dw.scratch_bytes = need;
+  }
+  int2* d_rowtab = nullptr;
+  int* d_rp = nullptr;
+  float2* d_wtab = nullptr;
+  float4* d_pw = nullptr;
+  LRT_CUDA(cudaMallocAsync(&d_rowtab, rowtab.size() * sizeof(int2), s));
+  LRT_CUDA(cudaMallocAsync(&d_rp, rp_of.size() * sizeof(int), s));
+  LRT_CUDA(cudaMallocAsync(&d_wtab, wtab.size() * sizeof(float2), s));
+  LRT_CUDA(cudaMallocAsync(&d_pw, (size_t)c->np * sizeof(float4), s));
+  LRT_CUDA(cudaMemcpyAsync(d_rowtab, rowtab.data(), rowtab.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  LRT_CUDA(cudaMemcpyAsync(d_rp, rp_of.data(), rp_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  LRT_CUDA(cudaMemcpyAsync(d_wtab, wtab.data(), wtab.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+  pair_weights_split<<<4 * nsm, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, d_pw);
+  LRT_CUDA(cudaGetLastError());
+  LRT_CUDA(cudaMemsetAsync(dw.scratch, 0, need, s));
+
+  Params P;
+  P.rho = (const float2*)dw.rho;
+  P.pw = d_pw;
+  P.rowtab = d_rowtab;
+  P.wtab = d_wtab;
+  P.C = dw.scratch;
+  P.status = dw.status;
+  P.np = c->np;
+  P.ldc = ldc;
+  P.rows_valid = 2 * npairs;
+  P.cols_valid = ncols;
+  P.n_m = n_m;
+  P.n_n = n_n;
+  P.n_split = n_split;
+  P.k_per_split = kps;
+  P.flush = 128;
+  P.eta = (float)c->eta;
+  P.sA = sA;
+  P.sB = sB;
+  const size_t smem = (size_t)NS * STAGE_BYTES + 1024;
+  long long units = tiles * n_split;
+  int grid = (int)std::min<long long>(nsm, units);
+  if (bf) {
+    LRT_CUDA(cudaFuncSetAttribute(chi0_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    chi0_tc_kernel<true><<<grid, NTHREADS, smem, s>>>(P);
+  } else {
+    LRT_CUDA(cudaFuncSetAttribute(chi0_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    chi0_tc_kernel<false><<<grid, NTHREADS, smem, s>>>(P);
+  }
+  LRT_CUDA(cudaGetLastError());
+  const double scale = 2.0 / (c->nk * c->volume) / ((double)sA * (double)sB);
+  long long total = (long long)c->nwi * nG * nG;
+  chi0_unpack<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dw.scratch, ldc, d_rp, nG, c->nwi, scale,
+                                                             q.chi0);
+  LRT_CUDA(cudaGetLastError());
+  LRT_CUDA(cudaFreeAsync(d_rowtab, s));
+  LRT_CUDA(cudaFreeAsync(d_rp, s));
+  LRT_CUDA(cudaFreeAsync(d_wtab, s));
+  LRT_CUDA(cudaFreeAsync(d_pw, s));
+  return LRT_OK;
 }
 
 }  // namespace lrt

@@ -15,6 +15,9 @@ constexpr double kHZero = 1e-4;        // Ha; frequency standing in for w -> 0 i
 constexpr double kBasisTol = 1e-9;     // |k+G|^2 <= 2 ecut + kBasisTol
 constexpr double kShellTol = 1e-9;     // |q+G|^2 (and |G|^2) closer than this: same shell
 constexpr double kPadDiag = 1.0e6;     // Ha; diagonal of the padding rows of H(k)
+constexpr double kDegenTol = 1e-6;     // Ha; eigenvalues this close to the last kept band
+                                       // form one multiplet (band weights)
+constexpr int kExtraBands = 8;         // eigenpairs kept beyond nbands to see such a multiplet
 
 // Thread-local message of the last failure.
 void set_error(const std::string& msg);
@@ -32,6 +35,9 @@ struct QData {
   double mu = 0.0;
   double* eps = nullptr;          // device [2][nk][nb]
   double* occ = nullptr;          // device [2][nk][nb]
+  double* wgt = nullptr;          // device [2][nk][nb] band weights (1, 0, or j/m on a split
+                                  // degenerate multiplet at the band cut)
+  std::vector<double> wgt_h;      // host copy
   double2* coeff = nullptr;       // device [2][nk][nb][npw]
   int32_t* gather = nullptr;      // device [nk][nG][npw]: index into the k+q basis or -1
   double2* chi0 = nullptr;        // device [nwi][nG][nG]
@@ -68,7 +74,8 @@ struct lrt_ctx {
   int kn[3] = {1, 1, 1};
   int kscheme = 0;
   int nk = 0;
-  int nb = 0;
+  int nbands = 0;                 // bands requested per k point
+  int nb = 0;                     // bands carried: nbands plus split-multiplet members
   double T = 0.0, eta = 0.0;
   int nq = 0;
   std::vector<double> q;          // [nq][3]
@@ -98,6 +105,7 @@ namespace lrt {
 lrt_status build_geometry(lrt_ctx* c, const int* nG);
 lrt_status solve_ground_states(lrt_ctx* c, const double* occupations);
 lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host);
+lrt_status reset_band_weights(lrt_ctx* c, int iq, const double* eps_host);
 double fxc_alda(double n);
 double fxc_model(double qg, double n, double A, double B, double C);
 

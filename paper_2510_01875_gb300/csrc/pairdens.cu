@@ -97,10 +97,10 @@ __global__ void __launch_bounds__(256) pair_density_kernel(
   }
 }
 
-// Delta_p = eps_nk - eps_n'k+q and df_p = f_nk - f_n'k+q.
+// Delta_p = eps_nk - eps_n'k+q and df_p = w_nk w_n'k+q (f_nk - f_n'k+q) (band weights w).
 __global__ void pair_weights_kernel(const double* __restrict__ eps, const double* __restrict__ occ,
-                                    int nk, int nb, double* __restrict__ delta,
-                                    double* __restrict__ df) {
+                                    const double* __restrict__ wgt, int nk, int nb,
+                                    double* __restrict__ delta, double* __restrict__ df) {
   int64_t np = (int64_t)nk * nb * nb;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -109,7 +109,7 @@ __global__ void pair_weights_kernel(const double* __restrict__ eps, const double
     int k = (int)(kn / nb);
     size_t ikq = (size_t)(nk + k) * nb + m;
     delta[p] = eps[kn] - eps[ikq];
-    df[p] = occ[kn] - occ[ikq];
+    df[p] = wgt[kn] * wgt[ikq] * (occ[kn] - occ[ikq]);
   }
 }
 
@@ -132,7 +132,7 @@ lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool
 }
 
 lrt_status launch_pair_weights(const lrt_ctx* c, const QData& q, cudaStream_t s) {
-  pair_weights_kernel<<<1216, 256, 0, s>>>(q.eps, q.occ, c->nk, c->nb, c->dw.delta, c->dw.df);
+  pair_weights_kernel<<<1216, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, c->dw.delta, c->dw.df);
   LRT_CUDA(cudaGetLastError());
   return LRT_OK;
 }

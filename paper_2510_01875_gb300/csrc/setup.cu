@@ -418,12 +418,36 @@ double fermi(double e, double mu, double T) {
 
 }  // namespace
 
-// mu by 200 halvings of [min eps - 60 T, max eps + 60 T] so that (2/N_k) sum f = N_e over
+// Band weights of one k point from its nfull ascending eigenvalues: 1 for the lowest nbands,
+// 0 above; a multiplet within kDegenTol of the last kept band that the cut splits (j of its
+// m members kept) gives each member j/m, which makes the kept projector gauge-invariant.
+// Returns the number of bands with nonzero weight, or -1 if the multiplet reaches the last
+// computed band.
+int band_weights(const double* e, int nfull, int nbands, double* w) {
+  for (int n = 0; n < nfull; ++n) w[n] = n < nbands ? 1.0 : 0.0;
+  const double last = e[nbands - 1];
+  int lo = nbands - 1, hi = nbands - 1;
+  for (int n = 0; n < nfull; ++n)
+    if (std::fabs(e[n] - last) <= kDegenTol) {
+      lo = std::min(lo, n);
+      hi = std::max(hi, n);
+    }
+  int m = hi - lo + 1, j = nbands - lo;
+  if (m == j) return nbands;
+  if (hi >= nfull - 1) return -1;
+  for (int n = lo; n <= hi; ++n) w[n] = (double)j / m;
+  return hi + 1;
+}
+
+// mu by 200 halvings of [min eps - 60 T, max eps + 60 T] so that (2/N_k) sum w f = N_e over
 // the k mesh of q; f on both meshes uploaded.
 lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host) {
   int nk = c->nk, nb = c->nb;
   size_t half = (size_t)nk * nb;
-  if (2.0 * nb < c->nelec) {
+  const double* wg = c->qd[iq].wgt_h.data();
+  double cap = 0.0;
+  for (size_t i = 0; i < half; ++i) cap += wg[i];
+  if (2.0 * cap / nk < c->nelec) {
     set_error("not enough bands to hold the electrons");
     return LRT_EINVAL;
   }
@@ -437,7 +461,7 @@ lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host) {
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
     double s = 0.0;
-    for (size_t i = 0; i < half; ++i) s += fermi(eps_host[i], mid, c->T);
+    for (size_t i = 0; i < half; ++i) s += wg[i] * fermi(eps_host[i], mid, c->T);
     if (2.0 * s / nk < c->nelec)
       lo = mid;
     else
@@ -453,7 +477,13 @@ lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host) {
 }
 
 lrt_status solve_ground_states(lrt_ctx* c, const double* occupations) {
-  int nk = c->nk, nb = c->nb, npw = c->npw;
+  int nk = c->nk, npw = c->npw;
+  // eigenpairs kept per k before the band weights are known: nbands plus room for a
+  // multiplet split by the cut
+  int npw_min = npw;
+  for (auto& Q : c->qd)
+    for (int v : Q.npw_k) npw_min = std::min(npw_min, v);
+  const int nb = std::min(npw_min, c->nbands + kExtraBands);
   size_t per_mat = (size_t)npw * npw * sizeof(double2);
   int total = 2 * nk * c->nq;
   // batch of matrices per eigensolver call (about 3 GB of matrices)
@@ -571,19 +601,89 @@ lrt_status solve_ground_states(lrt_ctx* c, const double* occupations) {
     }
   }
   LRT_CUDA(cudaDeviceSynchronize());
-  // occupations
-  std::vector<double> eps((size_t)2 * nk * nb);
+  // band weights and the number of bands carried (global over q)
+  std::vector<std::vector<double>> eps_all(c->nq), w_all(c->nq);
+  int nb_used = c->nbands;
   for (int iq = 0; iq < c->nq; ++iq) {
-    QData& Q = c->qd[iq];
-    if (occupations) {
-      Q.mu = NAN;
-      LRT_CUDA(cudaMemcpy(Q.occ, occupations + (size_t)iq * 2 * nk * nb, eps.size() * sizeof(double),
-                          cudaMemcpyHostToDevice));
-    } else {
-      LRT_CUDA(cudaMemcpy(eps.data(), Q.eps, eps.size() * sizeof(double), cudaMemcpyDeviceToHost));
-      LRT_TRY(set_occupations_fd(c, iq, eps.data()));
+    eps_all[iq].resize((size_t)2 * nk * nb);
+    w_all[iq].resize((size_t)2 * nk * nb);
+    LRT_CUDA(cudaMemcpy(eps_all[iq].data(), c->qd[iq].eps, eps_all[iq].size() * sizeof(double),
+                        cudaMemcpyDeviceToHost));
+    for (int s = 0; s < 2 * nk; ++s) {
+      double* w = &w_all[iq][(size_t)s * nb];
+      if (occupations) {
+        for (int n = 0; n < nb; ++n) w[n] = n < c->nbands ? 1.0 : 0.0;
+        continue;
+      }
+      int used = band_weights(&eps_all[iq][(size_t)s * nb], nb, c->nbands, w);
+      if (used < 0) {
+        set_error("a degenerate multiplet at the band cut extends past the computed bands");
+        return LRT_EINVAL;
+      }
+      nb_used = std::max(nb_used, used);
     }
   }
+  // compact every q to nb_used bands
+  c->nb = nb_used;
+  for (int iq = 0; iq < c->nq; ++iq) {
+    QData& Q = c->qd[iq];
+    if (nb_used < nb) {
+      double* e2 = nullptr;
+      double2* c2 = nullptr;
+      LRT_CUDA(cudaMalloc(&e2, (size_t)2 * nk * nb_used * sizeof(double)));
+      LRT_CUDA(cudaMalloc(&c2, (size_t)2 * nk * nb_used * npw * sizeof(double2)));
+      LRT_CUDA(cudaMemcpy2D(e2, nb_used * sizeof(double), Q.eps, nb * sizeof(double),
+                            nb_used * sizeof(double), 2 * nk, cudaMemcpyDeviceToDevice));
+      LRT_CUDA(cudaMemcpy2D(c2, (size_t)nb_used * npw * sizeof(double2), Q.coeff,
+                            (size_t)nb * npw * sizeof(double2), (size_t)nb_used * npw * sizeof(double2),
+                            2 * nk, cudaMemcpyDeviceToDevice));
+      cudaFree(Q.eps);
+      cudaFree(Q.coeff);
+      Q.eps = e2;
+      Q.coeff = c2;
+      cudaFree(Q.occ);
+      Q.occ = nullptr;
+      LRT_CUDA(cudaMalloc(&Q.occ, (size_t)2 * nk * nb_used * sizeof(double)));
+    }
+    Q.wgt_h.resize((size_t)2 * nk * nb_used);
+    std::vector<double> e((size_t)2 * nk * nb_used);
+    for (int s = 0; s < 2 * nk; ++s)
+      for (int n = 0; n < nb_used; ++n) {
+        Q.wgt_h[(size_t)s * nb_used + n] = w_all[iq][(size_t)s * nb + n];
+        e[(size_t)s * nb_used + n] = eps_all[iq][(size_t)s * nb + n];
+      }
+    LRT_CUDA(cudaMalloc(&Q.wgt, Q.wgt_h.size() * sizeof(double)));
+    LRT_CUDA(cudaMemcpy(Q.wgt, Q.wgt_h.data(), Q.wgt_h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (occupations) {
+      // caller's f for the nominal bands, zero above
+      Q.mu = NAN;
+      std::vector<double> f((size_t)2 * nk * nb_used, 0.0);
+      for (int s = 0; s < 2 * nk; ++s)
+        for (int n = 0; n < c->nbands; ++n)
+          f[(size_t)s * nb_used + n] = occupations[((size_t)iq * 2 * nk + s) * c->nbands + n];
+      LRT_CUDA(cudaMemcpy(Q.occ, f.data(), f.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+      LRT_TRY(set_occupations_fd(c, iq, e.data()));
+    }
+  }
+  c->np = (int64_t)nk * c->nb * c->nb;
+  return LRT_OK;
+}
+
+// Band weights recomputed from eigenvalues supplied through the orbital hook.
+lrt_status reset_band_weights(lrt_ctx* c, int iq, const double* eps_host) {
+  QData& Q = c->qd[iq];
+  int nb = c->nb;
+  std::vector<double> w(nb);
+  for (int s = 0; s < 2 * c->nk; ++s) {
+    int used = band_weights(eps_host + (size_t)s * nb, nb, c->nbands, w.data());
+    if (used < 0) {
+      set_error("a degenerate multiplet at the band cut extends past the supplied bands");
+      return LRT_EINVAL;
+    }
+    std::copy(w.begin(), w.end(), Q.wgt_h.begin() + (size_t)s * nb);
+  }
+  LRT_CUDA(cudaMemcpy(Q.wgt, Q.wgt_h.data(), Q.wgt_h.size() * sizeof(double), cudaMemcpyHostToDevice));
   return LRT_OK;
 }
 

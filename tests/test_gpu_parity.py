@@ -48,23 +48,22 @@ def compare(wl, g, tol=TOL, chi0_tol=None):
         r = pipeline.run_q(wl, iq, keep_chi0=True)
         assert np.allclose(g["freqs"], r["freqs"], rtol=0, atol=0)
         assert g["hcol"] == r["hcol"]
-        eps = g["gs"][iq][0]
-        assert np.abs(eps[0] - r_eps(wl, iq)).max() < 1e-10
+        eps, _, mu, wgt = g["gs"][iq]
+        ref_gs = response.ground_state(wl, iq)
+        nb = wl.nbands
+        assert np.abs(eps[0][:, :nb] - ref_gs["eps_k"][:, :nb]).max() < 1e-10
+        assert np.abs(eps[1][:, :nb] - ref_gs["eps_kq"][:, :nb]).max() < 1e-10
+        # band weights (split multiplets at the band cut) agree
+        nbr = ref_gs["nb"]
+        assert np.array_equal(wgt[0][:, :nbr], ref_gs["w_k"]) and not wgt[0][:, nbr:].any()
+        assert np.array_equal(wgt[1][:, :nbr], ref_gs["w_kq"]) and not wgt[1][:, nbr:].any()
         if not math.isnan(r["mu"]):
-            assert abs(g["gs"][iq][2] - r["mu"]) < 1e-10
+            assert abs(mu - r["mu"]) < 1e-10
         assert rel_max(g["chi0"][iq], r["chi0"]) < chi0_tol, "chi0"
         assert rel_max(g["chi"][iq][:, 0], r["chi00"]) < tol, "chi_00"
         assert rel_max(g["S"][iq], r["S"]) < tol, "S"
         assert np.abs(g["F"][iq] / r["F"] - 1).max() < tol, "F"
         assert np.abs(g["metrics"][iq] / r["metrics"] - 1).max() < tol, "metrics"
-
-
-_eps_cache = {}
-
-
-def r_eps(wl, iq):
-    gs = response.ground_state(wl, iq)
-    return gs["eps_k"]
 
 
 CASES = {

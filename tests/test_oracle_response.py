@@ -237,10 +237,10 @@ def test_bruteforce_chi0_realspace_route():
     for ik in range(wl.nk):
         rho = _rho_realspace(wl.lattice, gs["k"][ik], gs["basis_k"][ik], gs["C_k"][ik], gs["kq"][ik],
                              gs["basis_kq"][ik], gs["C_kq"][ik], r["gset"], nr)
-        for n in range(wl.nbands):
-            for m in range(wl.nbands):
+        for n in range(gs["nb"]):
+            for m in range(gs["nb"]):
                 d = gs["eps_k"][ik, n] - gs["eps_kq"][ik, m]
-                f = gs["f_k"][ik, n] - gs["f_kq"][ik, m]
+                f = (gs["f_k"][ik, n] - gs["f_kq"][ik, m]) * gs["w_k"][ik, n] * gs["w_kq"][ik, m]
                 for iw, w in enumerate(r["freqs"]):
                     wt = f / (w + d + 1j * wl.eta)
                     for a in range(len(r["gset"])):
@@ -248,3 +248,57 @@ def test_bruteforce_chi0_realspace_route():
                             ref[iw, a, b] += rho[n, m, a] * np.conj(rho[n, m, b]) * wt
     ref *= 2.0 / (wl.nk * om)
     assert np.abs(r["chi0"] - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def _split_multiplet_case():
+    """fcc primitive cell on a Gamma-centred mesh with a band cut that splits a degenerate
+    multiplet at some k points (high-symmetry points keep the Oh degeneracies)."""
+    lat = W.fcc_primitive(W.AL_A)
+    q = 0.5 * crystal.reciprocal(lat)[1]
+    base = W.tiny(natoms_displaced=False, kscheme="commensurate", kmesh=(2, 2, 2), ecut=2.5, nq=1,
+                  nG=5, nw=12, T_ev=4.0)
+    for nb in range(6, 16):
+        wl = base.replace(q=q[None], nbands=nb)
+        gs = response.ground_state(wl, 0)
+        if np.any((gs["w_k"] > 0) & (gs["w_k"] < 1)) or np.any((gs["w_kq"] > 0) & (gs["w_kq"] < 1)):
+            return wl, gs
+    raise RuntimeError("no split multiplet found")
+
+
+def test_band_weights_make_chi0_gauge_invariant():
+    """A random unitary rotation inside each multiplet split by the band cut leaves chi0
+    unchanged with the band weights, and changes it without them."""
+    wl, gs = _split_multiplet_case()
+    gset = crystal.response_gset(wl.lattice, wl.q[0], int(wl.nG[0]))
+    freqs, _ = response.internal_frequencies(wl.omega)
+    om = crystal.volume(wl.lattice)
+
+    def chi0_of(g):
+        rho = response.pair_densities(wl, g, gset).reshape(-1, len(gset))
+        d, df = response.pair_weights(g)
+        return response.chi0(rho, d, df, freqs, wl.eta, wl.nk, om)
+
+    ref = chi0_of(gs)
+    rng = np.random.default_rng(0)
+    rot = dict(gs)
+    for tag in ("k", "kq"):
+        Cs = []
+        for i, C in enumerate(gs["C_" + tag]):
+            w = gs["w_" + tag][i]
+            mem = np.where((w > 0) & (w < 1))[0]
+            C = C.copy()
+            if len(mem):
+                X = rng.normal(size=(len(mem), len(mem))) + 1j * rng.normal(size=(len(mem), len(mem)))
+                U, _ = np.linalg.qr(X)
+                C[:, mem] = C[:, mem] @ U
+            Cs.append(C)
+        rot["C_" + tag] = Cs
+    assert np.abs(chi0_of(rot) - ref).max() < 1e-12 * np.abs(ref).max()
+    # with a plain cut at nbands the same rotation is visible
+    plain, plain_rot = dict(gs), dict(rot)
+    for g in (plain, plain_rot):
+        for tag in ("k", "kq"):
+            w = np.zeros_like(gs["w_" + tag])
+            w[:, :wl.nbands] = 1.0
+            g["w_" + tag] = w
+    assert np.abs(chi0_of(plain_rot) - chi0_of(plain)).max() > 1e-6 * np.abs(ref).max()
