@@ -1,0 +1,462 @@
+#!/usr/bin/env python
+"""Benchmark of the LR-TDDFT response path on one GB300 (or N, one process per GPU).
+
+Workload: fcc Al, 1 atom, 12^3 k-mesh (time-reversal-symmetric, shifted by -q/2), 120 bands
+(16 Ha cut-off), T = 10 eV, 8 q with |q| in [0.5, 2.5] 1/A along x, 59 response G-vectors,
+1024 frequencies on [-40, 120] eV, eta = 0.5 eV, RPA + ALDA kernel.  A step is the whole
+response path for all 8 q: pair densities, the chi0 contraction (split precision FP16x3 by
+default), the FP64 Dyson solve, S(q,w), F(q,tau) on 64 tau in [0, beta/2] with its metrics,
+and the attenuation of narrow-band fluctuations.  The ground state (eigensolves) is set up
+once, outside the timed region.
+
+Reported value: chi0 complex MACs per second over the step, counting the full Adler-Wiser
+sum N_G^2 N_w N_p per q (N_p = N_k N_b^2), all ranks together.  Every operand is larger than
+the 129 MB L2 (pair densities: 11.8 GB per q), so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (tests' reference implementation) on a bounded
+sample of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+CONFIG_INDEX = 1
+METRIC = "chi0 complex MAC/s (split-precision chi0, FP64 Dyson/S/F, whole response path)"
+UNIT = "cMAC/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "bf16x3", "fp64"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-form slice, the accuracy check and the CPU baseline")
+    ap.add_argument("--nq", type=int, default=0, help="use the first nq q vectors (0 = all)")
+    return ap.parse_args()
+
+
+def workload(nq=0):
+    from paper_2510_01875_gb300 import workloads as W
+    wl = W.CONFIGS[CONFIG_INDEX]()
+    if nq:
+        wl = wl.replace(q=wl.q[:nq], nG=wl.nG[:nq])
+    return wl
+
+
+def cmac_per_q(ctx, wl):
+    return float(int(wl.nG[0]) ** 2) * wl.nw * float(ctx.nk) * ctx.nb * ctx.nb
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(pg, value):
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if pg.get_backend() == "nccl" else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, value):
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if pg.get_backend() == "nccl" else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ---------------------------------------------------------------- our implementation
+def run_ours(args, world, rank, local, pg):
+    import torch
+    from paper_2510_01875_gb300 import binding, build
+    build.build()
+    binding.load()
+    torch.cuda.set_device(local)
+    wl = workload(args.nq)
+    t0 = time.time()
+    ctx = binding.Context(wl, args.precision, device=local)
+    setup_s = time.time() - t0
+    dev = torch.device("cuda", local)
+    ntau = wl.ntau
+    tau = torch.linspace(0.0, 0.5 / wl.T, ntau, dtype=torch.float64, device=dev)
+    F = torch.zeros((wl.nq, ntau), dtype=torch.float64, device=dev)
+    M = torch.zeros((wl.nq, 5), dtype=torch.float64, device=dev)
+    S = torch.zeros((wl.nq, wl.nw), dtype=torch.float64, device=dev)
+    params = binding.atten_params()
+
+    def step():
+        # every call on the legacy default stream (0), which torch's events also use
+        ctx.chi0_assemble()
+        ctx.dyson_solve()
+        ctx.dsf_device(S.data_ptr())
+        ctx.itcf_device(ntau, tau.data_ptr(), F.data_ptr(), M.data_ptr())
+        ctx.attenuate(params)
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ctx.profile(True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(pg)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms_max = max_over_ranks(pg, ms)
+    cmac_step = cmac_per_q(ctx, wl) * wl.nq
+    value = sum_over_ranks(pg, cmac_step) / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the chi0 contraction)
+    peaks, src = measured_peaks()
+    if args.precision == "fp64":
+        bound, unit = "alu", "TFLOP/s"
+        flops_per_cmac = 4.0
+        peak = peaks.get("fp64_tflops", 1.25)
+        peak_note = "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+    else:
+        bound, unit = "tensor", "TFLOP/s"
+        flops_per_cmac = 12.0      # 2 real MACs per complex MAC (Hermitian split) x 3 products
+        peak = peaks["bf16_tflops_sustained"]
+        peak_note = f"bf16 dense sustained, {src} (fp16 runs at the bf16 rate)"
+    chi0_ms = prof["chi0_ms"] / max(prof["chi0_launches"], 1)
+    chi0_tflops = flops_per_cmac * prof["chi0_cmac"] / (prof["chi0_ms"] / 1e3) / 1e12
+    roofline = {"bound": bound, "achieved": chi0_tflops, "peak": peak, "unit": unit,
+                "frac": chi0_tflops / peak, "traffic": None,
+                "kernel": "chi0_tc_kernel" if args.precision != "fp64" else "chi0_fp64_kernel",
+                "launch_ms": chi0_ms, "peak_source": peak_note,
+                "pair_density_ms_per_launch": prof["rho_ms"] / max(prof["rho_launches"], 1),
+                "chi0_share_of_step": prof["chi0_ms"] / (ms * args.steps)}
+
+    # end to end through the C ABI with host buffers: per step the orbitals, eigenvalues and
+    # occupations of every q go host -> device, and S, F, the metrics and S_p come back
+    e2e = run_e2e(ctx, wl, args, cmac_step, pg, world)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(args, ctx, wl)
+    ctx.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16x3/f32-accumulate chi0, f64 elsewhere" if args.precision == "fp16x3"
+            else ("bf16x3/f32-accumulate chi0, f64 elsewhere" if args.precision == "bf16x3" else "f64"),
+            "data": "synthetic (seeded empty-core Al, no external data)",
+            "config": {"workload": wl.name, "precision": args.precision, "nq": wl.nq,
+                       "nk": ctx.nk, "nbands": ctx.nb, "nG": int(wl.nG[0]), "nw": wl.nw,
+                       "np_per_q": ctx.nk * ctx.nb * ctx.nb, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (pair densities 11.8 GB per q)"},
+            "q_spectra_per_s": sum_over_ranks(None, wl.nq * world) / (ms_max / 1e3),
+            "setup_s": setup_s,
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": prof["launches"],
+            "clocks": clk,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(ctx, wl, args, cmac_step, pg, world):
+    import torch
+    from paper_2510_01875_gb300 import binding
+    nk, nb, npw = ctx.nk, ctx.nb, ctx.npw
+    # pinned host copies of every q's inputs (taken once, outside the timed region)
+    coeff = [torch.empty((2, nk, nb, npw, 2), dtype=torch.float64).pin_memory() for _ in range(wl.nq)]
+    eps = [torch.empty((2, nk, nb), dtype=torch.float64).pin_memory() for _ in range(wl.nq)]
+    occ = [torch.empty((2, nk, nb), dtype=torch.float64).pin_memory() for _ in range(wl.nq)]
+    for iq in range(wl.nq):
+        ctx.get_orbitals(iq, coeff[iq].numpy().view(np.complex128).reshape(2, nk, nb, npw))
+        e, f, _, _ = ctx.get_ground_state(iq)
+        eps[iq].numpy()[:] = e
+        occ[iq].numpy()[:] = f
+    tau = np.linspace(0.0, 0.5 / wl.T, wl.ntau)
+    params = binding.atten_params()
+    h2d = sum(c.numel() * 8 + e.numel() * 8 + o.numel() * 8 for c, e, o in zip(coeff, eps, occ))
+    d2h = (wl.nq * wl.nw * 8) * 2 + wl.nq * wl.ntau * 8 + wl.nq * 5 * 8
+
+    def step():
+        for iq in range(wl.nq):
+            ctx.set_orbitals(iq, eps[iq].numpy(), coeff[iq].numpy().view(np.complex128), occ[iq].numpy())
+        ctx.chi0_assemble()
+        ctx.dyson_solve()
+        S = ctx.dsf()
+        F, m = ctx.itcf(tau)
+        Sp, _ = ctx.attenuate(params)
+        return S, F, m, Sp
+
+    step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    t0 = time.perf_counter()
+    n = max(1, min(args.steps, 2))
+    for _ in range(n):
+        step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    dt = (time.perf_counter() - t0) / n
+    dt = max_over_ranks(pg, dt)
+    return {"value": sum_over_ranks(pg, cmac_step) / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": n}
+
+
+def run_extras(args, ctx_main, wl):
+    """FP64 form on a slice (1 q, 16 frequencies) beside the split form, and the split form's
+    error against the FP64 form on the full 1-atom 8^3 workload."""
+    from paper_2510_01875_gb300 import binding
+    from paper_2510_01875_gb300 import workloads as W
+    out = {}
+    # slice: q[0], 16 frequencies around the plasmon
+    j0 = int(np.searchsorted(wl.omega, W.ev(15.0)))
+    sl = wl.replace(q=wl.q[:1], nG=wl.nG[:1], omega=wl.omega[j0:j0 + 16])
+    forms = {}
+    for prec in ("fp64", args.precision if args.precision != "fp64" else "fp16x3"):
+        c = binding.Context(sl, prec)
+        c.chi0_assemble()
+        c.profile(True)
+        c.chi0_assemble()
+        p = c.profile_read()
+        forms[prec] = {"chi0": c.get_chi0(0), "ms": p["chi0_ms"], "cmac": p["chi0_cmac"]}
+        c.close()
+    fp = forms["fp64"]
+    sp = forms[[k for k in forms if k != "fp64"][0]]
+    err = float(np.abs(sp["chi0"] - fp["chi0"]).max() / np.abs(fp["chi0"]).max())
+    out["fp64_form"] = {"value": fp["cmac"] / (fp["ms"] / 1e3), "unit": UNIT,
+                        "chi0_tflops": 4.0 * fp["cmac"] / (fp["ms"] / 1e3) / 1e12,
+                        "sample": "1 q, 16 frequencies (15-17.5 eV), all 2.49e7 pairs; rate is "
+                                  "K-dominated so it extrapolates linearly to the full workload",
+                        "split_rate_same_slice": sp["cmac"] / (sp["ms"] / 1e3),
+                        "split_vs_fp64_chi0_err": err}
+    # accuracy of the split form against FP64 on the 1-atom 8^3 workload (full S and F)
+    c0 = W.config0()
+    res = {}
+    for prec in ("fp64", args.precision if args.precision != "fp64" else "fp16x3"):
+        c = binding.Context(c0, prec)
+        c.chi0_assemble()
+        c.dyson_solve()
+        S = c.dsf()
+        F, m = c.itcf(np.linspace(0.0, 0.5 / c0.T, c0.ntau))
+        res[prec] = (c.get_chi0(0), S, F)
+        c.close()
+    a = res["fp64"]
+    b = res[[k for k in res if k != "fp64"][0]]
+    peaks = [j for j in range(1, c0.nw - 1) if a[1][0, j] > a[1][0, j - 1] and a[1][0, j] >= a[1][0, j + 1]
+             and a[1][0, j] > 0.1 * a[1][0].max()]
+    out["split_accuracy"] = {
+        "workload": c0.name,
+        "chi0_maxnorm_rel": float(np.abs(b[0] - a[0]).max() / np.abs(a[0]).max()),
+        "S_maxnorm_rel": float(np.abs(b[1] - a[1]).max() / np.abs(a[1]).max()),
+        "S_peak_rel": float(max(abs(b[1][0, j] / a[1][0, j] - 1) for j in peaks)) if peaks else None,
+        "F_pointwise_rel": float(np.abs(b[2] / a[2] - 1).max()),
+        "bounds": {"F": 1e-5, "S_peaks": 1e-4}}
+    out["cpu_baseline"] = cpu_baseline(wl)
+    return out
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(wl, seconds=15.0):
+    """The FP64 oracle on a bounded sample of the workload: q[0], the first k point of the mesh
+    (all N_b^2 = 14400 band pairs), N_G = 59, as many of the 1025 internal frequencies as fit in
+    about `seconds`: pair densities, chi0, Dyson, S.  The eigensolves of the sample are not
+    timed (the GPU's setup is not timed either).  Returns (cMAC/s, description)."""
+    from oracle import crystal, occupations, response
+    q = wl.q[0]
+    gset = crystal.response_gset(wl.lattice, q, int(wl.nG[0]))
+    kp, kqp = crystal.pair_meshes(wl.lattice, wl.kmesh, q, wl.kscheme)
+    ek, Ck, bk = [], [], []
+    for kv in (kp[0], kqp[0]):
+        b = response.basis_for(wl, kv)
+        e, C = crystal.eigenstates(wl.lattice, wl.positions, wl.Z, wl.r_c, kv, b, wl.nbands)
+        ek.append(e)
+        Ck.append(C)
+        bk.append(b)
+    mu = occupations.chemical_potential(ek[0][None, :], wl.T, wl.Z * wl.natoms, 1)
+    f0, f1 = occupations.fermi(ek[0], mu, wl.T), occupations.fermi(ek[1], mu, wl.T)
+    freqs, _ = response.internal_frequencies(wl.omega)
+    om = crystal.volume(wl.lattice)
+    K = response.kernel_diag(wl, q, gset)
+    t0 = time.perf_counter()
+    rho = response.pair_density(Ck[0], bk[0], Ck[1], bk[1], gset).reshape(-1, len(gset))
+    d = (ek[0][:, None] - ek[1][None, :]).reshape(-1)
+    df = (f0[:, None] - f1[None, :]).reshape(-1)
+    t_rho = time.perf_counter() - t0
+    # probe the per-frequency cost, then size the sample
+    t0 = time.perf_counter()
+    response.chi0(rho, d, df, freqs[:4], wl.eta, 1, om)
+    per_w = (time.perf_counter() - t0) / 4
+    nw = int(max(4, min(len(freqs), seconds / max(per_w, 1e-6))))
+    t0 = time.perf_counter()
+    c0 = response.chi0(rho, d, df, freqs[:nw], wl.eta, 1, om)
+    x = response.dyson_column0(c0, K)
+    S = -x[:, 0].imag
+    dt = time.perf_counter() - t0 + t_rho
+    cmac = float(len(gset)) ** 2 * nw * len(d)
+    desc = (f"{wl.name}: q[0], 1 of {wl.nk} k points ({len(d)} pairs), {len(gset)} G, {nw} of "
+            f"{len(freqs)} frequencies; pair densities + chi0 + Dyson + S, FP64 numpy")
+    return cmac / dt, desc, dt
+
+
+def blas_threads():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(wl):
+    v, desc, dt = oracle_sample(wl)
+    return {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc,
+            "seconds": dt}
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    wl = workload(args.nq)
+    for _ in range(args.warmup):
+        oracle_sample(wl, seconds=2.0)
+    vals, times, desc = [], [], ""
+    for _ in range(args.steps):
+        v, desc, dt = oracle_sample(wl, seconds=10.0)
+        vals.append(v)
+        times.append(dt)
+    value = float(np.mean(vals))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded empty-core Al, no external data)",
+            "config": {"workload": wl.name, "precision": "fp64 (CPU oracle)"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -200,6 +200,19 @@ typedef struct {
 lrt_status lrtddft_attenuate(lrt_ctx* ctx, const lrt_atten_params* params, double* Sp,
                              lrt_atten_report* report);
 
+/* ---- instrumentation ---- */
+
+/* Reset the counters below and turn the CUDA-event timing of the chi0 contraction and
+ * pair-density kernel launches on (enable = 1) or off (0).  Events are recorded on the stream
+ * each launch is enqueued on. */
+lrt_status lrtddft_profile(lrt_ctx* ctx, int enable);
+/* Synchronises the device and reads the counters since the last lrtddft_profile call:
+ * out[0] kernels launched by the library, out[1] chi0 contraction launches timed,
+ * out[2] their total device time in ms, out[3] pair-density launches timed, out[4] their
+ * total ms, out[5] chi0 complex MACs of the timed contractions (N_G^2 N_w N_p summed, with
+ * the caller's N_w), out[6..7] reserved (0). */
+lrt_status lrtddft_profile_read(lrt_ctx* ctx, double out[8]);
+
 /* ---- test and debug hooks ---- */
 
 /* Replace the orbitals of q index iq: eps [2][nk][nb] ascending per k point (k mesh then k+q
@@ -209,6 +222,9 @@ lrt_status lrtddft_attenuate(lrt_ctx* ctx, const lrt_atten_params* params, doubl
  * Host pointers. */
 lrt_status lrtddft_set_orbitals(lrt_ctx* ctx, int iq, const double* eps, const double* coeff,
                                 const double* occ);
+/* Orbital coefficients of q index iq: coeff [2][nk][nb][npw] complex (the layout
+ * lrtddft_set_orbitals takes). */
+lrt_status lrtddft_get_orbitals(const lrt_ctx* ctx, int iq, double* coeff);
 /* Miller indices of the padded basis of q index iq: miller [2][nk][npw][3] (int32; padding
  * rows hold INT32_MIN), npw_k [2][nk]. */
 lrt_status lrtddft_get_basis(const lrt_ctx* ctx, int iq, int32_t* miller, int32_t* npw_k);

@@ -87,7 +87,10 @@ SIGNATURES = {
     "lrtddft_itcf_laplace": (C.c_int, [_P, C.c_int, _D, C.c_int, _D, _D]),
     "lrtddft_itcf_laplace_device": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
     "lrtddft_attenuate": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D, C.POINTER(lrt_atten_report)]),
+    "lrtddft_profile": (C.c_int, [_P, C.c_int]),
+    "lrtddft_profile_read": (C.c_int, [_P, _D]),
     "lrtddft_set_orbitals": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "lrtddft_get_orbitals": (C.c_int, [_P, C.c_int, _D]),
     "lrtddft_get_basis": (C.c_int, [_P, C.c_int, _I32, _I32]),
     "lrtddft_get_ground_state": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
     "lrtddft_get_gset": (C.c_int, [_P, C.c_int, _I32, _D]),
@@ -219,6 +222,16 @@ class Context:
         _check("lrtddft_attenuate", self.lib.lrtddft_attenuate(self.h, C.byref(p), _dp(Sp), rep))
         return Sp, [report_dict(r) for r in rep]
 
+    # --- instrumentation ---
+    def profile(self, enable: bool = True):
+        _check("lrtddft_profile", self.lib.lrtddft_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        out = np.zeros(8)
+        _check("lrtddft_profile_read", self.lib.lrtddft_profile_read(self.h, _dp(out)))
+        return {"launches": int(out[0]), "chi0_launches": int(out[1]), "chi0_ms": float(out[2]),
+                "rho_launches": int(out[3]), "rho_ms": float(out[4]), "chi0_cmac": float(out[5])}
+
     # --- hooks ---
     def set_orbitals(self, iq: int, eps: np.ndarray, coeff: np.ndarray, occ: Optional[np.ndarray] = None):
         eps = np.ascontiguousarray(eps, dtype=np.float64)
@@ -226,6 +239,12 @@ class Context:
         oc = None if occ is None else np.ascontiguousarray(occ, dtype=np.float64)
         _check("lrtddft_set_orbitals", self.lib.lrtddft_set_orbitals(
             self.h, iq, _dp(eps), cf.ctypes.data_as(_D), None if oc is None else _dp(oc)))
+
+    def get_orbitals(self, iq: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+        if out is None:
+            out = np.zeros((2, self.nk, self.nb, self.npw), dtype=np.complex128)
+        _check("lrtddft_get_orbitals", self.lib.lrtddft_get_orbitals(self.h, iq, out.ctypes.data_as(_D)))
+        return out
 
     def get_basis(self, iq: int):
         m = np.zeros((2, self.nk, self.npw, 3), dtype=np.int32)

@@ -21,8 +21,20 @@ lrt_status bad(const char* msg) {
   return LRT_EINVAL;
 }
 
+void free_events(lrt_ctx* c) {
+  for (auto& e : c->ev_chi0) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  for (auto& e : c->ev_rho) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+}
+
 void free_ctx(lrt_ctx* c) {
   if (!c) return;
+  if (!c->host_only) free_events(c);
   if (c->host_only) {
     delete c;
     return;
@@ -245,7 +257,7 @@ extern "C" lrt_status lrtddft_chi0_assemble(lrt_ctx* c, int q_begin, int q_end, 
   for (int iq = q_begin; iq < q_end; ++iq) {
     QData& Q = c->qd[iq];
     if (!Q.chi0) LRT_CUDA(cudaMalloc(&Q.chi0, (size_t)c->nwi * Q.nG * Q.nG * sizeof(double2)));
-    LRT_TRY(launch_pair_weights(c, Q, s));
+    if (c->precision == LRT_PREC_FP64) LRT_TRY(launch_pair_weights(c, Q, s));
     LRT_TRY(launch_pair_density(c, Q, c->dw.rho, c->precision != LRT_PREC_FP64, s));
     if (c->precision == LRT_PREC_FP64)
       LRT_TRY(launch_chi0_fp64(c, Q, s));
@@ -298,6 +310,8 @@ extern "C" lrt_status lrtddft_dsf_device(lrt_ctx* c, double* S_dev, void* stream
 extern "C" lrt_status lrtddft_dsf(lrt_ctx* c, double* S) {
   if (!c || !S) return bad("NULL argument");
   LRT_TRY(need_all_chi(c));
+  // host-buffer calls run on the legacy stream after all earlier work on any stream
+  LRT_CUDA(cudaDeviceSynchronize());
   LRT_TRY(launch_dsf(c, c->dw.S, 0));
   LRT_CUDA(cudaMemcpy(S, c->dw.S, (size_t)c->nq * c->nw * sizeof(double), cudaMemcpyDeviceToHost));
   LRT_TRY(check_status_word(c));
@@ -338,7 +352,8 @@ extern "C" lrt_status lrtddft_itcf_laplace(lrt_ctx* c, int ntau, const double* t
     set_error("device allocation");
     return done(LRT_ENOMEM);
   }
-  if (cudaMemcpy(dtau, tau, ntau * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+  if (cudaMemcpy(dtau, tau, ntau * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
     return done(LRT_ECUDA);
   lrt_status st = lrtddft_itcf_laplace_device(c, ntau, dtau, mode, dF, dm, 0);
   if (st != LRT_OK) return done(st);
@@ -354,6 +369,7 @@ extern "C" lrt_status lrtddft_attenuate(lrt_ctx* c, const lrt_atten_params* p, d
                                         lrt_atten_report* rep) {
   if (!c || !Sp) return bad("NULL argument");
   LRT_TRY(need_all_chi(c));
+  LRT_CUDA(cudaDeviceSynchronize());
   LRT_TRY(launch_dsf(c, c->dw.S, 0));
   LRT_TRY(run_attenuation(c, p, c->dw.S, Sp, rep, 0));
   return check_status_word(c);
@@ -442,5 +458,64 @@ extern "C" lrt_status lrtddft_get_frequencies(const lrt_ctx* c, double* freqs, i
   if (!c) return bad("NULL context");
   if (freqs) std::copy(c->freqs.begin(), c->freqs.end(), freqs);
   if (hcol) *hcol = c->hcol;
+  return LRT_OK;
+}
+
+static void drop_events(const lrt_ctx* c) {
+  for (auto& e : c->ev_chi0) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  for (auto& e : c->ev_rho) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  c->ev_chi0.clear();
+  c->ev_rho.clear();
+}
+
+extern "C" lrt_status lrtddft_profile(lrt_ctx* c, int enable) {
+  if (!c) return bad("NULL context");
+  LRT_TRY(need_device(c));
+  LRT_CUDA(cudaDeviceSynchronize());
+  drop_events(c);
+  c->launches = 0;
+  c->timed_cmac = 0.0;
+  c->profiling = enable != 0;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_profile_read(lrt_ctx* c, double out[8]) {
+  if (!c || !out) return bad("NULL argument");
+  LRT_TRY(need_device(c));
+  LRT_CUDA(cudaDeviceSynchronize());
+  double t_chi0 = 0.0, t_rho = 0.0;
+  for (auto& e : c->ev_chi0) {
+    float ms = 0.f;
+    LRT_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+    t_chi0 += ms;
+  }
+  for (auto& e : c->ev_rho) {
+    float ms = 0.f;
+    LRT_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+    t_rho += ms;
+  }
+  out[0] = (double)c->launches;
+  out[1] = (double)c->ev_chi0.size();
+  out[2] = t_chi0;
+  out[3] = (double)c->ev_rho.size();
+  out[4] = t_rho;
+  out[5] = c->timed_cmac;
+  out[6] = out[7] = 0.0;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_orbitals(const lrt_ctx* c, int iq, double* coeff) {
+  if (!c || !coeff) return bad("NULL argument");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  LRT_TRY(need_device(c));
+  const QData& Q = c->qd[iq];
+  LRT_CUDA(cudaMemcpy(coeff, Q.coeff, (size_t)2 * c->nk * c->nb * c->npw * sizeof(double2),
+                      cudaMemcpyDeviceToHost));
   return LRT_OK;
 }

@@ -589,6 +589,7 @@ lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const 
   LRT_CUDA(cudaGetLastError());
   att_select<<<nq, 256, 0, s>>>(S_dev, (const double2*)c->dw.chi00, c->dw.omega, cfg, dc, yf, co, fnw,
                                 spd, dout, nacc);
+  count_launch(c, 3);
   LRT_CUDA(cudaGetLastError());
   LRT_CUDA(cudaMemcpyAsync(Sp_host, spd, (size_t)nq * c->nw * sizeof(double), cudaMemcpyDeviceToHost, s));
   std::vector<AttQ> hq(nq);

@@ -115,9 +115,14 @@ lrt_status launch_chi0_fp64(const lrt_ctx* c, QData& q, cudaStream_t s) {
   LRT_CUDA(cudaMemsetAsync(q.chi0, 0, (size_t)c->nwi * q.nG * q.nG * sizeof(double2), s));
   dim3 grid(npairs, nwt, (unsigned)split);
   double pref = 2.0 / (c->nk * c->volume);
-  chi0_fp64_kernel<<<grid, 256, 0, s>>>((const double2*)c->dw.rho, c->dw.delta, c->dw.df,
-                                        c->dw.freqs, c->nwi, q.nG, c->np, c->eta, pref, nblk, per,
-                                        q.chi0);
+  {
+    TimedLaunch tl(c, &c->ev_chi0, s);
+    chi0_fp64_kernel<<<grid, 256, 0, s>>>((const double2*)c->dw.rho, c->dw.delta, c->dw.df,
+                                          c->dw.freqs, c->nwi, q.nG, c->np, c->eta, pref, nblk, per,
+                                          q.chi0);
+  }
+  count_launch(c);
+  if (c->profiling) c->timed_cmac += (double)q.nG * q.nG * c->nw * (double)c->np;
   LRT_CUDA(cudaGetLastError());
   return LRT_OK;
 }

@@ -560,18 +560,25 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   const size_t smem = (size_t)NS * STAGE_BYTES + 1024;
   long long units = tiles * n_split;
   int grid = (int)std::min<long long>(nsm, units);
-  if (bf) {
+  if (bf)
     LRT_CUDA(cudaFuncSetAttribute(chi0_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    chi0_tc_kernel<true><<<grid, NTHREADS, smem, s>>>(P);
-  } else {
+  else
     LRT_CUDA(cudaFuncSetAttribute(chi0_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    chi0_tc_kernel<false><<<grid, NTHREADS, smem, s>>>(P);
+  {
+    TimedLaunch tl(c, &c->ev_chi0, s);
+    if (bf)
+      chi0_tc_kernel<true><<<grid, NTHREADS, smem, s>>>(P);
+    else
+      chi0_tc_kernel<false><<<grid, NTHREADS, smem, s>>>(P);
   }
+  count_launch(c, 2);   // pair_weights_split + the contraction
+  if (c->profiling) c->timed_cmac += (double)nG * nG * c->nw * (double)c->np;
   LRT_CUDA(cudaGetLastError());
   const double scale = 2.0 / (c->nk * c->volume) / ((double)sA * (double)sB);
   long long total = (long long)c->nwi * nG * nG;
   chi0_unpack<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dw.scratch, ldc, d_rp, nG, c->nwi, scale,
                                                              q.chi0);
+  count_launch(c);
   LRT_CUDA(cudaGetLastError());
   LRT_CUDA(cudaFreeAsync(d_rowtab, s));
   LRT_CUDA(cudaFreeAsync(d_rp, s));

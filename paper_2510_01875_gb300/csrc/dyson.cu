@@ -132,6 +132,7 @@ lrt_status launch_dyson(const lrt_ctx* c, QData& q, int iq, cudaStream_t s) {
   LRT_CUDA(cudaFuncSetAttribute(dyson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   dyson_kernel<<<c->nwi, 256, smem, s>>>(q.chi0, q.Kdev, N, q.chi, c->dw.status);
+  count_launch(c);
   LRT_CUDA(cudaGetLastError());
   return LRT_OK;
 }

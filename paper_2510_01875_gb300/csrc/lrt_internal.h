@@ -97,7 +97,46 @@ struct lrt_ctx {
   lrt::DeviceWork dw;
   bool have_S = false;
   bool host_only = false;
+  // instrumentation (lrtddft_profile): launch counter and event pairs around the chi0
+  // contraction and pair-density launches
+  mutable long long launches = 0;
+  bool profiling = false;
+  mutable std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_chi0, ev_rho;
+  mutable double timed_cmac = 0.0;
 };
+
+namespace lrt {
+// Count kernel launches for lrtddft_profile_read.
+inline void count_launch(const lrt_ctx* c, int n = 1) { c->launches += n; }
+inline cudaEvent_t new_event();
+// With profiling on, record an event pair around one launch: begin() before, end() after.
+struct TimedLaunch {
+  const lrt_ctx* c;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* list;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  TimedLaunch(const lrt_ctx* ctx, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* l,
+              cudaStream_t st)
+      : c(ctx), list(l), s(st) {
+    if (c->profiling) {
+      a = new_event();
+      cudaEventRecord(a, s);
+    }
+  }
+  ~TimedLaunch() {
+    if (c->profiling) {
+      cudaEvent_t b = new_event();
+      cudaEventRecord(b, s);
+      list->emplace_back(a, b);
+    }
+  }
+};
+inline cudaEvent_t new_event() {
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace lrt
 
 namespace lrt {
 

@@ -121,18 +121,23 @@ lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool
   dim3 grid(ntile * ntile, q.nG, c->nk);
   const double2* ck = q.coeff;
   const double2* ckq = q.coeff + (size_t)c->nk * c->nb * c->npw;
-  if (fp32)
-    pair_density_kernel<float><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw, q.nG,
-                                                    ntile, (float2*)rho);
-  else
-    pair_density_kernel<double><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw, q.nG,
-                                                     ntile, (double2*)rho);
+  {
+    TimedLaunch tl(c, &c->ev_rho, s);
+    if (fp32)
+      pair_density_kernel<float><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw, q.nG,
+                                                      ntile, (float2*)rho);
+    else
+      pair_density_kernel<double><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw,
+                                                       q.nG, ntile, (double2*)rho);
+  }
+  count_launch(c);
   LRT_CUDA(cudaGetLastError());
   return LRT_OK;
 }
 
 lrt_status launch_pair_weights(const lrt_ctx* c, const QData& q, cudaStream_t s) {
   pair_weights_kernel<<<1216, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, c->dw.delta, c->dw.df);
+  count_launch(c);
   LRT_CUDA(cudaGetLastError());
   return LRT_OK;
 }

@@ -177,6 +177,7 @@ lrt_status launch_dsf(const lrt_ctx* c, double* S_dev, cudaStream_t s) {
   int total = c->nq * c->nw;
   dsf_kernel<<<(total + 255) / 256, 256, 0, s>>>((const double2*)c->dw.chi00, c->dw.omega, c->nq,
                                                  c->nw, c->nwi, c->hcol, c->T, c->density, S_dev);
+  count_launch(c, c->nq + 1);
   LRT_CUDA(cudaGetLastError());
   return LRT_OK;
 }
@@ -197,6 +198,7 @@ lrt_status launch_itcf(const lrt_ctx* c, const double* S_dev, int ntau, const do
   else
     itcf_direct_kernel<<<blocks, 256, 0, s>>>(S_dev, c->dw.omega, tau_dev, c->nq, c->nw, ntau,
                                               F_dev);
+  count_launch(c, metrics_dev ? 2 : 1);
   LRT_CUDA(cudaGetLastError());
   if (metrics_dev) {
     int mb = (c->nq * 32 + 255) / 256;
