@@ -194,7 +194,7 @@ def run_ours(args, world, rank, local, pg):
         ctx.itcf_device(ntau, tau.data_ptr(), F.data_ptr(), M.data_ptr())
         ctx.attenuate(params)
 
-    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+    for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     clocks = Clocks(local)
@@ -239,13 +239,24 @@ def run_ours(args, world, rank, local, pg):
                 "pair_density_ms_per_launch": prof["rho_ms"] / max(prof["rho_launches"], 1),
                 "chi0_share_of_step": prof["chi0_ms"] / (ms * args.steps)}
 
+    print(json.dumps({"progress": "device-timed", "ms_per_step": ms_max, "value": value,
+                      "roofline": roofline, "launches": prof["launches"], "clocks": clk,
+                      "setup_s": setup_s}), file=sys.stderr, flush=True)
+
     # end to end through the C ABI with host buffers: per step the orbitals, eigenvalues and
     # occupations of every q go host -> device, and S, F, the metrics and S_p come back
-    e2e = run_e2e(ctx, wl, args, cmac_step, pg, world)
+    try:
+        e2e = run_e2e(ctx, wl, args, cmac_step, pg, world)
+    except Exception as exc:  # reported, not hidden: the line carries the failure
+        e2e = {"value": None, "unit": UNIT, "error": repr(exc)}
+    print(json.dumps({"progress": "e2e", "e2e": e2e}), file=sys.stderr, flush=True)
 
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = run_extras(args, ctx, wl)
+        try:
+            extras = run_extras(args, ctx, wl)
+        except Exception as exc:
+            extras = {"extras_error": repr(exc)}
     ctx.close()
 
     if rank == 0:

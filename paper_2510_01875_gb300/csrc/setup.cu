@@ -422,8 +422,8 @@ double fermi(double e, double mu, double T) {
 // 0 above; a multiplet within kDegenTol of the last kept band that the cut splits (j of its
 // m members kept) gives each member j/m, which makes the kept projector gauge-invariant.
 // Returns the number of bands with nonzero weight, or -1 if the multiplet reaches the last
-// computed band.
-int band_weights(const double* e, int nfull, int nbands, double* w) {
+// computed band (so that members above it could be missing) and `complete` is false.
+int band_weights(const double* e, int nfull, int nbands, double* w, bool complete = false) {
   for (int n = 0; n < nfull; ++n) w[n] = n < nbands ? 1.0 : 0.0;
   const double last = e[nbands - 1];
   int lo = nbands - 1, hi = nbands - 1;
@@ -434,7 +434,7 @@ int band_weights(const double* e, int nfull, int nbands, double* w) {
     }
   int m = hi - lo + 1, j = nbands - lo;
   if (m == j) return nbands;
-  if (hi >= nfull - 1) return -1;
+  if (hi >= nfull - 1 && !complete) return -1;
   for (int n = lo; n <= hi; ++n) w[n] = (double)j / m;
   return hi + 1;
 }
@@ -676,7 +676,8 @@ lrt_status reset_band_weights(lrt_ctx* c, int iq, const double* eps_host) {
   int nb = c->nb;
   std::vector<double> w(nb);
   for (int s = 0; s < 2 * c->nk; ++s) {
-    int used = band_weights(eps_host + (size_t)s * nb, nb, c->nbands, w.data());
+    // the context's nb already holds every member of a multiplet split at setup
+    int used = band_weights(eps_host + (size_t)s * nb, nb, c->nbands, w.data(), true);
     if (used < 0) {
       set_error("a degenerate multiplet at the band cut extends past the supplied bands");
       return LRT_EINVAL;
