@@ -47,14 +47,19 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-form slice, the accuracy check and the CPU baseline")
     ap.add_argument("--nq", type=int, default=0, help="use the first nq q vectors (0 = all)")
+    ap.add_argument("--kmesh", type=int, default=0,
+                    help="k mesh n^3 instead of 12^3 (small cases for profiler captures)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     return ap.parse_args()
 
 
-def workload(nq=0):
+def workload(nq=0, kmesh=0):
     from paper_2510_01875_gb300 import workloads as W
     wl = W.CONFIGS[CONFIG_INDEX]()
     if nq:
         wl = wl.replace(q=wl.q[:nq], nG=wl.nG[:nq])
+    if kmesh:
+        wl = wl.replace(kmesh=(kmesh, kmesh, kmesh), name=wl.name.replace("k12", f"k{kmesh}"))
     return wl
 
 
@@ -174,7 +179,7 @@ def run_ours(args, world, rank, local, pg):
     build.build()
     binding.load()
     torch.cuda.set_device(local)
-    wl = workload(args.nq)
+    wl = workload(args.nq, args.kmesh)
     t0 = time.time()
     ctx = binding.Context(wl, args.precision, device=local)
     setup_s = time.time() - t0
@@ -246,7 +251,8 @@ def run_ours(args, world, rank, local, pg):
     # end to end through the C ABI with host buffers: per step the orbitals, eigenvalues and
     # occupations of every q go host -> device, and S, F, the metrics and S_p come back
     try:
-        e2e = run_e2e(ctx, wl, args, cmac_step, pg, world)
+        e2e = (run_e2e(ctx, wl, args, cmac_step, pg, world) if not args.no_e2e
+               else {"value": None, "unit": UNIT, "skipped": "--no-e2e"})
     except Exception as exc:  # reported, not hidden: the line carries the failure
         e2e = {"value": None, "unit": UNIT, "error": repr(exc)}
     print(json.dumps({"progress": "e2e", "e2e": e2e}), file=sys.stderr, flush=True)
@@ -437,7 +443,7 @@ def cpu_baseline(wl):
 def run_reference(args, world, rank, pg):
     if rank != 0:
         return
-    wl = workload(args.nq)
+    wl = workload(args.nq, args.kmesh)
     for _ in range(args.warmup):
         oracle_sample(wl, seconds=2.0)
     vals, times, desc = [], [], ""
