@@ -53,9 +53,10 @@ def test_split_against_oracle(name, prec):
         assert np.abs(F[iq] / r["F"] - 1).max() <= b["F"]
         for j in _peaks(r["S"]):
             assert abs(S[iq][j] / r["S"][j] - 1) <= b["S"]
-            # the peak stays within one grid step
-            lo, hi = max(0, j - 2), min(wl.nw, j + 3)
-            assert abs(int(np.argmax(S[iq][lo:hi])) + lo - j) <= 1
+            # the peak stays a local maximum within one grid step
+            s = S[iq]
+            assert any(s[i] >= s[i - 1] and s[i] >= s[i + 1]
+                       for i in range(max(1, j - 1), min(wl.nw - 1, j + 2)))
 
 
 def test_split_repeatable_and_status_clean():
