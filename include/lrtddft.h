@@ -200,6 +200,24 @@ typedef struct {
 lrt_status lrtddft_attenuate(lrt_ctx* ctx, const lrt_atten_params* params, double* Sp,
                              lrt_atten_report* report);
 
+/* Allocation-free lrtddft_attenuate: same arguments, results and errors, but no device memory
+ * is allocated during the call.  The paper has no counterpart; this exists for callers that
+ * cannot call cudaMalloc/cudaFree when they attenuate: programs whose device memory is
+ * reserved by another allocator (e.g. a framework's caching pool that holds the free
+ * memory), or that must not pay the device-wide synchronisation cudaFree implies.
+ *  - Workspace: one fixed 16 MiB array compiled into the library.  Every GPU that loads the
+ *    library holds it until the process exits.  A call whose workspace (8 bytes per sample
+ *    for each q and each (degree, window) candidate, twice, plus small tables) exceeds
+ *    16 MiB returns LRT_EINVAL with the sizes in lrtddft_last_error.
+ *  - The first call for a context on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress, with the device current); make that first call before
+ *    any stream capture.
+ *  - All calls share the array, which keeps the last call's contents; each call clears the
+ *    part it uses before its kernels run.  Calls whose work overlaps on the GPU (several host
+ *    threads, contexts or streams) race on the array: serialise them. */
+lrt_status lrtddft_attenuate_noalloc(lrt_ctx* ctx, const lrt_atten_params* params, double* Sp,
+                                     lrt_atten_report* report);
+
 /* ---- instrumentation ---- */
 
 /* Reset the counters below and turn the CUDA-event timing of the chi0 contraction and

@@ -87,6 +87,8 @@ SIGNATURES = {
     "lrtddft_itcf_laplace": (C.c_int, [_P, C.c_int, _D, C.c_int, _D, _D]),
     "lrtddft_itcf_laplace_device": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
     "lrtddft_attenuate": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D, C.POINTER(lrt_atten_report)]),
+    "lrtddft_attenuate_noalloc": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D,
+                                            C.POINTER(lrt_atten_report)]),
     "lrtddft_profile": (C.c_int, [_P, C.c_int]),
     "lrtddft_profile_read": (C.c_int, [_P, _D]),
     "lrtddft_set_orbitals": (C.c_int, [_P, C.c_int, _D, _D, _D]),
@@ -220,6 +222,16 @@ class Context:
         Sp = np.zeros((self.nq, self.nw))
         rep = (lrt_atten_report * self.nq)()
         _check("lrtddft_attenuate", self.lib.lrtddft_attenuate(self.h, C.byref(p), _dp(Sp), rep))
+        return Sp, [report_dict(r) for r in rep]
+
+    def attenuate_noalloc(self, params: Optional[lrt_atten_params] = None):
+        """lrtddft_attenuate without device allocation (fixed 16 MiB workspace in the library;
+        calls must not overlap on the GPU)."""
+        p = params if params is not None else atten_params()
+        Sp = np.zeros((self.nq, self.nw))
+        rep = (lrt_atten_report * self.nq)()
+        _check("lrtddft_attenuate_noalloc",
+               self.lib.lrtddft_attenuate_noalloc(self.h, C.byref(p), _dp(Sp), rep))
         return Sp, [report_dict(r) for r in rep]
 
     # --- instrumentation ---

@@ -20,7 +20,9 @@
 //                         F(beta/2), S_p = mean (or best) of the accepted degrees.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <set>
+#include <string>
 #include <vector>
 
 #include "lrt_internal.h"
@@ -625,4 +627,235 @@ lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const 
   return LRT_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free attenuation.  The workspace is one file-scope device array that every GPU
+// loading the library holds until the process exits; its device address is looked up once
+// per device (cudaGetSymbolAddress with that device current) on the first call made for a
+// context on that device.  Calls share the array: two calls whose kernels overlap on the GPU
+// (from different host threads or streams) race and corrupt each other's results.
+// The paper has no counterpart: this entry point exists for callers that cannot allocate
+// device memory at call time.
+constexpr size_t kNoAllocScratchBytes = 16u << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_atten_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_scratch_mu;
+static void* g_scratch_addr[64] = {};
+
+static lrt_status scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal out of range for the fixed workspace table");
+    return LRT_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_atten_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("cudaGetSymbolAddress for the attenuation workspace: ") +
+                cudaGetErrorString(e));
+      return LRT_ECUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return LRT_OK;
+}
+
+lrt_status run_attenuation_noalloc(const lrt_ctx* c, const lrt_atten_params* pin,
+                                   const double* S_dev, double* Sp_host, lrt_atten_report* rep,
+                                   cudaStream_t s) {
+  lrt_atten_params p{};
+  if (pin) p = *pin;
+  AttCfg cfg{};
+  cfg.jp = c->nw;
+  for (int j = 0; j < c->nw; ++j)
+    if (c->omega[j] >= 0.0) {
+      cfg.jp = j;
+      break;
+    }
+  cfg.N = c->nw - cfg.jp;
+  if (cfg.N < 8) {
+    set_error("attenuation needs at least 8 samples with w >= 0");
+    return LRT_EINVAL;
+  }
+  cfg.zero = c->omega[cfg.jp] == 0.0;
+  cfg.dw = c->omega[cfg.jp + 1] - c->omega[cfg.jp];
+  for (int j = cfg.jp + 1; j < c->nw; ++j)
+    if (std::fabs((c->omega[j] - c->omega[j - 1]) - cfg.dw) > 1e-9 * cfg.dw) {
+      set_error("attenuation needs uniformly spaced samples with w >= 0");
+      return LRT_EINVAL;
+    }
+  const int N = cfg.N;
+  if (p.feat_lo <= 0.0 && p.feat_hi <= 0.0) {
+    cfg.i0 = std::max(1, (int)std::floor(0.05 * (N - 1)));
+    cfg.i1 = std::min(N - 2, (int)std::ceil(0.95 * (N - 1)));
+  } else {
+    const double* w = c->omega.data() + cfg.jp;
+    cfg.i0 = std::max(1, (int)(std::lower_bound(w, w + N, p.feat_lo) - w));
+    cfg.i1 = std::min(N - 2, (int)(std::upper_bound(w, w + N, p.feat_hi) - w) - 1);
+  }
+  cfg.L = cfg.i1 - cfg.i0 + 1;
+  if (cfg.L < 8) {
+    set_error("featureless range too short");
+    return LRT_EINVAL;
+  }
+  cfg.K = cfg.L / 2;
+  double low = p.low_exclude > 0 ? p.low_exclude : 0.05;
+  cfg.kmin = std::max(1, (int)std::ceil(low * cfg.K));
+  cfg.ntargets = p.n_targets > 0 ? std::min(p.n_targets, kMaxTargets) : 2;
+  cfg.lf = p.lambda_f > 0 ? p.lambda_f : N;
+  cfg.lc = p.lambda_c > 0 ? p.lambda_c : N;
+  cfg.r0 = p.retain_floor > 0 ? p.retain_floor : 1e-4;
+  cfg.dmin = p.d_min > 0 ? p.d_min : 1;
+  int dmax = p.d_max > 0 ? p.d_max : 4;
+  if (dmax < cfg.dmin || dmax - cfg.dmin + 1 > kMaxDegree || dmax > kMaxDegree) {
+    set_error("degree range");
+    return LRT_EINVAL;
+  }
+  cfg.ndeg = dmax - cfg.dmin + 1;
+  cfg.ntau = p.ntau > 1 ? p.ntau : 64;
+  cfg.accept_mean = p.accept_mean > 0 ? p.accept_mean : 4e-3;
+  cfg.accept_rms = p.accept_rms > 0 ? p.accept_rms : 4.2e-5;
+  cfg.average = (p.average == 2) ? 0 : 1;
+  cfg.T = c->T;
+  cfg.n = c->density;
+  cfg.nw = c->nw;
+  cfg.nwi = c->nwi;
+  cfg.hcol = c->hcol;
+  double wlo = p.w_min > 0 ? p.w_min : 4.0 * cfg.dw;
+  double whi = p.w_max > 0 ? p.w_max : 0.25 * N * cfg.dw;
+  int nwin = p.n_w > 0 ? p.n_w : 24;
+  std::set<int> ms;
+  for (int i = 0; i < nwin; ++i) {
+    double w = nwin == 1 ? wlo : wlo + (whi - wlo) * i / (nwin - 1);
+    ms.insert(2 * (int)std::floor(w / (2.0 * cfg.dw) + 0.5) + 1);
+  }
+  std::vector<int2> cands;
+  for (int d = cfg.dmin; d <= dmax; ++d)
+    for (int m : ms)
+      if (m >= d + 2 && m <= N && m >= 3) cands.push_back(make_int2(d, m));
+  cfg.ncand = (int)cands.size();
+  if (cfg.ncand == 0) {
+    set_error("no admissible (degree, window) candidate");
+    return LRT_EINVAL;
+  }
+  const int nq = c->nq;
+  // carve the fixed array; reject what does not fit
+  auto up = [](size_t n) { return (n + 255) / 256 * 256; };
+  const size_t prep_b = up((size_t)nq * (cfg.L + cfg.K + 1) * sizeof(double));
+  const size_t yf_b = up((size_t)nq * cfg.ncand * N * sizeof(double));
+  const size_t dw_b = up((size_t)nq * cfg.ncand * cfg.L * sizeof(double));
+  const size_t fn_b = up((size_t)nq * cfg.ntau * sizeof(double));
+  const size_t sp_b = up((size_t)nq * c->nw * sizeof(double));
+  const size_t aq_b = up(nq * sizeof(AttQ));
+  const size_t co_b = up((size_t)nq * cfg.ncand * sizeof(CandOut));
+  const size_t do_b = up((size_t)nq * kMaxDegree * sizeof(DegOut));
+  const size_t dc_b = up(cfg.ncand * sizeof(int2));
+  const size_t na_b = up(nq * sizeof(int));
+  const size_t need = prep_b + yf_b + dw_b + fn_b + sp_b + aq_b + co_b + do_b + dc_b + na_b;
+  if (need > kNoAllocScratchBytes) {
+    set_error("attenuation workspace of " + std::to_string(need) + " bytes exceeds the " +
+              std::to_string(kNoAllocScratchBytes) +
+              "-byte fixed array of the allocation-free entry point (fewer q, windows or "
+              "frequencies per call fit)");
+    return LRT_EINVAL;
+  }
+  void* base = nullptr;
+  LRT_TRY(scratch_address(c->device, &base));
+  char* buf = static_cast<char*>(base);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    char* p0 = buf + off;
+    off += b;
+    return p0;
+  };
+  double* prep = (double*)take(prep_b);
+  double* yf = (double*)take(yf_b);
+  double* dwork = (double*)take(dw_b);
+  double* fnw = (double*)take(fn_b);
+  double* spd = (double*)take(sp_b);
+  AttQ* aq = (AttQ*)take(aq_b);
+  CandOut* co = (CandOut*)take(co_b);
+  DegOut* dout = (DegOut*)take(do_b);
+  int2* dc = (int2*)take(dc_b);
+  int* nacc = (int*)take(na_b);
+  // the array keeps the previous call's contents: start this call from zeros
+  LRT_CUDA(cudaMemsetAsync(buf, 0, need, s));
+  LRT_CUDA(cudaMemcpyAsync(dc, cands.data(), cands.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  att_prep<<<nq, 256, 0, s>>>(S_dev, cfg, prep, aq);
+  LRT_CUDA(cudaGetLastError());
+  att_candidates<<<dim3(cfg.ncand, nq), 256, 0, s>>>(S_dev, cfg, dc, aq, yf, dwork, co);
+  LRT_CUDA(cudaGetLastError());
+  att_select<<<nq, 256, 0, s>>>(S_dev, (const double2*)c->dw.chi00, c->dw.omega, cfg, dc, yf, co, fnw,
+                                spd, dout, nacc);
+  count_launch(c, 3);
+  LRT_CUDA(cudaGetLastError());
+  LRT_CUDA(cudaMemcpyAsync(Sp_host, spd, (size_t)nq * c->nw * sizeof(double), cudaMemcpyDeviceToHost, s));
+  std::vector<AttQ> hq(nq);
+  std::vector<DegOut> hd((size_t)nq * kMaxDegree);
+  std::vector<int> hn(nq);
+  LRT_CUDA(cudaMemcpyAsync(hq.data(), aq, nq * sizeof(AttQ), cudaMemcpyDeviceToHost, s));
+  LRT_CUDA(cudaMemcpyAsync(hd.data(), dout, hd.size() * sizeof(DegOut), cudaMemcpyDeviceToHost, s));
+  LRT_CUDA(cudaMemcpyAsync(hn.data(), nacc, nq * sizeof(int), cudaMemcpyDeviceToHost, s));
+  LRT_CUDA(cudaStreamSynchronize(s));
+  if (rep) {
+    for (int iq = 0; iq < nq; ++iq) {
+      lrt_atten_report& r = rep[iq];
+      r.n_accepted = hn[iq];
+      for (int i = 0; i < 4; ++i) r.targets[i] = i < hq[iq].ntg ? hq[iq].tg[i] : -1;
+      for (int i = 0; i < LRT_ATTEN_MAX_DEG; ++i) {
+        if (i < cfg.ndeg && hd[(size_t)iq * kMaxDegree + i].m > 0) {
+          const DegOut& o = hd[(size_t)iq * kMaxDegree + i];
+          r.degree[i] = o.d;
+          r.window[i] = o.m;
+          r.score[i] = o.score;
+          r.mean_ratio[i] = o.mean_ratio;
+          r.rms_ratio[i] = o.rms_ratio;
+          r.accepted[i] = o.accepted;
+        } else {
+          r.degree[i] = -1;
+          r.window[i] = 0;
+          r.score[i] = r.mean_ratio[i] = r.rms_ratio[i] = 0.0;
+          r.accepted[i] = 0;
+        }
+      }
+    }
+  }
+  return LRT_OK;
+}
+
 }  // namespace lrt
+
+// Allocation-free variant of lrtddft_attenuate (declared in include/lrtddft.h).
+extern "C" lrt_status lrtddft_attenuate_noalloc(lrt_ctx* c, const lrt_atten_params* p, double* Sp,
+                                                lrt_atten_report* rep) {
+  using namespace lrt;
+  if (!c || !Sp) {
+    set_error("NULL argument");
+    return LRT_EINVAL;
+  }
+  if (c->host_only) {
+    set_error("host-only context");
+    return LRT_ESTATE;
+  }
+  LRT_CUDA(cudaSetDevice(c->device));
+  for (auto& Q : c->qd)
+    if (!Q.have_chi) {
+      set_error("spectra requested before dyson_solve on every q");
+      return LRT_ESTATE;
+    }
+  LRT_CUDA(cudaDeviceSynchronize());
+  LRT_TRY(launch_dsf(c, c->dw.S, 0));
+  LRT_TRY(run_attenuation_noalloc(c, p, c->dw.S, Sp, rep, 0));
+  int st = 0;
+  LRT_CUDA(cudaMemcpy(&st, c->dw.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & 1) {
+    set_error("zero pivot in a Dyson matrix");
+    return LRT_ESINGULAR;
+  }
+  if (st & 2) {
+    set_error("a bounded device wait ran out");
+    return LRT_ETIMEOUT;
+  }
+  return LRT_OK;
+}
