@@ -21,7 +21,7 @@ constexpr int PC = 32;   // pairs per chunk
 __global__ void __launch_bounds__(256) chi0_fp64_kernel(
     const double2* __restrict__ rho, const double* __restrict__ delta,
     const double* __restrict__ df, const double* __restrict__ freqs, int nwi, int nG,
-    int64_t np, double eta, double pref, int nblk, int64_t p_per_split,
+    int64_t np, int64_t ld, double eta, double pref, int nblk, int64_t p_per_split,
     double2* __restrict__ chi0) {
   __shared__ double2 rI[PC][GB];
   __shared__ double2 rJ[PC][GB];
@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(256) chi0_fp64_kernel(
       int64_t pp = p0 + p;
       int GI = I * GB + g, GJ = J * GB + g;
       double2 z = make_double2(0.0, 0.0);
-      rI[p][g] = (pp < pend && GI < nG) ? rho[(size_t)GI * np + pp] : z;
-      rJ[p][g] = (pp < pend && GJ < nG) ? rho[(size_t)GJ * np + pp] : z;
+      rI[p][g] = (pp < pend && GI < nG) ? rho[(size_t)GI * ld + pp] : z;
+      rJ[p][g] = (pp < pend && GJ < nG) ? rho[(size_t)GJ * ld + pp] : z;
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -118,7 +118,8 @@ lrt_status launch_chi0_fp64(const lrt_ctx* c, QData& q, cudaStream_t s) {
   {
     TimedLaunch tl(c, &c->ev_chi0, s);
     chi0_fp64_kernel<<<grid, 256, 0, s>>>((const double2*)c->dw.rho, c->dw.delta, c->dw.df,
-                                          c->dw.freqs, c->nwi, q.nG, c->np, c->eta, pref, nblk, per,
+                                          c->dw.freqs, c->nwi, q.nG, c->np, c->rho_ld, c->eta, pref,
+                                          nblk, per,
                                           q.chi0);
   }
   count_launch(c);

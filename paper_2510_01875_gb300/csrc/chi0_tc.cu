@@ -33,23 +33,33 @@ namespace {
 constexpr int TM = 128;            // GEMM rows per tile (64 row pairs)
 constexpr int TN = 256;            // GEMM columns per tile (128 frequencies)
 constexpr int KS = 32;             // pairs (K) per pipeline stage
-constexpr int NS = 4;              // pipeline stages
+constexpr int NS = 3;              // operand (A/B) stages
+constexpr int NSR = 6;             // prefetch stages of rho rows and pair weights
+constexpr int RROWS = 32;          // distinct G of one row tile held in a prefetch stage
 constexpr int NPROD = 8;           // producer warps 0..7
 constexpr int WMMA = 8;            // MMA warp
-constexpr int NTHREADS = 13 * 32;
+constexpr int WLOAD = 13;          // loader warp (bulk copies of rho and the pair weights)
+constexpr int NTHREADS = 14 * 32;  // + epilogue warps 9..12
 constexpr int A_BYTES = TM * KS * 2;                 // 8 KB per 16-bit tile
 constexpr int B_BYTES = TN * KS * 2;                 // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int RROW_BYTES = KS * 8;                   // one G: 32 complex FP32 = 256 B
+constexpr int R_STAGE = RROWS * RROW_BYTES + KS * 16;   // rho rows + 32 float4 pair weights
 constexpr int A_SBO = (TM / 64) * 1024;              // bytes between 8-pair groups of A
 constexpr int B_SBO = (TN / 64) * 1024;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
+constexpr int kFlushStages = 64;   // FP32 accumulation period: 64 stages = 2048 pairs
 
 struct Params {
-  const float2* rho;          // [nG][np]
-  const float4* pw;           // [np] {Delta_hi, Delta_lo, df, 0}
-  const int2* rowtab;         // [n_m * 64] (G, G') per row pair, (-1, -1) padding
+  const float2* rho;          // [nG][ld_rho]
+  const float4* pw;           // [np rounded up to 32] {Delta_hi, Delta_lo, df, 0}
+  const int2* rowtab;         // [n_m * 64] local (G, G') indices per row pair, (-1, -1) padding
+  const int* gl;              // [n_m * RROWS] global G of each local index, -1 padding
+  long long ld_rho;
   const float2* wtab;         // [n_n * 128] frequency hi/lo per column pair
-  double* C;                  // [n_m * TM][ldc] FP64 sums
+  double* C;                  // [n_n * TN][ldr] FP64 sums, column-major
+  double* part;               // [gridDim.x][TN][TM] per-CTA unit partials, column-major
+  long long ldr;              // = n_m * TM
   int* status;
   long long np;
   int ldc;                    // = n_n * TN
@@ -104,6 +114,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
     }
   }
   return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted in bytes on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() {
@@ -203,20 +229,28 @@ template <bool BF>
 __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], final_bar;
+  __shared__ __align__(8) uint64_t rfull[NSR], rempty[NSR];
   __shared__ uint32_t tmem_base_s;
   __shared__ int2 rowtab_s[64];
+  __shared__ int gl_s[RROWS];
+  __shared__ int ngl_s;
   __shared__ float2 wtab_s[128];
   __shared__ volatile int abort_s;
-  __shared__ int unit_sync;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* base_gen = smem_raw + (base - smem_u32(smem_raw));
+  const uint32_t rbase = base + NS * STAGE_BYTES;          // prefetch ring
+  const uint8_t* rbase_gen = base_gen + NS * STAGE_BYTES;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], NPROD);
       mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < NSR; ++s) {
+      mbar_init(&rfull[s], 1);
+      mbar_init(&rempty[s], NPROD);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -248,6 +282,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     __syncthreads();
     if (threadIdx.x < 64) rowtab_s[threadIdx.x] = P.rowtab[U.mt * 64 + threadIdx.x];
     if (threadIdx.x < 128) wtab_s[threadIdx.x] = P.wtab[U.nt * 128 + threadIdx.x];
+    if (threadIdx.x < RROWS) gl_s[threadIdx.x] = P.gl[U.mt * RROWS + threadIdx.x];
+    if (threadIdx.x == 0) {
+      int n = 0;
+      while (n < RROWS && P.gl[U.mt * RROWS + n] >= 0) ++n;
+      ngl_s = n;
+    }
     __syncthreads();
     if (abort_s) break;
     const long long nstage = (U.ke - U.kb + KS - 1) / KS;
@@ -256,11 +296,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     if (warp < NPROD) {
       // ---------------- producers ----------------
       for (long long st = 0; st < nstage; ++st, ++it) {
-        const int s = it % NS;
+        const int s = it % NS, sr = it % NSR;
+        if (!mbar_wait(&rfull[sr], (it / NSR) & 1, &abort_s, P.status)) break;
         if (!mbar_wait(&empty[s], ((it / NS) & 1) ^ 1, &abort_s, P.status)) break;
         const long long p = U.kb + st * KS + lane;
         const bool valid = p < U.ke;
-        float4 pw = valid ? P.pw[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2* rrow = reinterpret_cast<const float2*>(rbase_gen + sr * R_STAGE) + lane;
+        const float4* rpw =
+            reinterpret_cast<const float4*>(rbase_gen + sr * R_STAGE + RROWS * RROW_BYTES);
+        float4 pw = valid ? rpw[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t sA_hi = base + s * STAGE_BYTES, sA_lo = sA_hi + A_BYTES;
         const uint32_t sB_hi = sA_lo + A_BYTES, sB_lo = sB_hi + B_BYTES;
 #pragma unroll 1
@@ -273,8 +317,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
               int2 g = rowtab_s[4 * c + i];
               float pr = 0.f, pi = 0.f;
               if (valid && g.x >= 0) {
-                float2 a = P.rho[(size_t)g.x * P.np + p];
-                float2 b = P.rho[(size_t)g.y * P.np + p];
+                float2 a = rrow[g.x * KS];
+                float2 b = rrow[g.y * KS];
                 pr = (a.x * b.x + a.y * b.y) * P.sA;
                 pi = (a.y * b.x - a.x * b.y) * P.sA;
               }
@@ -305,8 +349,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
         }
         fence_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&full[s]);
+        if (lane == 0) {
+          mbar_arrive(&full[s]);
+          mbar_arrive(&rempty[sr]);
+        }
       }
+    } else if (warp == WLOAD) {
+      // ---------------- loader: rho rows and pair weights of each stage ----------------
+      if (lane == 0) {
+        const int ngl = ngl_s;
+        const uint32_t bytes = (uint32_t)(ngl * RROW_BYTES + KS * 16);
+        for (long long st = 0; st < nstage; ++st, ++it) {
+          const int sr = it % NSR;
+          if (!mbar_wait(&rempty[sr], ((it / NSR) & 1) ^ 1, &abort_s, P.status)) break;
+          const long long p0 = U.kb + st * KS;
+          mbar_expect_tx(&rfull[sr], bytes);
+          const uint32_t dst = rbase + sr * R_STAGE;
+          for (int i = 0; i < ngl; ++i)
+            bulk_g2s(dst + i * RROW_BYTES, P.rho + (size_t)gl_s[i] * P.ld_rho + p0, RROW_BYTES,
+                     &rfull[sr]);
+          bulk_g2s(dst + RROWS * RROW_BYTES, P.pw + p0, KS * 16, &rfull[sr]);
+        }
+      }
+      it = __shfl_sync(0xffffffffu, it, 0);
     } else if (warp == WMMA) {
       // ---------------- MMA issuer ----------------
       for (long long per = 0; per < nper; ++per, ++pc) {
@@ -347,15 +412,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       }
     } else {
       // ---------------- epilogue ----------------
+      // The unit's FP64 sums live in a private column-major slab of global memory (one row per
+      // lane: a warp touches 32 consecutive doubles per column) and are added into C once, when
+      // the unit's pair range is done.
       const int q = warp & 3;            // tensor-memory lane quadrant of this warp
       const int row = q * 32 + lane;
       const long long grow = (long long)U.mt * TM + row;
+      double* part = P.part + (size_t)blockIdx.x * TM * TN + row;
+      bool unit_ok = true;
       for (long long per = 0; per < nper; ++per, ++pc) {
         const uint32_t b = pc & 1;
         bool ok = true;
         if (lane == 0) ok = mbar_wait(&acc_full[b], (pc >> 1) & 1, &abort_s, P.status);
         ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
+        if (!ok) {
+          unit_ok = false;
+          break;
+        }
         tc_fence_after();
 #pragma unroll 1
         for (int c = 0; c < TN / 32; ++c) {
@@ -372,23 +445,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
                 "=r"(r[30]), "=r"(r[31])
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (grow < P.rows_valid) {
-            double* crow = P.C + grow * P.ldc + (long long)U.nt * TN + c * 32;
-            const int col0 = U.nt * TN + c * 32;
+          double* slab = part + (size_t)(c * 32) * TM;
+          if (per == 0) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (col0 + j < P.cols_valid) atomicAdd(crow + j, (double)__uint_as_float(r[j]));
+            for (int j = 0; j < 32; ++j) slab[(size_t)j * TM] = (double)__uint_as_float(r[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) slab[(size_t)j * TM] += (double)__uint_as_float(r[j]);
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[b]);
       }
+      if (unit_ok && grow < P.rows_valid) {
+        const int col0 = U.nt * TN;
+        for (int j = 0; j < TN && col0 + j < P.cols_valid; ++j)
+          atomicAdd(P.C + (size_t)(col0 + j) * P.ldr + grow, part[(size_t)j * TM]);
+      }
     }
     // keep every role on the same unit; an abort stops all of them
     __syncthreads();
   }
-  // drain: wait (bounded) for this CTA's MMAs before freeing tensor memory
+  // drain: the loader waits (bounded) for its last bulk copies, the MMA warp for this CTA's
+  // MMAs, before the shared and tensor memory go away
+  if (warp == WLOAD && lane == 0) {
+    for (uint32_t j = (it > (uint32_t)NSR ? it - NSR : 0u); j < it; ++j) {
+      unsigned long long t0 = gtime();
+      while (!mbar_try(&rfull[j % NSR], (j / NSR) & 1)) {
+        if (gtime() - t0 > kTimeoutNs) {
+          atomicOr(P.status, 2);
+          break;
+        }
+      }
+    }
+  }
   if (warp == WMMA) {
     if (lane == 0) {
       mma_commit(&final_bar);
@@ -407,13 +498,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   tc_fence_after();
   if (warp == WMMA)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN));
-  (void)unit_sync;
   (void)base_gen;
 }
 
-// chi0[w][G][G'] from the FP64 sums
-__global__ void chi0_unpack(const double* __restrict__ C, int ldc, const int* __restrict__ rp_of,
-                            int nG, int nwi, double scale, double2* __restrict__ chi0) {
+// chi0[w][G][G'] from the FP64 sums (C column-major: C[col * ldr + row])
+__global__ void chi0_unpack(const double* __restrict__ C, long long ldr,
+                            const int* __restrict__ rp_of, int nG, int nwi, double scale,
+                            double2* __restrict__ chi0) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long total = (long long)nwi * nG * nG;
   if (t >= total) return;
@@ -421,9 +512,9 @@ __global__ void chi0_unpack(const double* __restrict__ C, int ldc, const int* __
   int G = (int)((t / nG) % nG);
   int w = (int)(t / ((long long)nG * nG));
   int rp = rp_of[G * nG + Gp];
-  const double* re = C + (long long)(2 * rp) * ldc + 2 * w;
-  const double* im = C + (long long)(2 * rp + 1) * ldc + 2 * w;
-  double RR = re[0], RI = re[1], IR = im[0], II = im[1];
+  const double* cre = C + (long long)(2 * w) * ldr;       // column Re w
+  const double* cim = C + (long long)(2 * w + 1) * ldr;   // column Im w
+  double RR = cre[2 * rp], IR = cre[2 * rp + 1], RI = cim[2 * rp], II = cim[2 * rp + 1];
   double2 v;
   if (G <= Gp)
     v = make_double2(RR - II, RI + IR);
@@ -474,11 +565,32 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   const int npairs = (int)pairs.size();
   const int n_m = (npairs + 63) / 64;
   std::vector<int2> rowtab((size_t)n_m * 64, make_int2(-1, -1));
+  std::vector<int> gl((size_t)n_m * RROWS, -1);
   std::vector<int> rp_of((size_t)nG * nG);
   for (int i = 0; i < npairs; ++i) {
-    rowtab[i] = pairs[i];
     rp_of[pairs[i].x * nG + pairs[i].y] = i;
     rp_of[pairs[i].y * nG + pairs[i].x] = i;
+  }
+  // per row tile: the distinct G it touches (local indices into the prefetched rho rows)
+  for (int t = 0; t < n_m; ++t) {
+    int* g = &gl[(size_t)t * RROWS];
+    int n = 0;
+    auto local = [&](int G) {
+      for (int i = 0; i < n; ++i)
+        if (g[i] == G) return i;
+      if (n == RROWS) return -1;
+      g[n] = G;
+      return n++;
+    };
+    for (int r = 0; r < 64 && t * 64 + r < npairs; ++r) {
+      const int2 pr = pairs[t * 64 + r];
+      int a = local(pr.x), b = local(pr.y);
+      if (a < 0 || b < 0) {
+        set_error("a row tile touches more than 32 distinct G");
+        return LRT_EUNSUPPORTED;
+      }
+      rowtab[(size_t)t * 64 + r] = make_int2(a, b);
+    }
   }
   const int ncols = 2 * c->nwi;
   const int n_n = (ncols + TN - 1) / TN;
@@ -513,8 +625,12 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   kps = (kps + KS - 1) / KS * KS;
   const int n_split = (int)((c->np + kps - 1) / kps);
 
-  // device tables and buffers
-  size_t need = (size_t)n_m * TM * ldc * sizeof(double);
+  // device tables and buffers: C (column-major FP64 sums) followed by the per-CTA slabs
+  const long long ldr = (long long)n_m * TM;
+  const long long units = tiles * n_split;
+  const int grid = (int)std::min<long long>(nsm, units);
+  const size_t c_bytes = (size_t)ldr * ldc * sizeof(double);
+  const size_t need = c_bytes + (size_t)grid * TM * TN * sizeof(double);
   DeviceWork& dw = const_cast<DeviceWork&>(c->dw);
   if (dw.scratch_bytes < need) {
     cudaFree(dw.scratch);
@@ -524,26 +640,36 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
     dw.scratch_bytes = need;
   }
   int2* d_rowtab = nullptr;
+  int* d_gl = nullptr;
   int* d_rp = nullptr;
   float2* d_wtab = nullptr;
   float4* d_pw = nullptr;
+  // pair weights padded to whole 32-pair stages (the bulk copies read full stages)
+  const size_t npw_pad = (size_t)((c->np + KS - 1) / KS * KS);
   LRT_CUDA(cudaMallocAsync(&d_rowtab, rowtab.size() * sizeof(int2), s));
+  LRT_CUDA(cudaMallocAsync(&d_gl, gl.size() * sizeof(int), s));
   LRT_CUDA(cudaMallocAsync(&d_rp, rp_of.size() * sizeof(int), s));
   LRT_CUDA(cudaMallocAsync(&d_wtab, wtab.size() * sizeof(float2), s));
-  LRT_CUDA(cudaMallocAsync(&d_pw, (size_t)c->np * sizeof(float4), s));
+  LRT_CUDA(cudaMallocAsync(&d_pw, npw_pad * sizeof(float4), s));
+  LRT_CUDA(cudaMemsetAsync(d_pw, 0, npw_pad * sizeof(float4), s));
   LRT_CUDA(cudaMemcpyAsync(d_rowtab, rowtab.data(), rowtab.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  LRT_CUDA(cudaMemcpyAsync(d_gl, gl.data(), gl.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   LRT_CUDA(cudaMemcpyAsync(d_rp, rp_of.data(), rp_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   LRT_CUDA(cudaMemcpyAsync(d_wtab, wtab.data(), wtab.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
   pair_weights_split<<<4 * nsm, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, d_pw);
   LRT_CUDA(cudaGetLastError());
-  LRT_CUDA(cudaMemsetAsync(dw.scratch, 0, need, s));
+  LRT_CUDA(cudaMemsetAsync(dw.scratch, 0, c_bytes, s));
 
   Params P;
   P.rho = (const float2*)dw.rho;
   P.pw = d_pw;
   P.rowtab = d_rowtab;
+  P.gl = d_gl;
+  P.ld_rho = c->rho_ld;
   P.wtab = d_wtab;
   P.C = dw.scratch;
+  P.part = dw.scratch + (size_t)ldr * ldc;
+  P.ldr = ldr;
   P.status = dw.status;
   P.np = c->np;
   P.ldc = ldc;
@@ -553,13 +679,11 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   P.n_n = n_n;
   P.n_split = n_split;
   P.k_per_split = kps;
-  P.flush = 128;
+  P.flush = kFlushStages;
   P.eta = (float)c->eta;
   P.sA = sA;
   P.sB = sB;
-  const size_t smem = (size_t)NS * STAGE_BYTES + 1024;
-  long long units = tiles * n_split;
-  int grid = (int)std::min<long long>(nsm, units);
+  const size_t smem = (size_t)NS * STAGE_BYTES + (size_t)NSR * R_STAGE + 1024;
   if (bf)
     LRT_CUDA(cudaFuncSetAttribute(chi0_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   else
@@ -576,11 +700,12 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   LRT_CUDA(cudaGetLastError());
   const double scale = 2.0 / (c->nk * c->volume) / ((double)sA * (double)sB);
   long long total = (long long)c->nwi * nG * nG;
-  chi0_unpack<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dw.scratch, ldc, d_rp, nG, c->nwi, scale,
+  chi0_unpack<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dw.scratch, ldr, d_rp, nG, c->nwi, scale,
                                                              q.chi0);
   count_launch(c);
   LRT_CUDA(cudaGetLastError());
   LRT_CUDA(cudaFreeAsync(d_rowtab, s));
+  LRT_CUDA(cudaFreeAsync(d_gl, s));
   LRT_CUDA(cudaFreeAsync(d_rp, s));
   LRT_CUDA(cudaFreeAsync(d_wtab, s));
   LRT_CUDA(cudaFreeAsync(d_pw, s));

@@ -93,6 +93,8 @@ struct lrt_ctx {
   int npw = 0;                    // padded plane-wave count (max over all k points)
   int nGmax = 0;
   int64_t np = 0;                 // pairs per q = nk nb^2
+  int64_t rho_ld = 0;             // row stride of rho[G][p]: np rounded up to 32 (256 B rows
+                                  // for bulk copies of 32-pair stages)
   std::vector<lrt::QData> qd;
   lrt::DeviceWork dw;
   bool have_S = false;

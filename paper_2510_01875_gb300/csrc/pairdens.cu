@@ -5,8 +5,9 @@
 // coefficients taken from an FFT of u*_nk u_n'k+q on the real-space grid (N_pw N_G is
 // 15-50x smaller at these cut-offs).
 //
-// Output layout: rho[G][p], p = (k nb + n) nb + n', so that the chi0 contraction streams a
-// contiguous run of pairs for each G.
+// Output layout: rho[G][p] with row stride ld (the pair count rounded up to 32), p = (k nb + n)
+// nb + n', so that the chi0 contraction streams a contiguous, 256-byte aligned run of pairs for
+// each G.
 #include "lrt_internal.h"
 
 namespace lrt {
@@ -30,7 +31,7 @@ constexpr int TK = 16;   // plane waves per step
 template <typename R>
 __global__ void __launch_bounds__(256) pair_density_kernel(
     const double2* __restrict__ ck, const double2* __restrict__ ckq,
-    const int32_t* __restrict__ gather, int nk, int nb, int npw, int nG, int ntile,
+    const int32_t* __restrict__ gather, int nk, int nb, int npw, int nG, int ntile, int64_t ld,
     typename C2<R>::T* __restrict__ rho) {
   using CT = typename C2<R>::T;
   __shared__ CT As[TK][TN];
@@ -83,8 +84,7 @@ __global__ void __launch_bounds__(256) pair_density_kernel(
     }
     __syncthreads();
   }
-  const int64_t np = (int64_t)nk * nb * nb;
-  CT* out = rho + (size_t)G * np + (size_t)k * nb * nb;
+  CT* out = rho + (size_t)G * ld + (size_t)k * nb * nb;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     int n = n0 + ty + 16 * i;
@@ -125,10 +125,10 @@ lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool
     TimedLaunch tl(c, &c->ev_rho, s);
     if (fp32)
       pair_density_kernel<float><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw, q.nG,
-                                                      ntile, (float2*)rho);
+                                                      ntile, c->rho_ld, (float2*)rho);
     else
       pair_density_kernel<double><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw,
-                                                       q.nG, ntile, (double2*)rho);
+                                                       q.nG, ntile, c->rho_ld, (double2*)rho);
   }
   count_launch(c);
   LRT_CUDA(cudaGetLastError());

@@ -667,6 +667,7 @@ lrt_status solve_ground_states(lrt_ctx* c, const double* occupations) {
     }
   }
   c->np = (int64_t)nk * c->nb * c->nb;
+  c->rho_ld = (c->np + 31) / 32 * 32;
   return LRT_OK;
 }
 
