@@ -78,7 +78,7 @@ lrt_status check_status_word(lrt_ctx* c) {
 
 lrt_status ensure_rho(lrt_ctx* c) {
   size_t elem = (c->precision == LRT_PREC_FP64) ? sizeof(double2) : sizeof(float2);
-  size_t need = (size_t)c->nGmax * c->rho_ld * elem;
+  size_t need = (size_t)(c->rho_gpad ? c->rho_gpad : c->nGmax) * c->rho_ld * elem;
   if (c->dw.rho_bytes >= need) return LRT_OK;
   cudaFree(c->dw.rho);
   c->dw.rho = nullptr;

@@ -6,18 +6,27 @@
 // c = (w, Re|Im of w_p(w) = df_p / (w + Delta_p + i eta)).  From RR, RI, IR, II of a row pair
 // and a column pair, chi0(G,G') = (RR - II) + i(RI + IR) and chi0(G',G) = (RR + II) + i(RI - IR).
 //
-// Both operands are generated inside the kernel and never stored in global memory: producer
-// warps read rho (FP32, [G][p]) and (Delta_p, df_p), form P and w in FP32, split every value
-// v into v_hi = round16(v) and v_lo = round16(v - v_hi) (FP16 with power-of-two scaling, or
-// BF16), and write the four tiles MN-major with the 128-byte swizzle (one lane per pair =
-// per K index; 16-byte vector stores of 8 consecutive rows or columns).  One thread issues
-// tcgen05.mma kind::f16 for A_hi B_hi + A_hi B_lo + A_lo B_hi into an FP32 accumulator in
-// tensor memory; every `flush` stages the accumulator is drained by four epilogue warps
-// (tcgen05.ld) into FP64 sums in global memory while the MMAs continue in the second
-// accumulator.  Units of work are (row tile, column tile, pair range), handed out round-robin
-// to one CTA per SM.  Every wait on an mbarrier is bounded; on expiry the kernel sets bit 2 of
-// the status word, stops issuing work, waits (bounded) for its own MMAs and frees its tensor
-// memory before returning.
+// Both operands are generated inside the kernel and never stored in global memory.  Per
+// 32-pair stage:
+//  - a loader warp copies the stage's rho rows (blocked layout rho[p/32][G][p%32]: one 2 KB
+//    bulk copy per 8-G block the row tile touches) and the 32 (Delta_hi, Delta_lo, df) into a
+//    shared-memory ring with cp.async.bulk, completion counted in bytes on an mbarrier;
+//  - 16 producer warps form P (8 warps, 256 rows) and w (8 warps, 256 columns) in FP32, with
+//    w + Delta carried as (hi, lo) floats so the sum keeps FP64-level accuracy when it
+//    cancels, split every value v into v_hi = round16(v) and v_lo = round16(v - v_hi) (FP16
+//    with power-of-two scales, or BF16), and write the tiles MN-major with the 128-byte
+//    swizzle (each lane owns one pair = one K index and stores 16-byte chunks of 8 rows or
+//    columns);
+//  - one thread issues tcgen05.mma kind::f16, M = 128, N = 256, K = 16, for
+//    A_hi B_hi + A_hi B_lo + A_lo B_hi into two FP32 accumulators in tensor memory (two row
+//    tiles share each B tile: 256 x 256 outputs per CTA);
+//  - every `flush` stages four epilogue warps read the accumulators (tcgen05.ld) and add them
+//    into a per-CTA double-float (FP32 hi + lo, two-sum) slab in global memory; at the end of
+//    a unit the slab is added into the FP64 sums C.
+// Units of work are (row super-tile, column tile, pair range), handed out round-robin to one
+// CTA per SM.  Every wait on an mbarrier is bounded; on expiry the kernel sets bit 2 of the
+// status word, stops issuing work, waits (bounded) for its own copies and MMAs and frees its
+// tensor memory before returning.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -30,42 +39,45 @@
 namespace lrt {
 namespace {
 
-constexpr int TM = 128;            // GEMM rows per tile (64 row pairs)
-constexpr int TN = 256;            // GEMM columns per tile (128 frequencies)
+constexpr int TM = 128;            // rows per accumulator (64 row pairs)
+constexpr int NACC = 2;            // accumulators (row tiles) per CTA
+constexpr int TN = 256;            // columns per tile (128 frequencies)
 constexpr int KS = 32;             // pairs (K) per pipeline stage
-constexpr int NS = 3;              // operand (A/B) stages
-constexpr int NSR = 6;             // prefetch stages of rho rows and pair weights
-constexpr int RROWS = 32;          // distinct G of one row tile held in a prefetch stage
-constexpr int NPROD = 8;           // producer warps 0..7
-constexpr int WMMA = 8;            // MMA warp
-constexpr int WLOAD = 13;          // loader warp (bulk copies of rho and the pair weights)
-constexpr int NTHREADS = 14 * 32;  // + epilogue warps 9..12
-constexpr int A_BYTES = TM * KS * 2;                 // 8 KB per 16-bit tile
+constexpr int NS = 2;              // operand (A/B) stages
+constexpr int NSR = 6;             // prefetch stages of rho blocks and pair weights
+constexpr int GBLK = 8;            // G per block of the blocked rho layout
+constexpr int MAXBLK = 6;          // G blocks one row super-tile may touch
+constexpr int RROWS = MAXBLK * GBLK;
+constexpr int NPROD = 16;          // producer warps 0..15: 0..7 build A, 8..15 build B
+constexpr int WMMA = 16;           // MMA warp
+constexpr int WLOAD = 21;          // loader warp
+constexpr int NTHREADS = 22 * 32;  // + epilogue warps 17..20 (one per TMEM lane quadrant)
+constexpr int CHUNKS = 4;          // 16-byte chunks (8 rows or columns) per producer warp
+constexpr int A_BYTES = TM * KS * 2;                 // 8 KB per 16-bit row tile
 constexpr int B_BYTES = TN * KS * 2;                 // 16 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int RROW_BYTES = KS * 8;                   // one G: 32 complex FP32 = 256 B
-constexpr int R_STAGE = RROWS * RROW_BYTES + KS * 16;   // rho rows + 32 float4 pair weights
+constexpr int STAGE_BYTES = NACC * 2 * A_BYTES + 2 * B_BYTES;   // 64 KB
 constexpr int A_SBO = (TM / 64) * 1024;              // bytes between 8-pair groups of A
 constexpr int B_SBO = (TN / 64) * 1024;
+constexpr int RBLK_BYTES = GBLK * KS * 8;            // one G block of one stage: 2 KB
+constexpr int R_STAGE = RROWS * KS * 8 + KS * 16;    // rho rows + 32 float4 pair weights
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
-constexpr int kFlushStages = 64;   // FP32 accumulation period: 64 stages = 2048 pairs
+constexpr int kFlushStages = 128;  // FP32 accumulation period: 128 stages = 4096 pairs
 
 struct Params {
-  const float2* rho;          // [nG][ld_rho]
+  const float2* rho;          // blocked [ld/32][gpad][32]
   const float4* pw;           // [np rounded up to 32] {Delta_hi, Delta_lo, df, 0}
-  const int2* rowtab;         // [n_m * 64] local (G, G') indices per row pair, (-1, -1) padding
-  const int* gl;              // [n_m * RROWS] global G of each local index, -1 padding
-  long long ld_rho;
+  const int2* rowtab;         // [n_st * 128] local (G, G') indices per row pair, -1 padding
+  const int* blk;             // [n_st * MAXBLK] G blocks of the super-tile, -1 padding
   const float2* wtab;         // [n_n * 128] frequency hi/lo per column pair
   double* C;                  // [n_n * TN][ldr] FP64 sums, column-major
-  double* part;               // [gridDim.x][TN][TM] per-CTA unit partials, column-major
-  long long ldr;              // = n_m * TM
+  float2* slab;               // [gridDim.x][TN][NACC * TM] per-CTA (hi, lo), column-major
   int* status;
   long long np;
-  int ldc;                    // = n_n * TN
+  long long ldr;              // = n_st * NACC * TM
+  int gpad;
   int rows_valid;             // 2 * row pairs
   int cols_valid;             // 2 * nwi
-  int n_m, n_n, n_split;
+  int n_st, n_n, n_split;
   long long k_per_split;      // multiple of KS
   int flush;                  // stages per accumulator period
   float eta, sA, sB;
@@ -95,27 +107,43 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait with a suspend-time hint: the warp sleeps in hardware until the phase completes or
+// about `hint_ns` passes, instead of spinning on the issue slots.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t* b, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: false when this CTA is aborting or the wait ran out (then it starts the abort).
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
                                           int* status) {
-  unsigned long long t0 = 0;
-  uint32_t n = 0;
-  while (!mbar_try(b, parity)) {
+  if (mbar_try(b, parity)) return true;
+  const unsigned long long t0 = gtime();
+  while (!mbar_try_sleep(b, parity, 20000u)) {
     if (*abort_flag) return false;
-    if ((++n & 255u) == 0) {
-      unsigned long long t = gtime();
-      if (t0 == 0) {
-        t0 = t;
-      } else if (t - t0 > kTimeoutNs) {
-        *abort_flag = 1;
-        atomicOr(status, 2);
-        return false;
-      }
+    if (gtime() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      atomicOr(status, 2);
+      return false;
     }
   }
   return true;
 }
-
+// Bounded wait used while draining: ignores the abort flag.
+__device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity, int* status) {
+  const unsigned long long t0 = gtime();
+  while (!mbar_try_sleep(b, parity, 20000u)) {
+    if (gtime() - t0 > kTimeoutNs) {
+      atomicOr(status, 2);
+      return;
+    }
+  }
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
                    smem_u32(b)),
@@ -131,7 +159,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -205,20 +232,22 @@ struct Pack<true> {
   }
 };
 
+// No memory clobber: the operand tiles are read only by the tensor cores after the
+// fence.proxy.async + mbarrier arrive that follow (volatile asm keeps that order), so the
+// compiler may hoist the next chunk's loads above these stores.
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
-               "r"(v.w)
-               : "memory");
+               "r"(v.w));
 }
 
 struct Unit {
-  int mt, nt;
+  int st, nt;
   long long kb, ke;
 };
 __device__ __forceinline__ Unit unit_of(const Params& P, int u) {
   Unit U;
   int tile = u / P.n_split, ks = u % P.n_split;
-  U.mt = tile / P.n_n;
+  U.st = tile / P.n_n;
   U.nt = tile % P.n_n;
   U.kb = (long long)ks * P.k_per_split;
   U.ke = min(P.np, U.kb + P.k_per_split);
@@ -228,12 +257,12 @@ __device__ __forceinline__ Unit unit_of(const Params& P, int u) {
 template <bool BF>
 __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], final_bar;
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full, acc_empty, final_bar;
   __shared__ __align__(8) uint64_t rfull[NSR], rempty[NSR];
   __shared__ uint32_t tmem_base_s;
-  __shared__ int2 rowtab_s[64];
-  __shared__ int gl_s[RROWS];
-  __shared__ int ngl_s;
+  __shared__ int2 rowtab_s[NACC * 64];
+  __shared__ int blk_s[MAXBLK];
+  __shared__ int nblk_s;
   __shared__ float2 wtab_s[128];
   __shared__ volatile int abort_s;
 
@@ -252,10 +281,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       mbar_init(&rfull[s], 1);
       mbar_init(&rempty[s], NPROD);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
-    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, 4);
     mbar_init(&final_bar, 1);
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -263,30 +290,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   if (warp == WMMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_s)),
-                 "r"(2 * TN));
+                 "r"(NACC * TN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
-  const int nunits = P.n_m * P.n_n * P.n_split;
+  const int nunits = P.n_st * P.n_n * P.n_split;
   const uint32_t idesc = (1u << 4) | ((BF ? 1u : 0u) << 7) | ((BF ? 1u : 0u) << 10) | (1u << 15) |
                          (1u << 16) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
-  uint32_t it = 0;   // stage counter (producers and MMA)
+  uint32_t it = 0;   // stage counter (producers, loader, MMA)
   uint32_t pc = 0;   // accumulator period counter (MMA and epilogue)
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const Unit U = unit_of(P, u);
-    // per-unit tables (row pairs of the row tile, frequencies of the column tile)
+    // per-unit tables (row pairs and G blocks of the super-tile, frequencies of the column tile)
     __syncthreads();
-    if (threadIdx.x < 64) rowtab_s[threadIdx.x] = P.rowtab[U.mt * 64 + threadIdx.x];
+    if (threadIdx.x < NACC * 64) rowtab_s[threadIdx.x] = P.rowtab[U.st * NACC * 64 + threadIdx.x];
     if (threadIdx.x < 128) wtab_s[threadIdx.x] = P.wtab[U.nt * 128 + threadIdx.x];
-    if (threadIdx.x < RROWS) gl_s[threadIdx.x] = P.gl[U.mt * RROWS + threadIdx.x];
+    if (threadIdx.x < MAXBLK) blk_s[threadIdx.x] = P.blk[U.st * MAXBLK + threadIdx.x];
     if (threadIdx.x == 0) {
       int n = 0;
-      while (n < RROWS && P.gl[U.mt * RROWS + n] >= 0) ++n;
-      ngl_s = n;
+      while (n < MAXBLK && P.blk[U.st * MAXBLK + n] >= 0) ++n;
+      nblk_s = n;
     }
     __syncthreads();
     if (abort_s) break;
@@ -297,54 +324,63 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       // ---------------- producers ----------------
       for (long long st = 0; st < nstage; ++st, ++it) {
         const int s = it % NS, sr = it % NSR;
-        if (!mbar_wait(&rfull[sr], (it / NSR) & 1, &abort_s, P.status)) break;
-        if (!mbar_wait(&empty[s], ((it / NS) & 1) ^ 1, &abort_s, P.status)) break;
+        // every lane waits; the vote keeps the warp together if one lane's wait gives up
+        if (!__all_sync(0xffffffffu, mbar_wait(&rfull[sr], (it / NSR) & 1, &abort_s, P.status)))
+          break;
+        if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ((it / NS) & 1) ^ 1, &abort_s, P.status)))
+          break;
         const long long p = U.kb + st * KS + lane;
         const bool valid = p < U.ke;
         const float2* rrow = reinterpret_cast<const float2*>(rbase_gen + sr * R_STAGE) + lane;
         const float4* rpw =
-            reinterpret_cast<const float4*>(rbase_gen + sr * R_STAGE + RROWS * RROW_BYTES);
-        float4 pw = valid ? rpw[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const uint32_t sA_hi = base + s * STAGE_BYTES, sA_lo = sA_hi + A_BYTES;
-        const uint32_t sB_hi = sA_lo + A_BYTES, sB_lo = sB_hi + B_BYTES;
-#pragma unroll 1
-        for (int cc = 0; cc < 6; ++cc) {
-          const int c = warp * 6 + cc;   // 0..15 A chunks, 16..47 B chunks
-          float v[8];
-          if (c < 16) {
+            reinterpret_cast<const float4*>(rbase_gen + sr * R_STAGE + RROWS * KS * 8);
+        const float4 pw = valid ? rpw[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t sst = base + s * STAGE_BYTES;
+        if (warp < 8) {
+#pragma unroll
+          for (int cc = 0; cc < CHUNKS; ++cc) {
+            const int c = CHUNKS * warp + cc;        // 0..31: row tile c/16, chunk c%16
+            const int a = c >> 4, cl = c & 15;
+            float v[8];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-              int2 g = rowtab_s[4 * c + i];
+              const int2 g = rowtab_s[a * 64 + 4 * cl + i];
               float pr = 0.f, pi = 0.f;
               if (valid && g.x >= 0) {
-                float2 a = rrow[g.x * KS];
-                float2 b = rrow[g.y * KS];
-                pr = (a.x * b.x + a.y * b.y) * P.sA;
-                pi = (a.y * b.x - a.x * b.y) * P.sA;
+                const float2 x = rrow[g.x * KS];
+                const float2 y = rrow[g.y * KS];
+                pr = (x.x * y.x + x.y * y.y) * P.sA;
+                pi = (x.y * y.x - x.x * y.y) * P.sA;
               }
               v[2 * i] = pr;
               v[2 * i + 1] = pi;
             }
             uint4 hi, lo;
             Pack<BF>::split(v, hi, lo);
-            st_shared_v4(sA_hi + mn_chunk(lane, c, A_SBO), hi);
-            st_shared_v4(sA_lo + mn_chunk(lane, c, A_SBO), lo);
-          } else {
-            const int cb = c - 16;
-            const float dfs = pw.z * P.sB;
+            const uint32_t ahi = sst + a * 2 * A_BYTES;
+            st_shared_v4(ahi + mn_chunk(lane, cl, A_SBO), hi);
+            st_shared_v4(ahi + A_BYTES + mn_chunk(lane, cl, A_SBO), lo);
+          }
+        } else {
+          const float dfs = pw.z * P.sB;
+#pragma unroll
+          for (int cc = 0; cc < CHUNKS; ++cc) {
+            const int cb = CHUNKS * (warp - 8) + cc;  // 0..31: columns 8 cb ..
+            float v[8];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-              float2 w = wtab_s[4 * cb + i];
-              float x = (w.x + pw.x) + (w.y + pw.y);
-              float d = fmaf(x, x, P.eta * P.eta);
-              float sc = __fdividef(dfs, d);
+              const float2 w = wtab_s[4 * cb + i];
+              const float x = (w.x + pw.x) + (w.y + pw.y);
+              const float d = fmaf(x, x, P.eta * P.eta);
+              const float sc = __fdividef(dfs, d);
               v[2 * i] = sc * x;
               v[2 * i + 1] = -sc * P.eta;
             }
             uint4 hi, lo;
             Pack<BF>::split(v, hi, lo);
-            st_shared_v4(sB_hi + mn_chunk(lane, cb, B_SBO), hi);
-            st_shared_v4(sB_lo + mn_chunk(lane, cb, B_SBO), lo);
+            const uint32_t bhi = sst + NACC * 2 * A_BYTES;
+            st_shared_v4(bhi + mn_chunk(lane, cb, B_SBO), hi);
+            st_shared_v4(bhi + B_BYTES + mn_chunk(lane, cb, B_SBO), lo);
           }
         }
         fence_async_smem();
@@ -355,33 +391,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
         }
       }
     } else if (warp == WLOAD) {
-      // ---------------- loader: rho rows and pair weights of each stage ----------------
+      // ---------------- loader: rho blocks and pair weights of each stage ----------------
       if (lane == 0) {
-        const int ngl = ngl_s;
-        const uint32_t bytes = (uint32_t)(ngl * RROW_BYTES + KS * 16);
+        const int nb = nblk_s;
+        const uint32_t bytes = (uint32_t)(nb * RBLK_BYTES + KS * 16);
         for (long long st = 0; st < nstage; ++st, ++it) {
           const int sr = it % NSR;
           if (!mbar_wait(&rempty[sr], ((it / NSR) & 1) ^ 1, &abort_s, P.status)) break;
           const long long p0 = U.kb + st * KS;
           mbar_expect_tx(&rfull[sr], bytes);
           const uint32_t dst = rbase + sr * R_STAGE;
-          for (int i = 0; i < ngl; ++i)
-            bulk_g2s(dst + i * RROW_BYTES, P.rho + (size_t)gl_s[i] * P.ld_rho + p0, RROW_BYTES,
-                     &rfull[sr]);
-          bulk_g2s(dst + RROWS * RROW_BYTES, P.pw + p0, KS * 16, &rfull[sr]);
+          const float2* src = P.rho + (size_t)(p0 >> 5) * P.gpad * KS;
+          for (int i = 0; i < nb; ++i)
+            bulk_g2s(dst + i * RBLK_BYTES, src + (size_t)blk_s[i] * GBLK * KS, RBLK_BYTES, &rfull[sr]);
+          bulk_g2s(dst + RROWS * KS * 8, P.pw + p0, KS * 16, &rfull[sr]);
         }
       }
       it = __shfl_sync(0xffffffffu, it, 0);
     } else if (warp == WMMA) {
       // ---------------- MMA issuer ----------------
       for (long long per = 0; per < nper; ++per, ++pc) {
-        const uint32_t b = pc & 1;
         bool ok = true;
-        if (lane == 0) ok = mbar_wait(&acc_empty[b], ((pc >> 1) & 1) ^ 1, &abort_s, P.status);
+        if (lane == 0) ok = mbar_wait(&acc_empty, (pc & 1) ^ 1, &abort_s, P.status);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t d = tmem + b * TN;
         const long long s0 = per * P.flush, s1 = min(nstage, s0 + P.flush);
         for (long long st = s0; st < s1; ++st, ++it) {
           const int s = it % NS;
@@ -390,40 +424,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
           if (!ok) break;
           tc_fence_after();
           if (lane == 0) {
-            const uint32_t aH = base + s * STAGE_BYTES, aL = aH + A_BYTES;
-            const uint32_t bH = aL + A_BYTES, bL = bH + B_BYTES;
+            const uint32_t sst = base + s * STAGE_BYTES;
+            const uint32_t bH = sst + NACC * 2 * A_BYTES, bL = bH + B_BYTES;
 #pragma unroll
             for (int kk = 0; kk < KS / 16; ++kk) {
-              const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
-              const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
               const uint64_t dBh = sdesc(bH + kk * 2 * B_SBO, 1024, B_SBO);
               const uint64_t dBl = sdesc(bL + kk * 2 * B_SBO, 1024, B_SBO);
-              mma(d, dAh, dBh, idesc, (st > s0 || kk > 0) ? 1u : 0u);
-              mma(d, dAh, dBl, idesc, 1u);
-              mma(d, dAl, dBh, idesc, 1u);
+#pragma unroll
+              for (int a = 0; a < NACC; ++a) {
+                const uint32_t aH = sst + a * 2 * A_BYTES, aL = aH + A_BYTES;
+                const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
+                const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
+                const uint32_t d = tmem + a * TN;
+                mma(d, dAh, dBh, idesc, (st > s0 || kk > 0) ? 1u : 0u);
+                mma(d, dAh, dBl, idesc, 1u);
+                mma(d, dAl, dBh, idesc, 1u);
+              }
             }
             mma_commit(&empty[s]);
           }
           __syncwarp();
         }
         if (!ok) break;
-        if (lane == 0) mma_commit(&acc_full[b]);
+        if (lane == 0) mma_commit(&acc_full);
         __syncwarp();
       }
     } else {
       // ---------------- epilogue ----------------
-      // The unit's FP64 sums live in a private column-major slab of global memory (one row per
-      // lane: a warp touches 32 consecutive doubles per column) and are added into C once, when
-      // the unit's pair range is done.
+      // The unit's sums live in a per-CTA column-major slab of (hi, lo) float pairs
+      // (double-float, two-sum accumulation; a warp touches 32 consecutive rows per column)
+      // and are added into the FP64 sums C when the unit's pair range is done.
       const int q = warp & 3;            // tensor-memory lane quadrant of this warp
-      const int row = q * 32 + lane;
-      const long long grow = (long long)U.mt * TM + row;
-      double* part = P.part + (size_t)blockIdx.x * TM * TN + row;
+      float2* slab = P.slab + (size_t)blockIdx.x * TN * (NACC * TM);
       bool unit_ok = true;
       for (long long per = 0; per < nper; ++per, ++pc) {
-        const uint32_t b = pc & 1;
         bool ok = true;
-        if (lane == 0) ok = mbar_wait(&acc_full[b], (pc >> 1) & 1, &abort_s, P.status);
+        if (lane == 0) ok = mbar_wait(&acc_full, pc & 1, &abort_s, P.status);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           unit_ok = false;
@@ -431,37 +467,53 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
         }
         tc_fence_after();
 #pragma unroll 1
-        for (int c = 0; c < TN / 32; ++c) {
-          uint32_t r[32];
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + b * TN + c * 32;
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-              "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
-                "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                "=r"(r[30]), "=r"(r[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          double* slab = part + (size_t)(c * 32) * TM;
-          if (per == 0) {
+        for (int a = 0; a < NACC; ++a) {
+          const int row = a * TM + q * 32 + lane;
+#pragma unroll 1
+          for (int c = 0; c < TN / 16; ++c) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + c * 16;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                "%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float2* col = slab + (size_t)(c * 16) * (NACC * TM) + row;
+            if (per == 0) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) slab[(size_t)j * TM] = (double)__uint_as_float(r[j]);
-          } else {
+              for (int j = 0; j < 16; ++j)
+                col[(size_t)j * (NACC * TM)] = make_float2(__uint_as_float(r[j]), 0.f);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) slab[(size_t)j * TM] += (double)__uint_as_float(r[j]);
+              for (int j = 0; j < 16; ++j) {
+                float2 h = col[(size_t)j * (NACC * TM)];
+                const float v = __uint_as_float(r[j]);
+                const float s = h.x + v;                 // two-sum of h.x + v
+                const float bp = s - h.x;
+                const float err = (h.x - (s - bp)) + (v - bp);
+                col[(size_t)j * (NACC * TM)] = make_float2(s, h.y + err);
+              }
+            }
           }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[b]);
+        if (lane == 0) mbar_arrive(&acc_empty);
       }
-      if (unit_ok && grow < P.rows_valid) {
+      if (unit_ok) {
         const int col0 = U.nt * TN;
-        for (int j = 0; j < TN && col0 + j < P.cols_valid; ++j)
-          atomicAdd(P.C + (size_t)(col0 + j) * P.ldr + grow, part[(size_t)j * TM]);
+        for (int a = 0; a < NACC; ++a) {
+          const int row = a * TM + q * 32 + lane;
+          const long long grow = (long long)U.st * (NACC * TM) + row;
+          if (grow >= P.rows_valid) continue;
+          for (int j = 0; j < TN && col0 + j < P.cols_valid; ++j) {
+            const float2 h = slab[(size_t)j * (NACC * TM) + row];
+            atomicAdd(P.C + (size_t)(col0 + j) * P.ldr + grow, (double)h.x + (double)h.y);
+          }
+        }
       }
     }
     // keep every role on the same unit; an abort stops all of them
@@ -470,26 +522,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   // drain: the loader waits (bounded) for its last bulk copies, the MMA warp for this CTA's
   // MMAs, before the shared and tensor memory go away
   if (warp == WLOAD && lane == 0) {
-    for (uint32_t j = (it > (uint32_t)NSR ? it - NSR : 0u); j < it; ++j) {
-      unsigned long long t0 = gtime();
-      while (!mbar_try(&rfull[j % NSR], (j / NSR) & 1)) {
-        if (gtime() - t0 > kTimeoutNs) {
-          atomicOr(P.status, 2);
-          break;
-        }
-      }
-    }
+    for (uint32_t j = (it > (uint32_t)NSR ? it - NSR : 0u); j < it; ++j)
+      mbar_drain(&rfull[j % NSR], (j / NSR) & 1, P.status);
   }
   if (warp == WMMA) {
     if (lane == 0) {
       mma_commit(&final_bar);
-      unsigned long long t0 = gtime();
-      while (!mbar_try(&final_bar, 0)) {
-        if (gtime() - t0 > kTimeoutNs) {
-          atomicOr(P.status, 2);
-          break;
-        }
-      }
+      mbar_drain(&final_bar, 0, P.status);
     }
     __syncwarp();
   }
@@ -497,8 +536,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   __syncthreads();
   tc_fence_after();
   if (warp == WMMA)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN));
-  (void)base_gen;
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TN));
 }
 
 // chi0[w][G][G'] from the FP64 sums (C column-major: C[col * ldr + row])
@@ -524,7 +562,7 @@ __global__ void chi0_unpack(const double* __restrict__ C, long long ldr,
 }
 
 // {Delta_hi, Delta_lo, df, 0} per pair (Delta split so that w + Delta keeps FP64-level
-// accuracy when it cancels in FP32)
+// accuracy when it cancels in FP32); df carries the band weights.
 __global__ void pair_weights_split(const double* __restrict__ eps, const double* __restrict__ occ,
                                    const double* __restrict__ wgt, int nk, int nb,
                                    float4* __restrict__ pw) {
@@ -542,54 +580,55 @@ __global__ void pair_weights_split(const double* __restrict__ eps, const double*
   }
 }
 
-struct Plan {
-  int nG = -1, nwi = -1;
-  int n_m = 0, n_n = 0, rows_valid = 0;
-  int* rowtab = nullptr;
-  int* rp_of = nullptr;
-  float2* wtab = nullptr;
-};
-
 }  // namespace
 
 lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   const int nG = q.nG;
-  // row pairs (G <= G') in 8 x 8 blocks so that a tile touches few G
+  if (c->np <= 0) {
+    set_error("no pairs to contract");
+    return LRT_EINVAL;
+  }
+  if (c->rho_gpad < (nG + GBLK - 1) / GBLK * GBLK) {
+    set_error("pair densities are not in the blocked layout");
+    return LRT_ESTATE;
+  }
+  // row pairs (G <= G') in 8 x 8 blocks so that a row tile touches few G blocks
   std::vector<int2> pairs;
-  const int nblk = (nG + 7) / 8;
+  const int nblk = (nG + GBLK - 1) / GBLK;
   for (int I = 0; I < nblk; ++I)
     for (int J = I; J < nblk; ++J)
-      for (int a = I * 8; a < std::min(nG, I * 8 + 8); ++a)
-        for (int b = J * 8; b < std::min(nG, J * 8 + 8); ++b)
+      for (int a = I * GBLK; a < std::min(nG, I * GBLK + GBLK); ++a)
+        for (int b = J * GBLK; b < std::min(nG, J * GBLK + GBLK); ++b)
           if (I < J || a <= b) pairs.push_back(make_int2(a, b));
   const int npairs = (int)pairs.size();
-  const int n_m = (npairs + 63) / 64;
-  std::vector<int2> rowtab((size_t)n_m * 64, make_int2(-1, -1));
-  std::vector<int> gl((size_t)n_m * RROWS, -1);
+  const int per_st = NACC * 64;                       // row pairs per super-tile
+  const int n_st = (npairs + per_st - 1) / per_st;
+  std::vector<int2> rowtab((size_t)n_st * per_st, make_int2(-1, -1));
+  std::vector<int> blk((size_t)n_st * MAXBLK, -1);
   std::vector<int> rp_of((size_t)nG * nG);
   for (int i = 0; i < npairs; ++i) {
     rp_of[pairs[i].x * nG + pairs[i].y] = i;
     rp_of[pairs[i].y * nG + pairs[i].x] = i;
   }
-  // per row tile: the distinct G it touches (local indices into the prefetched rho rows)
-  for (int t = 0; t < n_m; ++t) {
-    int* g = &gl[(size_t)t * RROWS];
+  for (int t = 0; t < n_st; ++t) {
+    int* bl = &blk[(size_t)t * MAXBLK];
     int n = 0;
-    auto local = [&](int G) {
+    auto slot = [&](int G) {
+      const int b = G / GBLK;
       for (int i = 0; i < n; ++i)
-        if (g[i] == G) return i;
-      if (n == RROWS) return -1;
-      g[n] = G;
-      return n++;
+        if (bl[i] == b) return i * GBLK + G % GBLK;
+      if (n == MAXBLK) return -1;
+      bl[n] = b;
+      return (n++) * GBLK + G % GBLK;
     };
-    for (int r = 0; r < 64 && t * 64 + r < npairs; ++r) {
-      const int2 pr = pairs[t * 64 + r];
-      int a = local(pr.x), b = local(pr.y);
-      if (a < 0 || b < 0) {
-        set_error("a row tile touches more than 32 distinct G");
+    for (int r = 0; r < per_st && t * per_st + r < npairs; ++r) {
+      const int2 pr = pairs[t * per_st + r];
+      const int la = slot(pr.x), lb = slot(pr.y);
+      if (la < 0 || lb < 0) {
+        set_error("a row super-tile touches more than 6 G blocks");
         return LRT_EUNSUPPORTED;
       }
-      rowtab[(size_t)t * 64 + r] = make_int2(a, b);
+      rowtab[(size_t)t * per_st + r] = make_int2(la, lb);
     }
   }
   const int ncols = 2 * c->nwi;
@@ -608,12 +647,13 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   int dev = 0, nsm = 0;
   LRT_CUDA(cudaGetDevice(&dev));
   LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const long long tiles = (long long)n_m * n_n;
+  const long long tiles = (long long)n_st * n_n;
   // pair splits: at least 4 units per SM, chosen to fill the last round
   long long best_split = 1;
   double best_eff = 0.0;
   const long long max_split = std::max<long long>(1, c->np / (KS * 64));
-  for (long long sp = std::max<long long>(1, (4LL * nsm + tiles - 1) / tiles); sp <= 8LL * nsm / std::max<long long>(1, tiles) + 8 && sp <= max_split; ++sp) {
+  for (long long sp = std::max<long long>(1, (4LL * nsm + tiles - 1) / tiles);
+       sp <= 8LL * nsm / std::max<long long>(1, tiles) + 8 && sp <= max_split; ++sp) {
     long long units = tiles * sp;
     double eff = (double)units / (double)(((units + nsm - 1) / nsm) * nsm);
     if (eff > best_eff + 1e-9) {
@@ -625,12 +665,12 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   kps = (kps + KS - 1) / KS * KS;
   const int n_split = (int)((c->np + kps - 1) / kps);
 
-  // device tables and buffers: C (column-major FP64 sums) followed by the per-CTA slabs
-  const long long ldr = (long long)n_m * TM;
+  // device buffers: C (column-major FP64 sums) then the per-CTA slabs
+  const long long ldr = (long long)n_st * NACC * TM;
   const long long units = tiles * n_split;
   const int grid = (int)std::min<long long>(nsm, units);
   const size_t c_bytes = (size_t)ldr * ldc * sizeof(double);
-  const size_t need = c_bytes + (size_t)grid * TM * TN * sizeof(double);
+  const size_t need = c_bytes + (size_t)grid * TN * NACC * TM * sizeof(float2);
   DeviceWork& dw = const_cast<DeviceWork&>(c->dw);
   if (dw.scratch_bytes < need) {
     cudaFree(dw.scratch);
@@ -640,20 +680,20 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
     dw.scratch_bytes = need;
   }
   int2* d_rowtab = nullptr;
-  int* d_gl = nullptr;
+  int* d_blk = nullptr;
   int* d_rp = nullptr;
   float2* d_wtab = nullptr;
   float4* d_pw = nullptr;
   // pair weights padded to whole 32-pair stages (the bulk copies read full stages)
   const size_t npw_pad = (size_t)((c->np + KS - 1) / KS * KS);
   LRT_CUDA(cudaMallocAsync(&d_rowtab, rowtab.size() * sizeof(int2), s));
-  LRT_CUDA(cudaMallocAsync(&d_gl, gl.size() * sizeof(int), s));
+  LRT_CUDA(cudaMallocAsync(&d_blk, blk.size() * sizeof(int), s));
   LRT_CUDA(cudaMallocAsync(&d_rp, rp_of.size() * sizeof(int), s));
   LRT_CUDA(cudaMallocAsync(&d_wtab, wtab.size() * sizeof(float2), s));
   LRT_CUDA(cudaMallocAsync(&d_pw, npw_pad * sizeof(float4), s));
   LRT_CUDA(cudaMemsetAsync(d_pw, 0, npw_pad * sizeof(float4), s));
   LRT_CUDA(cudaMemcpyAsync(d_rowtab, rowtab.data(), rowtab.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-  LRT_CUDA(cudaMemcpyAsync(d_gl, gl.data(), gl.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  LRT_CUDA(cudaMemcpyAsync(d_blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   LRT_CUDA(cudaMemcpyAsync(d_rp, rp_of.data(), rp_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   LRT_CUDA(cudaMemcpyAsync(d_wtab, wtab.data(), wtab.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
   pair_weights_split<<<4 * nsm, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, d_pw);
@@ -664,18 +704,17 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   P.rho = (const float2*)dw.rho;
   P.pw = d_pw;
   P.rowtab = d_rowtab;
-  P.gl = d_gl;
-  P.ld_rho = c->rho_ld;
+  P.blk = d_blk;
   P.wtab = d_wtab;
   P.C = dw.scratch;
-  P.part = dw.scratch + (size_t)ldr * ldc;
-  P.ldr = ldr;
+  P.slab = reinterpret_cast<float2*>(dw.scratch + (size_t)ldr * ldc);
   P.status = dw.status;
   P.np = c->np;
-  P.ldc = ldc;
+  P.ldr = ldr;
+  P.gpad = c->rho_gpad;
   P.rows_valid = 2 * npairs;
   P.cols_valid = ncols;
-  P.n_m = n_m;
+  P.n_st = n_st;
   P.n_n = n_n;
   P.n_split = n_split;
   P.k_per_split = kps;
@@ -705,7 +744,7 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   count_launch(c);
   LRT_CUDA(cudaGetLastError());
   LRT_CUDA(cudaFreeAsync(d_rowtab, s));
-  LRT_CUDA(cudaFreeAsync(d_gl, s));
+  LRT_CUDA(cudaFreeAsync(d_blk, s));
   LRT_CUDA(cudaFreeAsync(d_rp, s));
   LRT_CUDA(cudaFreeAsync(d_wtab, s));
   LRT_CUDA(cudaFreeAsync(d_pw, s));

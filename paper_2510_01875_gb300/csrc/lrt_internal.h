@@ -47,7 +47,8 @@ struct QData {
 };
 
 struct DeviceWork {
-  void* rho = nullptr;            // [nGmax][np] complex (FP64 or FP32 by precision)
+  void* rho = nullptr;            // FP64 path: [nGmax][rho_ld] complex; split path: FP32
+                                  // complex blocked [rho_ld / 32][rho_gpad][32]
   size_t rho_bytes = 0;
   double* delta = nullptr;        // [np]
   double* df = nullptr;           // [np]
@@ -56,7 +57,7 @@ struct DeviceWork {
   double* S = nullptr;            // [nq][nw]
   double* chi00 = nullptr;        // [nq][nwi][2] gather of chi_00 for the spectra kernels
   int* status = nullptr;          // device status word (0 ok, bit 1 singular, bit 2 timeout)
-  double* scratch = nullptr;      // chi0 FP64 split-K partials (tensor path)
+  double* scratch = nullptr;      // tensor path: FP64 sums, then per-CTA double-float slabs
   size_t scratch_bytes = 0;
 };
 
@@ -93,8 +94,8 @@ struct lrt_ctx {
   int npw = 0;                    // padded plane-wave count (max over all k points)
   int nGmax = 0;
   int64_t np = 0;                 // pairs per q = nk nb^2
-  int64_t rho_ld = 0;             // row stride of rho[G][p]: np rounded up to 32 (256 B rows
-                                  // for bulk copies of 32-pair stages)
+  int64_t rho_ld = 0;             // np rounded up to 32 (whole 32-pair stages)
+  int rho_gpad = 0;               // split path: G count padded to 8 of the blocked rho layout
   std::vector<lrt::QData> qd;
   lrt::DeviceWork dw;
   bool have_S = false;

@@ -5,9 +5,10 @@
 // coefficients taken from an FFT of u*_nk u_n'k+q on the real-space grid (N_pw N_G is
 // 15-50x smaller at these cut-offs).
 //
-// Output layout: rho[G][p] with row stride ld (the pair count rounded up to 32), p = (k nb + n)
-// nb + n', so that the chi0 contraction streams a contiguous, 256-byte aligned run of pairs for
-// each G.
+// Output layout, p = (k nb + n) nb + n':
+//  FP64 path: rho[G][p] with row stride ld (the pair count rounded up to 32);
+//  split path: blocked rho[p / 32][G][p % 32] with G padded to a multiple of 8, so that the rows
+//  of one 8-G block for one 32-pair stage are a single contiguous 2 KB copy.
 #include "lrt_internal.h"
 
 namespace lrt {
@@ -32,7 +33,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) pair_density_kernel(
     const double2* __restrict__ ck, const double2* __restrict__ ckq,
     const int32_t* __restrict__ gather, int nk, int nb, int npw, int nG, int ntile, int64_t ld,
-    typename C2<R>::T* __restrict__ rho) {
+    int nGpad, typename C2<R>::T* __restrict__ rho) {
   using CT = typename C2<R>::T;
   __shared__ CT As[TK][TN];
   __shared__ CT Bs[TK][TN];
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(256) pair_density_kernel(
     }
     __syncthreads();
   }
-  CT* out = rho + (size_t)G * ld + (size_t)k * nb * nb;
+  const int64_t kbase = (int64_t)k * nb * nb;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     int n = n0 + ty + 16 * i;
@@ -92,7 +93,12 @@ __global__ void __launch_bounds__(256) pair_density_kernel(
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int m = m0 + tx + 16 * j;
-      if (m < nb) out[(size_t)n * nb + m] = CT{accr[i][j], acci[i][j]};
+      if (m >= nb) continue;
+      const int64_t p = kbase + (int64_t)n * nb + m;
+      // row layout rho[G][p] (nGpad == 0) or blocked rho[p / 32][G][p % 32]
+      const size_t idx = nGpad ? ((size_t)((p >> 5) * nGpad + G) << 5) + (size_t)(p & 31)
+                               : (size_t)G * ld + (size_t)p;
+      rho[idx] = CT{accr[i][j], acci[i][j]};
     }
   }
 }
@@ -125,10 +131,10 @@ lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool
     TimedLaunch tl(c, &c->ev_rho, s);
     if (fp32)
       pair_density_kernel<float><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw, q.nG,
-                                                      ntile, c->rho_ld, (float2*)rho);
+                                                      ntile, c->rho_ld, c->rho_gpad, (float2*)rho);
     else
       pair_density_kernel<double><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw,
-                                                       q.nG, ntile, c->rho_ld, (double2*)rho);
+                                                       q.nG, ntile, c->rho_ld, 0, (double2*)rho);
   }
   count_launch(c);
   LRT_CUDA(cudaGetLastError());

@@ -668,6 +668,7 @@ lrt_status solve_ground_states(lrt_ctx* c, const double* occupations) {
   }
   c->np = (int64_t)nk * c->nb * c->nb;
   c->rho_ld = (c->np + 31) / 32 * 32;
+  c->rho_gpad = (c->precision == LRT_PREC_FP64) ? 0 : (c->nGmax + 7) / 8 * 8;
   return LRT_OK;
 }
 
