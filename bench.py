@@ -276,7 +276,9 @@ def run_ours(args, world, rank, local, pg):
             "config": {"workload": wl.name, "precision": args.precision, "nq": wl.nq,
                        "nk": ctx.nk, "nbands": ctx.nb, "nG": int(wl.nG[0]), "nw": wl.nw,
                        "np_per_q": ctx.nk * ctx.nb * ctx.nb, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (pair densities 11.8 GB per q)"},
+                       "l2": "inputs larger than L2 (pair densities %.2f GB per q)" % (
+                           ctx.nk * ctx.nb * ctx.nb * int(wl.nG[0])
+                           * (16 if args.precision == "fp64" else 8) / 1e9)},
             "q_spectra_per_s": sum_over_ranks(None, wl.nq * world) / (ms_max / 1e3),
             "setup_s": setup_s,
             "roofline": roofline,

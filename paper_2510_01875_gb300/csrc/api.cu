@@ -84,6 +84,9 @@ lrt_status ensure_rho(lrt_ctx* c) {
   c->dw.rho = nullptr;
   LRT_CUDA(cudaMalloc(&c->dw.rho, need));
   c->dw.rho_bytes = need;
+  // padding (pairs past the last one, G rows past nG) is never written and must read as zero
+  LRT_CUDA(cudaMemset(c->dw.rho, 0, need));
+  LRT_CUDA(cudaDeviceSynchronize());
   return LRT_OK;
 }
 

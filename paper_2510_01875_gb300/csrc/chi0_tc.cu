@@ -20,9 +20,9 @@
 //  - one thread issues tcgen05.mma kind::f16, M = 128, N = 256, K = 16, for
 //    A_hi B_hi + A_hi B_lo + A_lo B_hi into two FP32 accumulators in tensor memory (two row
 //    tiles share each B tile: 256 x 256 outputs per CTA);
-//  - every `flush` stages four epilogue warps read the accumulators (tcgen05.ld) and add them
-//    into a per-CTA double-float (FP32 hi + lo, two-sum) slab in global memory; at the end of
-//    a unit the slab is added into the FP64 sums C.
+//  - every `flush` stages four epilogue warps read the accumulators (tcgen05.ld), hand the
+//    tensor memory back and add the values into the FP64 sums C with reductions that return
+//    nothing (red.global.add.f64), so FP32 accumulation never spans more than one period.
 // Units of work are (row super-tile, column tile, pair range), handed out round-robin to one
 // CTA per SM.  Every wait on an mbarrier is bounded; on expiry the kernel sets bit 2 of the
 // status word, stops issuing work, waits (bounded) for its own copies and MMAs and frees its
@@ -59,18 +59,21 @@ constexpr int STAGE_BYTES = NACC * 2 * A_BYTES + 2 * B_BYTES;   // 64 KB
 constexpr int A_SBO = (TM / 64) * 1024;              // bytes between 8-pair groups of A
 constexpr int B_SBO = (TN / 64) * 1024;
 constexpr int RBLK_BYTES = GBLK * KS * 8;            // one G block of one stage: 2 KB
-constexpr int R_STAGE = RROWS * KS * 8 + KS * 16;    // rho rows + 32 float4 pair weights
+constexpr int PW_OFF = RROWS * KS * 8;               // pair weights after the rows
+constexpr int R_STAGE = PW_OFF + KS * 16;            // rho rows, 32 float4 pair weights
+constexpr int NSUB = NACC * 64 / 16;                 // 4 x 4 (G, G') sub-blocks per super-tile
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
-constexpr int kFlushStages = 128;  // FP32 accumulation period: 128 stages = 4096 pairs
+constexpr int kFlushStages = 64;   // FP32 accumulation period: 64 stages = 2048 pairs
+constexpr int NCHUNK = NACC * TN / 16;  // 16-column pieces of the accumulators per lane
 
 struct Params {
   const float2* rho;          // blocked [ld/32][gpad][32]
-  const float4* pw;           // [np rounded up to 32] {Delta_hi, Delta_lo, df, 0}
-  const int2* rowtab;         // [n_st * 128] local (G, G') indices per row pair, -1 padding
+  const float4* pw;           // [np rounded up to 32] {Delta_hi, Delta_lo, df sB, 0}
+  const int2* rowtab;         // [n_st * NSUB] ring rows of the G quads of each sub-block
   const int* blk;             // [n_st * MAXBLK] G blocks of the super-tile, -1 padding
-  const float2* wtab;         // [n_n * 128] frequency hi/lo per column pair
+  const float4* wtab;         // [n_n * 64] per frequency pair {hi_f, hi_f+1, lo_f, lo_f+1}
   double* C;                  // [n_n * TN][ldr] FP64 sums, column-major
-  float2* slab;               // [gridDim.x][TN][NACC * TM] per-CTA (hi, lo), column-major
+  float4* stage;              // [gridDim.x][4 warps][NCHUNK][4][32 lanes] accumulator staging
   int* status;
   long long np;
   long long ldr;              // = n_st * NACC * TM
@@ -80,7 +83,7 @@ struct Params {
   int n_st, n_n, n_split;
   long long k_per_split;      // multiple of KS
   int flush;                  // stages per accumulator period
-  float eta, sA, sB;
+  float eta;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -206,8 +209,10 @@ struct Pack<false> {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       __half2 a = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
-      float2 af = __half22float2(a);
-      __half2 b = __floats2half2_rn(v[2 * i] - af.x, v[2 * i + 1] - af.y);
+      // v - hi, exact (one rounding of an exact difference)
+      const float2 rr = __ffma2_rn(__half22float2(a), make_float2(-1.f, -1.f),
+                                   make_float2(v[2 * i], v[2 * i + 1]));
+      __half2 b = __floats2half2_rn(rr.x, rr.y);
       h[i] = *reinterpret_cast<uint32_t*>(&a);
       l[i] = *reinterpret_cast<uint32_t*>(&b);
     }
@@ -222,8 +227,9 @@ struct Pack<true> {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       __nv_bfloat162 a = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-      float2 af = __bfloat1622float2(a);
-      __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i] - af.x, v[2 * i + 1] - af.y);
+      const float2 rr = __ffma2_rn(__bfloat1622float2(a), make_float2(-1.f, -1.f),
+                                   make_float2(v[2 * i], v[2 * i + 1]));
+      __nv_bfloat162 b = __floats2bfloat162_rn(rr.x, rr.y);
       h[i] = *reinterpret_cast<uint32_t*>(&a);
       l[i] = *reinterpret_cast<uint32_t*>(&b);
     }
@@ -238,6 +244,39 @@ struct Pack<true> {
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
                "r"(v.w));
+}
+
+// Add into global memory without a return value.
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// Single-instruction approximate reciprocal (relative error about 2^-23).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// Shared-memory loads with 32-bit addresses.  They are not volatile, so the compiler may
+// interleave the loads of several chunks; they are kept after the mbarrier wait that
+// publishes the data by adding stage_token() (an opaque zero produced after the wait) to
+// every address.
+__device__ __forceinline__ uint32_t stage_token() {
+  uint32_t t;
+  asm volatile("mov.u32 %0, 0;" : "=r"(t)::"memory");
+  return t;
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+  float2 v;
+  asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ float4 lds_f4(uint32_t addr) {
+  float4 v;
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "r"(addr));
+  return v;
 }
 
 struct Unit {
@@ -257,20 +296,18 @@ __device__ __forceinline__ Unit unit_of(const Params& P, int u) {
 template <bool BF>
 __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full, acc_empty, final_bar;
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full, acc_empty[NACC], final_bar;
   __shared__ __align__(8) uint64_t rfull[NSR], rempty[NSR];
   __shared__ uint32_t tmem_base_s;
-  __shared__ int2 rowtab_s[NACC * 64];
+  __shared__ int2 rowtab_s[NSUB];   // byte offsets of the two G quads of each A warp's sub-block
   __shared__ int blk_s[MAXBLK];
   __shared__ int nblk_s;
-  __shared__ float2 wtab_s[128];
+  __shared__ float4 wtab_s[64];
   __shared__ volatile int abort_s;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  uint8_t* base_gen = smem_raw + (base - smem_u32(smem_raw));
   const uint32_t rbase = base + NS * STAGE_BYTES;          // prefetch ring
-  const uint8_t* rbase_gen = base_gen + NS * STAGE_BYTES;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -282,7 +319,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       mbar_init(&rempty[s], NPROD);
     }
     mbar_init(&acc_full, 1);
-    mbar_init(&acc_empty, 4);
+    for (int a = 0; a < NACC; ++a) mbar_init(&acc_empty[a], 4);
     mbar_init(&final_bar, 1);
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -307,8 +344,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     const Unit U = unit_of(P, u);
     // per-unit tables (row pairs and G blocks of the super-tile, frequencies of the column tile)
     __syncthreads();
-    if (threadIdx.x < NACC * 64) rowtab_s[threadIdx.x] = P.rowtab[U.st * NACC * 64 + threadIdx.x];
-    if (threadIdx.x < 128) wtab_s[threadIdx.x] = P.wtab[U.nt * 128 + threadIdx.x];
+    if (threadIdx.x < NSUB) {
+      const int2 g = P.rowtab[U.st * NSUB + threadIdx.x];
+      rowtab_s[threadIdx.x] = make_int2(g.x * KS * 8, g.y * KS * 8);
+    }
+    if (threadIdx.x < 64) wtab_s[threadIdx.x] = P.wtab[U.nt * 64 + threadIdx.x];
     if (threadIdx.x < MAXBLK) blk_s[threadIdx.x] = P.blk[U.st * MAXBLK + threadIdx.x];
     if (threadIdx.x == 0) {
       int n = 0;
@@ -317,70 +357,91 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     }
     __syncthreads();
     if (abort_s) break;
-    const long long nstage = (U.ke - U.kb + KS - 1) / KS;
-    const long long nper = (nstage + P.flush - 1) / P.flush;
+    const int nstage = (int)((U.ke - U.kb + KS - 1) / KS);
+    const int nper = (nstage + P.flush - 1) / P.flush;
 
     if (warp < NPROD) {
       // ---------------- producers ----------------
-      for (long long st = 0; st < nstage; ++st, ++it) {
-        const int s = it % NS, sr = it % NSR;
+      // Lane = pair.  A warp w (0..7) owns the 4 x 4 sub-block (G quad a, G quad b) of rows
+      // 32 w .. 32 w + 31: chunk i holds the row pairs (4 a + i, 4 b + j), j = 0..3.  B warps
+      // (8..15) own 16 frequencies (4 chunks of 8 columns).  Padding pairs (beyond the last
+      // one) and padding G rows have zero pair densities and weights, so no masking is needed.
+      uint32_t sto[CHUNKS];   // shared-memory offsets of this lane's 16-byte chunks in a stage
+#pragma unroll
+      for (int cc = 0; cc < CHUNKS; ++cc) {
+        if (warp < 8) {
+          const int c = CHUNKS * warp + cc;
+          sto[cc] = (c >> 4) * 2 * A_BYTES + mn_chunk(lane, c & 15, A_SBO);
+        } else {
+          sto[cc] = NACC * 2 * A_BYTES + mn_chunk(lane, CHUNKS * (warp - 8) + cc, B_SBO);
+        }
+      }
+      const int2 ro = rowtab_s[warp & 7];                     // A warps
+      const float4* wt = wtab_s + 8 * (warp & 7);             // B warps: 8 frequency pairs
+      const float eta2 = P.eta * P.eta;
+      uint32_t s = it % NS, ph = (it / NS) & 1, sr = it % NSR, phr = (it / NSR) & 1;
+      for (int st = 0; st < nstage; ++st) {
         // every lane waits; the vote keeps the warp together if one lane's wait gives up
-        if (!__all_sync(0xffffffffu, mbar_wait(&rfull[sr], (it / NSR) & 1, &abort_s, P.status)))
-          break;
-        if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ((it / NS) & 1) ^ 1, &abort_s, P.status)))
-          break;
-        const long long p = U.kb + st * KS + lane;
-        const bool valid = p < U.ke;
-        const float2* rrow = reinterpret_cast<const float2*>(rbase_gen + sr * R_STAGE) + lane;
-        const float4* rpw =
-            reinterpret_cast<const float4*>(rbase_gen + sr * R_STAGE + RROWS * KS * 8);
-        const float4 pw = valid ? rpw[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!__all_sync(0xffffffffu, mbar_wait(&rfull[sr], phr, &abort_s, P.status))) break;
+        if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1, &abort_s, P.status))) break;
+        const uint32_t ring = rbase + sr * R_STAGE + stage_token();
         const uint32_t sst = base + s * STAGE_BYTES;
         if (warp < 8) {
+          // rho(4a + i) and rho(4b + j) of this lane's pair; x conj(y) as
+          // y.re (x.re, x.im) + y.im (x.im, -x.re) in packed FP32x2
+          const uint32_t ra = ring + lane * 8 + ro.x, rb = ring + lane * 8 + ro.y;
+          float2 X[4], Xr[4], Yr[4], Yi[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float2 x = lds_f2(ra + i * KS * 8), y = lds_f2(rb + i * KS * 8);
+            X[i] = x;
+            Xr[i] = make_float2(x.y, -x.x);
+            Yr[i] = make_float2(y.x, y.x);
+            Yi[i] = make_float2(y.y, y.y);
+          }
 #pragma unroll
           for (int cc = 0; cc < CHUNKS; ++cc) {
-            const int c = CHUNKS * warp + cc;        // 0..31: row tile c/16, chunk c%16
-            const int a = c >> 4, cl = c & 15;
             float v[8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int2 g = rowtab_s[a * 64 + 4 * cl + i];
-              float pr = 0.f, pi = 0.f;
-              if (valid && g.x >= 0) {
-                const float2 x = rrow[g.x * KS];
-                const float2 y = rrow[g.y * KS];
-                pr = (x.x * y.x + x.y * y.y) * P.sA;
-                pi = (x.y * y.x - x.x * y.y) * P.sA;
-              }
-              v[2 * i] = pr;
-              v[2 * i + 1] = pi;
+            for (int j = 0; j < 4; ++j) {
+              const float2 pv = __ffma2_rn(Yr[j], X[cc], __fmul2_rn(Yi[j], Xr[cc]));
+              v[2 * j] = pv.x;       // Re rho(G) rho*(G')
+              v[2 * j + 1] = pv.y;   // Im
             }
             uint4 hi, lo;
             Pack<BF>::split(v, hi, lo);
-            const uint32_t ahi = sst + a * 2 * A_BYTES;
-            st_shared_v4(ahi + mn_chunk(lane, cl, A_SBO), hi);
-            st_shared_v4(ahi + A_BYTES + mn_chunk(lane, cl, A_SBO), lo);
+            st_shared_v4(sst + sto[cc], hi);
+            st_shared_v4(sst + sto[cc] + A_BYTES, lo);
           }
         } else {
-          const float dfs = pw.z * P.sB;
+          // two frequencies per packed FP32x2 operation
+          const float4 pw = lds_f4(ring + PW_OFF + lane * 16);
+          const float2 dh = make_float2(pw.x, pw.x), dl = make_float2(pw.y, pw.y);
+          const float2 df = make_float2(pw.z, pw.z);
+          const float2 m = make_float2(-P.eta * pw.z, -P.eta * pw.z);
+          const float2 e2 = make_float2(eta2, eta2);
 #pragma unroll
           for (int cc = 0; cc < CHUNKS; ++cc) {
-            const int cb = CHUNKS * (warp - 8) + cc;  // 0..31: columns 8 cb ..
             float v[8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const float2 w = wtab_s[4 * cb + i];
-              const float x = (w.x + pw.x) + (w.y + pw.y);
-              const float d = fmaf(x, x, P.eta * P.eta);
-              const float sc = __fdividef(dfs, d);
-              v[2 * i] = sc * x;
-              v[2 * i + 1] = -sc * P.eta;
+            for (int h = 0; h < 2; ++h) {
+              const float4 w = wt[2 * cc + h];
+              // w + Delta from the hi and lo parts of both
+              const float2 x = __fadd2_rn(__fadd2_rn(make_float2(w.x, w.y), dh),
+                                          __fadd2_rn(make_float2(w.z, w.w), dl));
+              const float2 d = __ffma2_rn(x, x, e2);
+              const float2 r = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+              const float2 re = __fmul2_rn(__fmul2_rn(df, x), r);   // Re df / (x + i eta)
+              const float2 im = __fmul2_rn(m, r);                   // Im
+              v[4 * h] = re.x;
+              v[4 * h + 1] = im.x;
+              v[4 * h + 2] = re.y;
+              v[4 * h + 3] = im.y;
             }
             uint4 hi, lo;
             Pack<BF>::split(v, hi, lo);
-            const uint32_t bhi = sst + NACC * 2 * A_BYTES;
-            st_shared_v4(bhi + mn_chunk(lane, cb, B_SBO), hi);
-            st_shared_v4(bhi + B_BYTES + mn_chunk(lane, cb, B_SBO), lo);
+            st_shared_v4(sst + sto[cc], hi);
+            st_shared_v4(sst + sto[cc] + B_BYTES, lo);
           }
         }
         fence_async_smem();
@@ -389,49 +450,55 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
           mbar_arrive(&full[s]);
           mbar_arrive(&rempty[sr]);
         }
+        ++it;
+        if (++s == NS) { s = 0; ph ^= 1; }
+        if (++sr == NSR) { sr = 0; phr ^= 1; }
       }
     } else if (warp == WLOAD) {
       // ---------------- loader: rho blocks and pair weights of each stage ----------------
       if (lane == 0) {
         const int nb = nblk_s;
         const uint32_t bytes = (uint32_t)(nb * RBLK_BYTES + KS * 16);
-        for (long long st = 0; st < nstage; ++st, ++it) {
+        for (int st = 0; st < nstage; ++st, ++it) {
           const int sr = it % NSR;
           if (!mbar_wait(&rempty[sr], ((it / NSR) & 1) ^ 1, &abort_s, P.status)) break;
-          const long long p0 = U.kb + st * KS;
+          const long long p0 = U.kb + (long long)st * KS;
           mbar_expect_tx(&rfull[sr], bytes);
           const uint32_t dst = rbase + sr * R_STAGE;
           const float2* src = P.rho + (size_t)(p0 >> 5) * P.gpad * KS;
           for (int i = 0; i < nb; ++i)
             bulk_g2s(dst + i * RBLK_BYTES, src + (size_t)blk_s[i] * GBLK * KS, RBLK_BYTES, &rfull[sr]);
-          bulk_g2s(dst + RROWS * KS * 8, P.pw + p0, KS * 16, &rfull[sr]);
+          bulk_g2s(dst + PW_OFF, P.pw + p0, KS * 16, &rfull[sr]);
         }
       }
       it = __shfl_sync(0xffffffffu, it, 0);
     } else if (warp == WMMA) {
       // ---------------- MMA issuer ----------------
-      for (long long per = 0; per < nper; ++per, ++pc) {
-        bool ok = true;
-        if (lane == 0) ok = mbar_wait(&acc_empty, (pc & 1) ^ 1, &abort_s, P.status);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
-        tc_fence_after();
-        const long long s0 = per * P.flush, s1 = min(nstage, s0 + P.flush);
-        for (long long st = s0; st < s1; ++st, ++it) {
+      bool ok = true;
+      for (int per = 0; per < nper && ok; ++per, ++pc) {
+        const int s0 = per * P.flush, s1 = min(nstage, s0 + P.flush);
+        for (int st = s0; st < s1; ++st, ++it) {
           const int s = it % NS;
           if (lane == 0) ok = mbar_wait(&full[s], (it / NS) & 1, &abort_s, P.status);
           ok = __shfl_sync(0xffffffffu, ok, 0);
           if (!ok) break;
           tc_fence_after();
-          if (lane == 0) {
-            const uint32_t sst = base + s * STAGE_BYTES;
-            const uint32_t bH = sst + NACC * 2 * A_BYTES, bL = bH + B_BYTES;
+          const uint32_t sst = base + s * STAGE_BYTES;
+          const uint32_t bH = sst + NACC * 2 * A_BYTES, bL = bH + B_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < KS / 16; ++kk) {
-              const uint64_t dBh = sdesc(bH + kk * 2 * B_SBO, 1024, B_SBO);
-              const uint64_t dBl = sdesc(bL + kk * 2 * B_SBO, 1024, B_SBO);
+          for (int kk = 0; kk < KS / 16; ++kk) {
+            const uint64_t dBh = sdesc(bH + kk * 2 * B_SBO, 1024, B_SBO);
+            const uint64_t dBl = sdesc(bL + kk * 2 * B_SBO, 1024, B_SBO);
 #pragma unroll
-              for (int a = 0; a < NACC; ++a) {
+            for (int a = 0; a < NACC; ++a) {
+              if (st == s0 && kk == 0) {
+                // first use of accumulator a in this period: the epilogue must have read it
+                if (lane == 0) ok = mbar_wait(&acc_empty[a], (pc & 1) ^ 1, &abort_s, P.status);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+                tc_fence_after();
+              }
+              if (lane == 0) {
                 const uint32_t aH = sst + a * 2 * A_BYTES, aL = aH + A_BYTES;
                 const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
                 const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
@@ -440,9 +507,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
                 mma(d, dAh, dBl, idesc, 1u);
                 mma(d, dAl, dBh, idesc, 1u);
               }
+              __syncwarp();
             }
-            mma_commit(&empty[s]);
+            if (!ok) break;
           }
+          if (!ok) break;
+          if (lane == 0) mma_commit(&empty[s]);
           __syncwarp();
         }
         if (!ok) break;
@@ -451,67 +521,64 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       }
     } else {
       // ---------------- epilogue ----------------
-      // The unit's sums live in a per-CTA column-major slab of (hi, lo) float pairs
-      // (double-float, two-sum accumulation; a warp touches 32 consecutive rows per column)
-      // and are added into the FP64 sums C when the unit's pair range is done.
+      // Per period: (1) read the accumulators (tcgen05.ld) into a per-warp staging area in
+      // global memory with plain stores and hand each accumulator back as soon as it has been
+      // read; (2) while the next period runs, add the staged FP32 values into the FP64 sums C
+      // with reductions that return nothing (red.global.add.f64).  Each lane reads back only
+      // what it wrote.  C is column-major with ldr >= the super-tile rows and n_n * TN
+      // columns, so no bounds checks are needed (padding rows and columns collect values that
+      // are never read).
       const int q = warp & 3;            // tensor-memory lane quadrant of this warp
-      float2* slab = P.slab + (size_t)blockIdx.x * TN * (NACC * TM);
-      bool unit_ok = true;
-      for (long long per = 0; per < nper; ++per, ++pc) {
+      float4* stg = P.stage + ((size_t)blockIdx.x * 4 + q) * (NCHUNK * 4 * 32) + lane;
+      const long long grow0 = (long long)U.st * (NACC * TM) + q * 32 + lane;
+      double* cbase = P.C + (size_t)(U.nt * TN) * P.ldr;
+      for (int per = 0; per < nper; ++per, ++pc) {
         bool ok = true;
         if (lane == 0) ok = mbar_wait(&acc_full, pc & 1, &abort_s, P.status);
         ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) {
-          unit_ok = false;
-          break;
-        }
+        if (!ok) break;
         tc_fence_after();
 #pragma unroll 1
-        for (int a = 0; a < NACC; ++a) {
-          const int row = a * TM + q * 32 + lane;
-#pragma unroll 1
-          for (int c = 0; c < TN / 16; ++c) {
-            uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + c * 16;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-                "%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float2* col = slab + (size_t)(c * 16) * (NACC * TM) + row;
-            if (per == 0) {
+        for (int ch = 0; ch < NCHUNK; ++ch) {
+          const int a = ch / (TN / 16), c = ch % (TN / 16);
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + c * 16;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          float4* d = stg + (size_t)ch * 128;
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                col[(size_t)j * (NACC * TM)] = make_float2(__uint_as_float(r[j]), 0.f);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                float2 h = col[(size_t)j * (NACC * TM)];
-                const float v = __uint_as_float(r[j]);
-                const float s = h.x + v;                 // two-sum of h.x + v
-                const float bp = s - h.x;
-                const float err = (h.x - (s - bp)) + (v - bp);
-                col[(size_t)j * (NACC * TM)] = make_float2(s, h.y + err);
-              }
-            }
+          for (int k = 0; k < 4; ++k)
+            d[32 * k] = make_float4(__uint_as_float(r[4 * k]), __uint_as_float(r[4 * k + 1]),
+                                    __uint_as_float(r[4 * k + 2]), __uint_as_float(r[4 * k + 3]));
+          if (c == TN / 16 - 1) {
+            // accumulator a has been read: hand it back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[a]);
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty);
-      }
-      if (unit_ok) {
-        const int col0 = U.nt * TN;
-        for (int a = 0; a < NACC; ++a) {
-          const int row = a * TM + q * 32 + lane;
-          const long long grow = (long long)U.st * (NACC * TM) + row;
-          if (grow >= P.rows_valid) continue;
-          for (int j = 0; j < TN && col0 + j < P.cols_valid; ++j) {
-            const float2 h = slab[(size_t)j * (NACC * TM) + row];
-            atomicAdd(P.C + (size_t)(col0 + j) * P.ldr + grow, (double)h.x + (double)h.y);
+#pragma unroll 1
+        for (int ch = 0; ch < NCHUNK; ++ch) {
+          const int a = ch / (TN / 16), c = ch % (TN / 16);
+          const float4* sp = stg + (size_t)ch * 128;
+          float4 v[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[k] = sp[32 * k];
+          double* cp = cbase + (size_t)(c * 16) * P.ldr + grow0 + a * TM;
+          const size_t ldr = (size_t)P.ldr;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            red_add_f64(cp, (double)v[k].x);
+            red_add_f64(cp + ldr, (double)v[k].y);
+            red_add_f64(cp + 2 * ldr, (double)v[k].z);
+            red_add_f64(cp + 3 * ldr, (double)v[k].w);
+            cp += 4 * ldr;
           }
         }
       }
@@ -561,11 +628,11 @@ __global__ void chi0_unpack(const double* __restrict__ C, long long ldr,
   chi0[t] = make_double2(scale * v.x, scale * v.y);
 }
 
-// {Delta_hi, Delta_lo, df, 0} per pair (Delta split so that w + Delta keeps FP64-level
-// accuracy when it cancels in FP32); df carries the band weights.
+// {Delta_hi, Delta_lo, df sB, 0} per pair (Delta split so that w + Delta keeps FP64-level
+// accuracy when it cancels in FP32); df carries the band weights and the power-of-two scale sB.
 __global__ void pair_weights_split(const double* __restrict__ eps, const double* __restrict__ occ,
                                    const double* __restrict__ wgt, int nk, int nb,
-                                   float4* __restrict__ pw) {
+                                   float sB, float4* __restrict__ pw) {
   long long np = (long long)nk * nb * nb;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
        p += (long long)gridDim.x * blockDim.x) {
@@ -576,7 +643,7 @@ __global__ void pair_weights_split(const double* __restrict__ eps, const double*
     double d = eps[kn] - eps[ikq];
     float dh = (float)d;
     pw[p] = make_float4(dh, (float)(d - (double)dh),
-                        (float)(wgt[kn] * wgt[ikq] * (occ[kn] - occ[ikq])), 0.f);
+                        (float)(wgt[kn] * wgt[ikq] * (occ[kn] - occ[ikq]) * sB), 0.f);
   }
 }
 
@@ -592,54 +659,67 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
     set_error("pair densities are not in the blocked layout");
     return LRT_ESTATE;
   }
-  // row pairs (G <= G') in 8 x 8 blocks so that a row tile touches few G blocks
-  std::vector<int2> pairs;
+  // Row pairs in 4 x 4 sub-blocks of G quads (Qa <= Qb): sub-block row pair 4 i + j is
+  // (4 Qa + i, 4 Qb + j).  Sub-blocks are ordered by 8-G block pairs so that a super-tile of
+  // NSUB sub-blocks touches few G blocks.  In a diagonal sub-block (Qa == Qb) the six slots
+  // with i > j repeat pairs held by slots with i < j; like padding G, their rows are computed
+  // and never read.
+  const int nQ = (nG + 3) / 4;
   const int nblk = (nG + GBLK - 1) / GBLK;
+  std::vector<int2> sub;
   for (int I = 0; I < nblk; ++I)
     for (int J = I; J < nblk; ++J)
-      for (int a = I * GBLK; a < std::min(nG, I * GBLK + GBLK); ++a)
-        for (int b = J * GBLK; b < std::min(nG, J * GBLK + GBLK); ++b)
-          if (I < J || a <= b) pairs.push_back(make_int2(a, b));
-  const int npairs = (int)pairs.size();
-  const int per_st = NACC * 64;                       // row pairs per super-tile
-  const int n_st = (npairs + per_st - 1) / per_st;
-  std::vector<int2> rowtab((size_t)n_st * per_st, make_int2(-1, -1));
+      for (int qa = 2 * I; qa < std::min(nQ, 2 * I + 2); ++qa)
+        for (int qb = 2 * J; qb < std::min(nQ, 2 * J + 2); ++qb)
+          if (qa <= qb) sub.push_back(make_int2(qa, qb));
+  const int nsub = (int)sub.size();
+  const int n_st = (nsub + NSUB - 1) / NSUB;
+  std::vector<int2> rowtab((size_t)n_st * NSUB, make_int2(0, 0));
   std::vector<int> blk((size_t)n_st * MAXBLK, -1);
-  std::vector<int> rp_of((size_t)nG * nG);
-  for (int i = 0; i < npairs; ++i) {
-    rp_of[pairs[i].x * nG + pairs[i].y] = i;
-    rp_of[pairs[i].y * nG + pairs[i].x] = i;
-  }
+  std::vector<int> rp_of((size_t)nG * nG, 0);
   for (int t = 0; t < n_st; ++t) {
     int* bl = &blk[(size_t)t * MAXBLK];
     int n = 0;
-    auto slot = [&](int G) {
-      const int b = G / GBLK;
+    auto slot = [&](int q) {   // ring row of the first G of quad q
+      const int b = q / 2;
       for (int i = 0; i < n; ++i)
-        if (bl[i] == b) return i * GBLK + G % GBLK;
+        if (bl[i] == b) return i * GBLK + 4 * (q % 2);
       if (n == MAXBLK) return -1;
       bl[n] = b;
-      return (n++) * GBLK + G % GBLK;
+      return (n++) * GBLK + 4 * (q % 2);
     };
-    for (int r = 0; r < per_st && t * per_st + r < npairs; ++r) {
-      const int2 pr = pairs[t * per_st + r];
-      const int la = slot(pr.x), lb = slot(pr.y);
+    for (int w = 0; w < NSUB && t * NSUB + w < nsub; ++w) {
+      const int2 qq = sub[t * NSUB + w];
+      const int la = slot(qq.x), lb = slot(qq.y);
       if (la < 0 || lb < 0) {
         set_error("a row super-tile touches more than 6 G blocks");
         return LRT_EUNSUPPORTED;
       }
-      rowtab[(size_t)t * per_st + r] = make_int2(la, lb);
+      rowtab[(size_t)t * NSUB + w] = make_int2(la, lb);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          const int G = 4 * qq.x + i, Gp = 4 * qq.y + j;
+          if (G >= nG || Gp >= nG || G > Gp) continue;
+          const int r = (t * NSUB + w) * 16 + 4 * i + j;
+          rp_of[G * nG + Gp] = r;
+          rp_of[Gp * nG + G] = r;
+        }
     }
   }
   const int ncols = 2 * c->nwi;
   const int n_n = (ncols + TN - 1) / TN;
-  std::vector<float2> wtab((size_t)n_n * 128, make_float2(0.f, 0.f));
+  std::vector<float4> wtab((size_t)n_n * 64, make_float4(0.f, 0.f, 0.f, 0.f));
   for (int j = 0; j < c->nwi; ++j) {
-    float h = (float)c->freqs[j];
-    wtab[j] = make_float2(h, (float)(c->freqs[j] - (double)h));
+    // frequency pair j / 2 of its column tile: {hi_f, hi_f+1, lo_f, lo_f+1}
+    const float h = (float)c->freqs[j], l = (float)(c->freqs[j] - (double)h);
+    float* w4 = reinterpret_cast<float*>(&wtab[j / 2]);
+    w4[j % 2] = h;
+    w4[2 + j % 2] = l;
   }
   const bool bf = c->precision == LRT_PREC_BF16X3;
-  const float sA = bf ? 1.0f : 16384.0f;
+  // power-of-two scales that keep the FP16 low parts clear of the subnormal range: the pair
+  // densities carry split_rho_scale() (so P carries its square, sA) and df carries sB
+  const float sA = split_rho_scale(c->precision) * split_rho_scale(c->precision);
   float sB = 1.0f;
   if (!bf) sB = std::ldexp(1.0f, (int)std::floor(std::log2(16384.0 * c->eta)));
   const int ldc = n_n * TN;
@@ -665,12 +745,13 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   kps = (kps + KS - 1) / KS * KS;
   const int n_split = (int)((c->np + kps - 1) / kps);
 
-  // device buffers: C (column-major FP64 sums) then the per-CTA slabs
+  // device buffer: C (column-major FP64 sums)
   const long long ldr = (long long)n_st * NACC * TM;
   const long long units = tiles * n_split;
   const int grid = (int)std::min<long long>(nsm, units);
   const size_t c_bytes = (size_t)ldr * ldc * sizeof(double);
-  const size_t need = c_bytes + (size_t)grid * TN * NACC * TM * sizeof(float2);
+  const size_t stage_bytes = (size_t)grid * 4 * NCHUNK * 4 * 32 * sizeof(float4);
+  const size_t need = c_bytes + stage_bytes;
   DeviceWork& dw = const_cast<DeviceWork&>(c->dw);
   if (dw.scratch_bytes < need) {
     cudaFree(dw.scratch);
@@ -682,21 +763,21 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   int2* d_rowtab = nullptr;
   int* d_blk = nullptr;
   int* d_rp = nullptr;
-  float2* d_wtab = nullptr;
+  float4* d_wtab = nullptr;
   float4* d_pw = nullptr;
   // pair weights padded to whole 32-pair stages (the bulk copies read full stages)
   const size_t npw_pad = (size_t)((c->np + KS - 1) / KS * KS);
   LRT_CUDA(cudaMallocAsync(&d_rowtab, rowtab.size() * sizeof(int2), s));
   LRT_CUDA(cudaMallocAsync(&d_blk, blk.size() * sizeof(int), s));
   LRT_CUDA(cudaMallocAsync(&d_rp, rp_of.size() * sizeof(int), s));
-  LRT_CUDA(cudaMallocAsync(&d_wtab, wtab.size() * sizeof(float2), s));
+  LRT_CUDA(cudaMallocAsync(&d_wtab, wtab.size() * sizeof(float4), s));
   LRT_CUDA(cudaMallocAsync(&d_pw, npw_pad * sizeof(float4), s));
   LRT_CUDA(cudaMemsetAsync(d_pw, 0, npw_pad * sizeof(float4), s));
   LRT_CUDA(cudaMemcpyAsync(d_rowtab, rowtab.data(), rowtab.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
   LRT_CUDA(cudaMemcpyAsync(d_blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   LRT_CUDA(cudaMemcpyAsync(d_rp, rp_of.data(), rp_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  LRT_CUDA(cudaMemcpyAsync(d_wtab, wtab.data(), wtab.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
-  pair_weights_split<<<4 * nsm, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, d_pw);
+  LRT_CUDA(cudaMemcpyAsync(d_wtab, wtab.data(), wtab.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+  pair_weights_split<<<4 * nsm, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, sB, d_pw);
   LRT_CUDA(cudaGetLastError());
   LRT_CUDA(cudaMemsetAsync(dw.scratch, 0, c_bytes, s));
 
@@ -707,12 +788,12 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   P.blk = d_blk;
   P.wtab = d_wtab;
   P.C = dw.scratch;
-  P.slab = reinterpret_cast<float2*>(dw.scratch + (size_t)ldr * ldc);
+  P.stage = reinterpret_cast<float4*>(dw.scratch + (size_t)ldr * ldc);
   P.status = dw.status;
   P.np = c->np;
   P.ldr = ldr;
   P.gpad = c->rho_gpad;
-  P.rows_valid = 2 * npairs;
+  P.rows_valid = 2 * nsub * 16;
   P.cols_valid = ncols;
   P.n_st = n_st;
   P.n_n = n_n;
@@ -720,8 +801,6 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   P.k_per_split = kps;
   P.flush = kFlushStages;
   P.eta = (float)c->eta;
-  P.sA = sA;
-  P.sB = sB;
   const size_t smem = (size_t)NS * STAGE_BYTES + (size_t)NSR * R_STAGE + 1024;
   if (bf)
     LRT_CUDA(cudaFuncSetAttribute(chi0_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

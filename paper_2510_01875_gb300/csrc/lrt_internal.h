@@ -57,7 +57,7 @@ struct DeviceWork {
   double* S = nullptr;            // [nq][nw]
   double* chi00 = nullptr;        // [nq][nwi][2] gather of chi_00 for the spectra kernels
   int* status = nullptr;          // device status word (0 ok, bit 1 singular, bit 2 timeout)
-  double* scratch = nullptr;      // tensor path: FP64 sums, then per-CTA double-float slabs
+  double* scratch = nullptr;      // tensor path: FP64 sums of the contraction
   size_t scratch_bytes = 0;
 };
 
@@ -150,6 +150,10 @@ lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host);
 lrt_status reset_band_weights(lrt_ctx* c, int iq, const double* eps_host);
 double fxc_alda(double n);
 double fxc_model(double qg, double n, double A, double B, double C);
+
+// Power-of-two factor carried by the FP32 pair densities of the split-precision path (FP16
+// parts: keeps the products rho rho* clear of the FP16 subnormal range; exact in binary).
+inline float split_rho_scale(int precision) { return precision == LRT_PREC_FP16X3 ? 128.0f : 1.0f; }
 
 // pairdens.cu: rho[G][p] for one q (FP64 or FP32 storage)
 lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool fp32,

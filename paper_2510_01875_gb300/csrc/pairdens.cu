@@ -8,7 +8,8 @@
 // Output layout, p = (k nb + n) nb + n':
 //  FP64 path: rho[G][p] with row stride ld (the pair count rounded up to 32);
 //  split path: blocked rho[p / 32][G][p % 32] with G padded to a multiple of 8, so that the rows
-//  of one 8-G block for one 32-pair stage are a single contiguous 2 KB copy.
+//  of one 8-G block for one 32-pair stage are a single contiguous 2 KB copy; the values carry
+//  the exact power-of-two factor split_rho_scale().
 #include "lrt_internal.h"
 
 namespace lrt {
@@ -33,7 +34,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) pair_density_kernel(
     const double2* __restrict__ ck, const double2* __restrict__ ckq,
     const int32_t* __restrict__ gather, int nk, int nb, int npw, int nG, int ntile, int64_t ld,
-    int nGpad, typename C2<R>::T* __restrict__ rho) {
+    int nGpad, R scale, typename C2<R>::T* __restrict__ rho) {
   using CT = typename C2<R>::T;
   __shared__ CT As[TK][TN];
   __shared__ CT Bs[TK][TN];
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(256) pair_density_kernel(
       // row layout rho[G][p] (nGpad == 0) or blocked rho[p / 32][G][p % 32]
       const size_t idx = nGpad ? ((size_t)((p >> 5) * nGpad + G) << 5) + (size_t)(p & 31)
                                : (size_t)G * ld + (size_t)p;
-      rho[idx] = CT{accr[i][j], acci[i][j]};
+      rho[idx] = CT{accr[i][j] * scale, acci[i][j] * scale};
     }
   }
 }
@@ -131,10 +132,11 @@ lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool
     TimedLaunch tl(c, &c->ev_rho, s);
     if (fp32)
       pair_density_kernel<float><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw, q.nG,
-                                                      ntile, c->rho_ld, c->rho_gpad, (float2*)rho);
+                                                      ntile, c->rho_ld, c->rho_gpad,
+                                                      split_rho_scale(c->precision), (float2*)rho);
     else
       pair_density_kernel<double><<<grid, 256, 0, s>>>(ck, ckq, q.gather, c->nk, c->nb, c->npw,
-                                                       q.nG, ntile, c->rho_ld, 0, (double2*)rho);
+                                                       q.nG, ntile, c->rho_ld, 0, 1.0, (double2*)rho);
   }
   count_launch(c);
   LRT_CUDA(cudaGetLastError());
