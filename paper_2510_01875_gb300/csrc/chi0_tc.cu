@@ -6,27 +6,31 @@
 // c = (w, Re|Im of w_p(w) = df_p / (w + Delta_p + i eta)).  From RR, RI, IR, II of a row pair
 // and a column pair, chi0(G,G') = (RR - II) + i(RI + IR) and chi0(G',G) = (RR + II) + i(RI - IR).
 //
-// Both operands are generated inside the kernel and never stored in global memory.  Per
+// Both operands are generated inside the kernel and never stored in global memory.  A cluster
+// of two CTAs (one per SM) works as a pair with tcgen05.mma.cta_group::2 (M = 256, N = 256,
+// K = 16): each CTA builds its own 2 x 128 rows of A and half (128 columns) of the shared B
+// tile, and each CTA's tensor memory holds its rows of the two 256 x 256 accumulators.  Per
 // 32-pair stage:
 //  - a loader warp copies the stage's rho rows (blocked layout rho[p/32][G][p%32]: one 2 KB
-//    bulk copy per 8-G block the row tile touches) and the 32 (Delta_hi, Delta_lo, df) into a
+//    bulk copy per 8-G block the CTA's rows touch) and the 32 (Delta_hi, Delta_lo, df) into a
 //    shared-memory ring with cp.async.bulk, completion counted in bytes on an mbarrier;
-//  - 16 producer warps form P (8 warps, 256 rows) and w (8 warps, 256 columns) in FP32, with
-//    w + Delta carried as (hi, lo) floats so the sum keeps FP64-level accuracy when it
-//    cancels, split every value v into v_hi = round16(v) and v_lo = round16(v - v_hi) (FP16
-//    with power-of-two scales, or BF16), and write the tiles MN-major with the 128-byte
-//    swizzle (each lane owns one pair = one K index and stores 16-byte chunks of 8 rows or
-//    columns);
-//  - one thread issues tcgen05.mma kind::f16, M = 128, N = 256, K = 16, for
-//    A_hi B_hi + A_hi B_lo + A_lo B_hi into two FP32 accumulators in tensor memory (two row
-//    tiles share each B tile: 256 x 256 outputs per CTA);
-//  - every `flush` stages four epilogue warps read the accumulators (tcgen05.ld), hand the
-//    tensor memory back and add the values into the FP64 sums C with reductions that return
-//    nothing (red.global.add.f64), so FP32 accumulation never spans more than one period.
-// Units of work are (row super-tile, column tile, pair range), handed out round-robin to one
-// CTA per SM.  Every wait on an mbarrier is bounded; on expiry the kernel sets bit 2 of the
-// status word, stops issuing work, waits (bounded) for its own copies and MMAs and frees its
-// tensor memory before returning.
+//  - 16 producer warps form P = rho(G) rho*(G') (8 warps, one 4 x 4 (G, G') sub-block each)
+//    and w = df / (w + Delta + i eta) (8 warps, 16 columns each) in FP32, with w + Delta
+//    carried as (hi, lo) floats so the sum keeps FP64-level accuracy when it cancels, split
+//    every value v into v_hi = round16(v) and v_lo = round16(v - v_hi) (FP16 with power-of-two
+//    scales, or BF16), and write the tiles MN-major with the 128-byte swizzle (lane = pair =
+//    K index; 16-byte chunks of 8 rows or columns), then arrive on the even CTA's barrier;
+//  - one thread of the even CTA issues A_hi B_hi + A_hi B_lo + A_lo B_hi for both
+//    accumulators and commits to the barriers of both CTAs (multicast);
+//  - every `flush` stages four epilogue warps per CTA copy their accumulator rows
+//    (tcgen05.ld) to a staging area, hand the tensor memory back, and add the staged values
+//    into the FP64 sums C with reductions that return nothing (red.global.add.f64) while the
+//    next period runs, so FP32 accumulation never spans more than one period.
+// Units of work are (row super-tile pair, column tile, pair range), handed out round-robin to
+// the clusters.  Every wait on an mbarrier is bounded; on expiry the kernel sets bit 2 of the
+// status word, stops issuing work, waits (bounded) for its own copies and MMAs, and frees its
+// tensor memory before returning; cluster barriers at the start and the end keep either CTA
+// from touching the other's shared memory before it is set up or after it has left.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -39,12 +43,13 @@
 namespace lrt {
 namespace {
 
-constexpr int TM = 128;            // rows per accumulator (64 row pairs)
+constexpr int TM = 128;            // rows per accumulator per CTA (64 row pairs)
 constexpr int NACC = 2;            // accumulators (row tiles) per CTA
-constexpr int TN = 256;            // columns per tile (128 frequencies)
+constexpr int TN = 256;            // MMA N: columns per tile (128 frequencies), shared by the pair
+constexpr int TNH = TN / 2;        // B columns built by each CTA of the pair
 constexpr int KS = 32;             // pairs (K) per pipeline stage
-constexpr int NS = 2;              // operand (A/B) stages
-constexpr int NSR = 6;             // prefetch stages of rho blocks and pair weights
+constexpr int NS = 4;              // operand (A/B) stages
+constexpr int NSR = 2;             // prefetch stages of rho blocks and pair weights
 constexpr int GBLK = 8;            // G per block of the blocked rho layout
 constexpr int MAXBLK = 6;          // G blocks one row super-tile may touch
 constexpr int RROWS = MAXBLK * GBLK;
@@ -52,12 +57,13 @@ constexpr int NPROD = 16;          // producer warps 0..15: 0..7 build A, 8..15 
 constexpr int WMMA = 16;           // MMA warp
 constexpr int WLOAD = 21;          // loader warp
 constexpr int NTHREADS = 22 * 32;  // + epilogue warps 17..20 (one per TMEM lane quadrant)
-constexpr int CHUNKS = 4;          // 16-byte chunks (8 rows or columns) per producer warp
+constexpr int CHUNKS_A = 4;        // 16-byte chunks (8 rows) per A warp
+constexpr int CHUNKS_B = 2;        // 16-byte chunks (8 columns) per B warp
 constexpr int A_BYTES = TM * KS * 2;                 // 8 KB per 16-bit row tile
-constexpr int B_BYTES = TN * KS * 2;                 // 16 KB
-constexpr int STAGE_BYTES = NACC * 2 * A_BYTES + 2 * B_BYTES;   // 64 KB
+constexpr int B_BYTES = TNH * KS * 2;                // 8 KB per 16-bit half column tile
+constexpr int STAGE_BYTES = NACC * 2 * A_BYTES + 2 * B_BYTES;   // 48 KB
 constexpr int A_SBO = (TM / 64) * 1024;              // bytes between 8-pair groups of A
-constexpr int B_SBO = (TN / 64) * 1024;
+constexpr int B_SBO = (TNH / 64) * 1024;
 constexpr int RBLK_BYTES = GBLK * KS * 8;            // one G block of one stage: 2 KB
 constexpr int PW_OFF = RROWS * KS * 8;               // pair weights after the rows
 constexpr int R_STAGE = PW_OFF + KS * 16;            // rho rows, 32 float4 pair weights
@@ -72,15 +78,16 @@ struct Params {
   const int2* rowtab;         // [n_st * NSUB] ring rows of the G quads of each sub-block
   const int* blk;             // [n_st * MAXBLK] G blocks of the super-tile, -1 padding
   const float4* wtab;         // [n_n * 64] per frequency pair {hi_f, hi_f+1, lo_f, lo_f+1}
+                              // (CTA r of a pair builds the columns of pairs 32 r .. 32 r + 31)
   double* C;                  // [n_n * TN][ldr] FP64 sums, column-major
   float4* stage;              // [gridDim.x][4 warps][NCHUNK][4][32 lanes] accumulator staging
   int* status;
   long long np;
-  long long ldr;              // = n_st * NACC * TM
+  long long ldr;              // = n_st * NACC * TM (n_st even: super-tile 2 st2 + r is CTA r's)
   int gpad;
   int rows_valid;             // 2 * row pairs
   int cols_valid;             // 2 * nwi
-  int n_st, n_n, n_split;
+  int n_st2, n_n, n_split;    // super-tile pairs, column tiles, pair ranges
   long long k_per_split;      // multiple of KS
   int flush;                  // stages per accumulator period
   float eta;
@@ -103,7 +110,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(smem_u32(b)), "r"(parity)
@@ -115,7 +122,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 __device__ __forceinline__ bool mbar_try_sleep(uint64_t* b, uint32_t parity, uint32_t hint_ns) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(smem_u32(b)), "r"(parity), "r"(hint_ns)
@@ -162,6 +169,26 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Rank of this CTA in its cluster, and the shared::cluster address of a variable in CTA `rank`.
+__device__ __forceinline__ uint32_t cta_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+// Arrive on an mbarrier of a CTA of the cluster (this one included).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+// All threads of both CTAs.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -179,16 +206,27 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                    uint32_t acc) {
+// D (tensor memory of both CTAs) [+]= A (rows 0..127 from this CTA's shared memory, 128..255
+// from the peer's, same offsets) x B (columns 0..127 here, 128..255 at the peer).
+__device__ __forceinline__ void mma2(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
-__device__ __forceinline__ void mma_commit(uint64_t* b) {
+// Arrive on barrier b in both CTAs of the pair once all prior MMAs of this thread are done.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* b) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], %1;" ::"r"(smem_u32(b)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+// The same, on this CTA's barrier only.
+__device__ __forceinline__ void mma_commit_local(uint64_t* b) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(b))
       : "memory");
 }
@@ -280,13 +318,13 @@ __device__ __forceinline__ float4 lds_f4(uint32_t addr) {
 }
 
 struct Unit {
-  int st, nt;
+  int st2, nt;
   long long kb, ke;
 };
 __device__ __forceinline__ Unit unit_of(const Params& P, int u) {
   Unit U;
   int tile = u / P.n_split, ks = u % P.n_split;
-  U.st = tile / P.n_n;
+  U.st2 = tile / P.n_n;
   U.nt = tile % P.n_n;
   U.kb = (long long)ks * P.k_per_split;
   U.ke = min(P.np, U.kb + P.k_per_split);
@@ -296,22 +334,26 @@ __device__ __forceinline__ Unit unit_of(const Params& P, int u) {
 template <bool BF>
 __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   extern __shared__ uint8_t smem_raw[];
+  // full[s]: this CTA's producers arrive; in the even CTA also the odd CTA's relay.
+  // acc_empty[] is used in the even CTA only (the epilogues of both CTAs arrive on it).
   __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full, acc_empty[NACC], final_bar;
   __shared__ __align__(8) uint64_t rfull[NSR], rempty[NSR];
   __shared__ uint32_t tmem_base_s;
   __shared__ int2 rowtab_s[NSUB];   // byte offsets of the two G quads of each A warp's sub-block
   __shared__ int blk_s[MAXBLK];
   __shared__ int nblk_s;
-  __shared__ float4 wtab_s[64];
+  __shared__ float4 wtab_s[TNH / 4];
   __shared__ volatile int abort_s;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cta_rank();
+  const bool leader = rank == 0;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t rbase = base + NS * STAGE_BYTES;          // prefetch ring
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
-      mbar_init(&full[s], NPROD);
+      mbar_init(&full[s], leader ? NPROD + 1 : NPROD);
       mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < NSR; ++s) {
@@ -319,40 +361,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       mbar_init(&rempty[s], NPROD);
     }
     mbar_init(&acc_full, 1);
-    for (int a = 0; a < NACC; ++a) mbar_init(&acc_empty[a], 4);
+    for (int a = 0; a < NACC; ++a) mbar_init(&acc_empty[a], 8);
     mbar_init(&final_bar, 1);
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == WMMA) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+    // one warp of each CTA of the pair allocates (tensor memory of both CTAs)
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_s)),
                  "r"(NACC * TN));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();   // both CTAs' barriers initialised before any cross-CTA arrive
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
-  const int nunits = P.n_st * P.n_n * P.n_split;
+  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int nunits = P.n_st2 * P.n_n * P.n_split;
   const uint32_t idesc = (1u << 4) | ((BF ? 1u : 0u) << 7) | ((BF ? 1u : 0u) << 10) | (1u << 15) |
-                         (1u << 16) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+                         (1u << 16) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)((2 * TM) >> 4) << 24);
 
   uint32_t it = 0;   // stage counter (producers, loader, MMA)
   uint32_t pc = 0;   // accumulator period counter (MMA and epilogue)
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+  for (int u = cid; u < nunits; u += ncl) {
     const Unit U = unit_of(P, u);
+    const int st = 2 * U.st2 + (int)rank;   // this CTA's row super-tile
     // per-unit tables (row pairs and G blocks of the super-tile, frequencies of the column tile)
     __syncthreads();
     if (threadIdx.x < NSUB) {
-      const int2 g = P.rowtab[U.st * NSUB + threadIdx.x];
+      const int2 g = P.rowtab[st * NSUB + threadIdx.x];
       rowtab_s[threadIdx.x] = make_int2(g.x * KS * 8, g.y * KS * 8);
     }
-    if (threadIdx.x < 64) wtab_s[threadIdx.x] = P.wtab[U.nt * 64 + threadIdx.x];
-    if (threadIdx.x < MAXBLK) blk_s[threadIdx.x] = P.blk[U.st * MAXBLK + threadIdx.x];
+    if (threadIdx.x < TNH / 4) wtab_s[threadIdx.x] = P.wtab[U.nt * 64 + rank * (TNH / 4) + threadIdx.x];
+    if (threadIdx.x < MAXBLK) blk_s[threadIdx.x] = P.blk[st * MAXBLK + threadIdx.x];
     if (threadIdx.x == 0) {
       int n = 0;
-      while (n < MAXBLK && P.blk[U.st * MAXBLK + n] >= 0) ++n;
+      while (n < MAXBLK && P.blk[st * MAXBLK + n] >= 0) ++n;
       nblk_s = n;
     }
     __syncthreads();
@@ -363,24 +409,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     if (warp < NPROD) {
       // ---------------- producers ----------------
       // Lane = pair.  A warp w (0..7) owns the 4 x 4 sub-block (G quad a, G quad b) of rows
-      // 32 w .. 32 w + 31: chunk i holds the row pairs (4 a + i, 4 b + j), j = 0..3.  B warps
-      // (8..15) own 16 frequencies (4 chunks of 8 columns).  Padding pairs (beyond the last
-      // one) and padding G rows have zero pair densities and weights, so no masking is needed.
-      uint32_t sto[CHUNKS];   // shared-memory offsets of this lane's 16-byte chunks in a stage
+      // 32 w .. 32 w + 31: chunk i holds the row pairs (4 a + i, 4 b + j), j = 0..3.  B warp w
+      // (8..15) owns 8 frequencies (2 chunks of 8 columns) of this CTA's 64.  Padding pairs
+      // (beyond the last one) and padding G rows have zero pair densities and weights, so no
+      // masking is needed.
+      uint32_t sto[CHUNKS_A];   // shared-memory offsets of this lane's 16-byte chunks in a stage
 #pragma unroll
-      for (int cc = 0; cc < CHUNKS; ++cc) {
+      for (int cc = 0; cc < CHUNKS_A; ++cc) {
         if (warp < 8) {
-          const int c = CHUNKS * warp + cc;
+          const int c = CHUNKS_A * warp + cc;
           sto[cc] = (c >> 4) * 2 * A_BYTES + mn_chunk(lane, c & 15, A_SBO);
         } else {
-          sto[cc] = NACC * 2 * A_BYTES + mn_chunk(lane, CHUNKS * (warp - 8) + cc, B_SBO);
+          sto[cc] = NACC * 2 * A_BYTES + mn_chunk(lane, CHUNKS_B * (warp - 8) + (cc & 1), B_SBO);
         }
       }
-      const int2 ro = rowtab_s[warp & 7];                     // A warps
-      const float4* wt = wtab_s + 8 * (warp & 7);             // B warps: 8 frequency pairs
+      const int2 ro = rowtab_s[warp & 7];                      // A warps
+      const float4* wt = wtab_s + CHUNKS_B * 2 * (warp & 7);   // B warps: 4 frequency pairs
       const float eta2 = P.eta * P.eta;
       uint32_t s = it % NS, ph = (it / NS) & 1, sr = it % NSR, phr = (it / NSR) & 1;
-      for (int st = 0; st < nstage; ++st) {
+      for (int st_ = 0; st_ < nstage; ++st_) {
         // every lane waits; the vote keeps the warp together if one lane's wait gives up
         if (!__all_sync(0xffffffffu, mbar_wait(&rfull[sr], phr, &abort_s, P.status))) break;
         if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1, &abort_s, P.status))) break;
@@ -400,7 +447,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
             Yi[i] = make_float2(y.y, y.y);
           }
 #pragma unroll
-          for (int cc = 0; cc < CHUNKS; ++cc) {
+          for (int cc = 0; cc < CHUNKS_A; ++cc) {
             float v[8];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -421,7 +468,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
           const float2 m = make_float2(-P.eta * pw.z, -P.eta * pw.z);
           const float2 e2 = make_float2(eta2, eta2);
 #pragma unroll
-          for (int cc = 0; cc < CHUNKS; ++cc) {
+          for (int cc = 0; cc < CHUNKS_B; ++cc) {
             float v[8];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -459,10 +506,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       if (lane == 0) {
         const int nb = nblk_s;
         const uint32_t bytes = (uint32_t)(nb * RBLK_BYTES + KS * 16);
-        for (int st = 0; st < nstage; ++st, ++it) {
+        for (int st_ = 0; st_ < nstage; ++st_, ++it) {
           const int sr = it % NSR;
           if (!mbar_wait(&rempty[sr], ((it / NSR) & 1) ^ 1, &abort_s, P.status)) break;
-          const long long p0 = U.kb + (long long)st * KS;
+          const long long p0 = U.kb + (long long)st_ * KS;
           mbar_expect_tx(&rfull[sr], bytes);
           const uint32_t dst = rbase + sr * R_STAGE;
           const float2* src = P.rho + (size_t)(p0 >> 5) * P.gpad * KS;
@@ -473,65 +520,82 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       }
       it = __shfl_sync(0xffffffffu, it, 0);
     } else if (warp == WMMA) {
-      // ---------------- MMA issuer ----------------
-      bool ok = true;
-      for (int per = 0; per < nper && ok; ++per, ++pc) {
-        const int s0 = per * P.flush, s1 = min(nstage, s0 + P.flush);
-        for (int st = s0; st < s1; ++st, ++it) {
-          const int s = it % NS;
-          if (lane == 0) ok = mbar_wait(&full[s], (it / NS) & 1, &abort_s, P.status);
-          ok = __shfl_sync(0xffffffffu, ok, 0);
-          if (!ok) break;
-          tc_fence_after();
-          const uint32_t sst = base + s * STAGE_BYTES;
-          const uint32_t bH = sst + NACC * 2 * A_BYTES, bL = bH + B_BYTES;
+      // ---------------- MMA issuer (even CTA) ----------------
+      if (leader) {
+        bool ok = true;
+        for (int per = 0; per < nper && ok; ++per, ++pc) {
+          const int s0 = per * P.flush, s1 = min(nstage, s0 + P.flush);
+          for (int st_ = s0; st_ < s1; ++st_, ++it) {
+            const int s = it % NS;
+            if (lane == 0) ok = mbar_wait(&full[s], (it / NS) & 1, &abort_s, P.status);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t sst = base + s * STAGE_BYTES;
+            const uint32_t bH = sst + NACC * 2 * A_BYTES, bL = bH + B_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < KS / 16; ++kk) {
-            const uint64_t dBh = sdesc(bH + kk * 2 * B_SBO, 1024, B_SBO);
-            const uint64_t dBl = sdesc(bL + kk * 2 * B_SBO, 1024, B_SBO);
+            for (int kk = 0; kk < KS / 16; ++kk) {
+              const uint64_t dBh = sdesc(bH + kk * 2 * B_SBO, 1024, B_SBO);
+              const uint64_t dBl = sdesc(bL + kk * 2 * B_SBO, 1024, B_SBO);
 #pragma unroll
-            for (int a = 0; a < NACC; ++a) {
-              if (st == s0 && kk == 0) {
-                // first use of accumulator a in this period: the epilogue must have read it
-                if (lane == 0) ok = mbar_wait(&acc_empty[a], (pc & 1) ^ 1, &abort_s, P.status);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) break;
-                tc_fence_after();
+              for (int a = 0; a < NACC; ++a) {
+                if (st_ == s0 && kk == 0) {
+                  // first use of accumulator a in this period: both epilogues must have read it
+                  if (lane == 0) ok = mbar_wait(&acc_empty[a], (pc & 1) ^ 1, &abort_s, P.status);
+                  ok = __shfl_sync(0xffffffffu, ok, 0);
+                  if (!ok) break;
+                  tc_fence_after();
+                }
+                if (lane == 0) {
+                  const uint32_t aH = sst + a * 2 * A_BYTES, aL = aH + A_BYTES;
+                  const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
+                  const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
+                  const uint32_t d = tmem + a * TN;
+                  mma2(d, dAh, dBh, idesc, (st_ > s0 || kk > 0) ? 1u : 0u);
+                  mma2(d, dAh, dBl, idesc, 1u);
+                  mma2(d, dAl, dBh, idesc, 1u);
+                }
+                __syncwarp();
               }
-              if (lane == 0) {
-                const uint32_t aH = sst + a * 2 * A_BYTES, aL = aH + A_BYTES;
-                const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
-                const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
-                const uint32_t d = tmem + a * TN;
-                mma(d, dAh, dBh, idesc, (st > s0 || kk > 0) ? 1u : 0u);
-                mma(d, dAh, dBl, idesc, 1u);
-                mma(d, dAl, dBh, idesc, 1u);
-              }
-              __syncwarp();
+              if (!ok) break;
             }
             if (!ok) break;
+            if (lane == 0) mma_commit_pair(&empty[s]);
+            __syncwarp();
           }
           if (!ok) break;
-          if (lane == 0) mma_commit(&empty[s]);
+          if (lane == 0) mma_commit_pair(&acc_full);
           __syncwarp();
         }
-        if (!ok) break;
-        if (lane == 0) mma_commit(&acc_full);
-        __syncwarp();
+      } else {
+        // odd CTA: relay each stage its producers have completed to the even CTA's full[s]
+        // (one cluster-scope arrive per stage instead of one per producer warp)
+        const uint32_t full0 = cluster_addr(&full[0], 0);
+        for (int st_ = 0; st_ < nstage; ++st_, ++it) {
+          const int s = it % NS;
+          bool ok = true;
+          if (lane == 0) {
+            ok = mbar_wait(&full[s], (it / NS) & 1, &abort_s, P.status);
+            if (ok) mbar_arrive_cluster(full0 + s * 8);
+          }
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) break;
+        }
       }
     } else {
       // ---------------- epilogue ----------------
-      // Per period: (1) read the accumulators (tcgen05.ld) into a per-warp staging area in
-      // global memory with plain stores and hand each accumulator back as soon as it has been
-      // read; (2) while the next period runs, add the staged FP32 values into the FP64 sums C
-      // with reductions that return nothing (red.global.add.f64).  Each lane reads back only
-      // what it wrote.  C is column-major with ldr >= the super-tile rows and n_n * TN
-      // columns, so no bounds checks are needed (padding rows and columns collect values that
-      // are never read).
+      // Per period: (1) read this CTA's accumulator rows (tcgen05.ld) into a per-warp staging
+      // area in global memory with plain stores and hand each accumulator back (to the even
+      // CTA) as soon as it has been read; (2) while the next period runs, add the staged FP32
+      // values into the FP64 sums C with reductions that return nothing (red.global.add.f64).
+      // Each lane reads back only what it wrote.  C is column-major with ldr >= the super-tile
+      // rows and n_n * TN columns, so no bounds checks are needed (padding rows and columns
+      // collect values that are never read).
       const int q = warp & 3;            // tensor-memory lane quadrant of this warp
       float4* stg = P.stage + ((size_t)blockIdx.x * 4 + q) * (NCHUNK * 4 * 32) + lane;
-      const long long grow0 = (long long)U.st * (NACC * TM) + q * 32 + lane;
+      const long long grow0 = (long long)st * (NACC * TM) + q * 32 + lane;
       double* cbase = P.C + (size_t)(U.nt * TN) * P.ldr;
+      const uint32_t acc_empty0 = cluster_addr(&acc_empty[0], 0);
       for (int per = 0; per < nper; ++per, ++pc) {
         bool ok = true;
         if (lane == 0) ok = mbar_wait(&acc_full, pc & 1, &abort_s, P.status);
@@ -560,7 +624,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
             // accumulator a has been read: hand it back
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[a]);
+            if (lane == 0) mbar_arrive_cluster(acc_empty0 + a * 8);
           }
         }
 #pragma unroll 1
@@ -586,24 +650,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     // keep every role on the same unit; an abort stops all of them
     __syncthreads();
   }
-  // drain: the loader waits (bounded) for its last bulk copies, the MMA warp for this CTA's
-  // MMAs, before the shared and tensor memory go away
+  // drain: the loader waits (bounded) for its last bulk copies; the even CTA's MMA warp waits
+  // for all its MMAs and for the last commits to have arrived, so that nothing is in flight
+  // towards either CTA when the pair meets at the closing cluster barrier
   if (warp == WLOAD && lane == 0) {
     for (uint32_t j = (it > (uint32_t)NSR ? it - NSR : 0u); j < it; ++j)
       mbar_drain(&rfull[j % NSR], (j / NSR) & 1, P.status);
   }
-  if (warp == WMMA) {
+  if (warp == WMMA && leader) {
     if (lane == 0) {
-      mma_commit(&final_bar);
+      mma_commit_local(&final_bar);
       mbar_drain(&final_bar, 0, P.status);
+      for (uint32_t j = (it > (uint32_t)NS ? it - NS : 0u); j < it; ++j)
+        mbar_drain(&empty[j % NS], (j / NS) & 1, P.status);
+      if (pc > 0) mbar_drain(&acc_full, (pc - 1) & 1, P.status);
     }
     __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();
   tc_fence_after();
   if (warp == WMMA)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TN));
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TN));
 }
 
 // chi0[w][G][G'] from the FP64 sums (C column-major: C[col * ldr + row])
@@ -673,13 +742,17 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
         for (int qb = 2 * J; qb < std::min(nQ, 2 * J + 2); ++qb)
           if (qa <= qb) sub.push_back(make_int2(qa, qb));
   const int nsub = (int)sub.size();
-  const int n_st = (nsub + NSUB - 1) / NSUB;
+  // an even number of super-tiles: CTA r of a pair takes super-tile 2 st2 + r (a padding
+  // super-tile reads G block 0 and fills rows that are never read)
+  const int n_st = ((nsub + NSUB - 1) / NSUB + 1) / 2 * 2;
+  const int n_st2 = n_st / 2;
   std::vector<int2> rowtab((size_t)n_st * NSUB, make_int2(0, 0));
   std::vector<int> blk((size_t)n_st * MAXBLK, -1);
   std::vector<int> rp_of((size_t)nG * nG, 0);
   for (int t = 0; t < n_st; ++t) {
     int* bl = &blk[(size_t)t * MAXBLK];
     int n = 0;
+    if (t * NSUB >= nsub) bl[0] = 0;
     auto slot = [&](int q) {   // ring row of the first G of quad q
       const int b = q / 2;
       for (int i = 0; i < n; ++i)
@@ -724,18 +797,38 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   if (!bf) sB = std::ldexp(1.0f, (int)std::floor(std::log2(16384.0 * c->eta)));
   const int ldc = n_n * TN;
 
-  int dev = 0, nsm = 0;
+  const size_t smem = (size_t)NS * STAGE_BYTES + (size_t)NSR * R_STAGE + 1024;
+  auto kern = bf ? chi0_tc_kernel<true> : chi0_tc_kernel<false>;
+  LRT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchAttribute cl_attr[1];
+  cl_attr[0].id = cudaLaunchAttributeClusterDimension;
+  cl_attr[0].val.clusterDim.x = 2;
+  cl_attr[0].val.clusterDim.y = 1;
+  cl_attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = cl_attr;
+  cfg.numAttrs = 1;
+  int dev = 0, nsm = 0, ncl_max = 0;
   LRT_CUDA(cudaGetDevice(&dev));
   LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const long long tiles = (long long)n_st * n_n;
-  // pair splits: at least 4 units per SM, chosen to fill the last round
+  cfg.gridDim = dim3(2 * (nsm / 2));
+  LRT_CUDA(cudaOccupancyMaxActiveClusters(&ncl_max, (const void*)kern, &cfg));
+  if (ncl_max < 1) {
+    set_error("the chi0 tensor kernel cannot be resident as a CTA pair");
+    return LRT_EUNSUPPORTED;
+  }
+  const long long tiles = (long long)n_st2 * n_n;
+  // pair splits: at least 4 units per CTA pair, chosen to fill the last round
   long long best_split = 1;
   double best_eff = 0.0;
   const long long max_split = std::max<long long>(1, c->np / (KS * 64));
-  for (long long sp = std::max<long long>(1, (4LL * nsm + tiles - 1) / tiles);
-       sp <= 8LL * nsm / std::max<long long>(1, tiles) + 8 && sp <= max_split; ++sp) {
+  for (long long sp = std::max<long long>(1, (4LL * ncl_max + tiles - 1) / tiles);
+       sp <= 8LL * ncl_max / std::max<long long>(1, tiles) + 8 && sp <= max_split; ++sp) {
     long long units = tiles * sp;
-    double eff = (double)units / (double)(((units + nsm - 1) / nsm) * nsm);
+    double eff = (double)units / (double)(((units + ncl_max - 1) / ncl_max) * ncl_max);
     if (eff > best_eff + 1e-9) {
       best_eff = eff;
       best_split = sp;
@@ -748,7 +841,7 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   // device buffer: C (column-major FP64 sums)
   const long long ldr = (long long)n_st * NACC * TM;
   const long long units = tiles * n_split;
-  const int grid = (int)std::min<long long>(nsm, units);
+  const int grid = 2 * (int)std::min<long long>(ncl_max, units);
   const size_t c_bytes = (size_t)ldr * ldc * sizeof(double);
   const size_t stage_bytes = (size_t)grid * 4 * NCHUNK * 4 * 32 * sizeof(float4);
   const size_t need = c_bytes + stage_bytes;
@@ -795,23 +888,16 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   P.gpad = c->rho_gpad;
   P.rows_valid = 2 * nsub * 16;
   P.cols_valid = ncols;
-  P.n_st = n_st;
+  P.n_st2 = n_st2;
   P.n_n = n_n;
   P.n_split = n_split;
   P.k_per_split = kps;
   P.flush = kFlushStages;
   P.eta = (float)c->eta;
-  const size_t smem = (size_t)NS * STAGE_BYTES + (size_t)NSR * R_STAGE + 1024;
-  if (bf)
-    LRT_CUDA(cudaFuncSetAttribute(chi0_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  else
-    LRT_CUDA(cudaFuncSetAttribute(chi0_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cfg.gridDim = dim3(grid);
   {
     TimedLaunch tl(c, &c->ev_chi0, s);
-    if (bf)
-      chi0_tc_kernel<true><<<grid, NTHREADS, smem, s>>>(P);
-    else
-      chi0_tc_kernel<false><<<grid, NTHREADS, smem, s>>>(P);
+    LRT_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
   }
   count_launch(c, 2);   // pair_weights_split + the contraction
   if (c->profiling) c->timed_cmac += (double)nG * nG * c->nw * (double)c->np;
