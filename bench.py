@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import re
 import math
 import os
 import subprocess
@@ -238,7 +239,8 @@ def run_ours(args, world, rank, local, pg):
     chi0_ms = prof["chi0_ms"] / max(prof["chi0_launches"], 1)
     chi0_tflops = flops_per_cmac * prof["chi0_cmac"] / (prof["chi0_ms"] / 1e3) / 1e12
     roofline = {"bound": bound, "achieved": chi0_tflops, "peak": peak, "unit": unit,
-                "frac": chi0_tflops / peak, "traffic": None,
+                "frac": chi0_tflops / peak,
+                "traffic": profiled_traffic(args.precision, ctx.nk * ctx.nb * ctx.nb),
                 "kernel": "chi0_tc_kernel" if args.precision != "fp64" else "chi0_fp64_kernel",
                 "launch_ms": chi0_ms, "peak_source": peak_note,
                 "pair_density_ms_per_launch": prof["rho_ms"] / max(prof["rho_launches"], 1),
@@ -288,6 +290,27 @@ def run_ours(args, world, rank, local, pg):
         }
         line.update(extras)
         print(json.dumps(line), flush=True)
+
+
+def profiled_traffic(precision, np_per_q):
+    """DRAM bytes per contraction launch from the committed ncu summary of the kernel
+    (dram__bytes_read.sum + dram__bytes_write.sum on a 4^3-k case, per pair, scaled by this
+    launch's pair count), or None when the kernel source has changed since the capture or the
+    precision was not the profiled one."""
+    import glob
+    import hashlib
+    if precision != "fp16x3":
+        return None
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "paper_2510_01875_gb300", "csrc", "chi0_tc.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    for path in sorted(glob.glob(os.path.join(here, "profiles", "chi0_tc_kernel_*.md"))):
+        text = open(path).read()
+        m = re.search(r"sha256 prefix `([0-9a-f]+)`", text)
+        t = re.search(r"^traffic_bytes_per_pair: ([0-9.eE+]+)", text, re.M)
+        if m and t and digest.startswith(m.group(1)):
+            return float(t.group(1)) * float(np_per_q)
+    return None
 
 
 def run_e2e(ctx, wl, args, cmac_step, pg, world):

@@ -165,6 +165,37 @@ lrt_status lrtddft_itcf_laplace(lrt_ctx* ctx, int ntau, const double* tau, int m
 lrt_status lrtddft_itcf_laplace_device(lrt_ctx* ctx, int ntau, const double* tau_dev, int mode,
                                        double* F_dev, double* metrics_dev, void* stream);
 
+/* ---- Parameters and adjoint.  theta = (T, eta, A, B, C): temperature, broadening and the
+ * three parameters of the FXC_MODEL kernel (for RPA and RPA_ALDA the A, B, C components are
+ * 0).  The paper fits none of these by gradients; these calls serve fitting T and kernel
+ * parameters to measured spectra through the same response path (S by Eq. 8, F by the
+ * detailed-balance fold of Eq. 1). */
+
+/* New T (Ha), eta (Ha) and kernel for an existing context, without new eigensolves (the
+ * orbitals do not depend on them here): Fermi-Dirac occupations and mu are recomputed at T
+ * (occupations supplied by the caller stay as they are), K is rebuilt, and chi0, chi and the
+ * derivatives are invalidated, so chi0_assemble and dyson_solve must run again.
+ * LRT_EINVAL for T <= 0, eta <= 0, an unknown kernel kind or non-finite A, B, C. */
+lrt_status lrtddft_set_params(lrt_ctx* ctx, double T, double eta, const lrt_kernel* kernel);
+
+/* Derivatives with respect to theta at the current state (requires dyson_solve for every q):
+ *   dS [nq][nw][5]    dS(q, w)/dtheta on the caller's grid (NULL to skip);
+ *   dF [nq][ntau][5]  dF(q, tau)/dtheta of the FOLD form at the absolute times tau[ntau]
+ *                     (held fixed when T changes; NULL to skip, then tau may be NULL).
+ * The first call after chi0/chi changed recomputes the pair densities of every q, the Dyson
+ * LU from the stored chi0 (M^T u = e_0, M = 1 - chi0 K), and the projections
+ * sum_p (u.rho_p)(rho_p^*.v) dw_p/dtheta (2 N_G complex MACs per pair and frequency) on the
+ * GPU; the results are kept until chi0, chi or the parameters change.  Errors as
+ * itcf_laplace; LRT_ESINGULAR if a Dyson matrix is singular. */
+lrt_status lrtddft_jacobian(lrt_ctx* ctx, int ntau, const double* tau, double* dS, double* dF);
+
+/* Vector-Jacobian products: grad[5] = sum_{q,tau} dL_dF[q][tau] dF(q,tau)/dtheta (FOLD form,
+ * absolute tau[ntau] as in itcf_laplace) and grad[5] = sum_{q,w} dL_dS[q][w] dS(q,w)/dtheta.
+ * Host buffers; same requirements and caching as lrtddft_jacobian. */
+lrt_status lrtddft_itcf_vjp(lrt_ctx* ctx, int ntau, const double* tau, const double* dL_dF,
+                            double grad[5]);
+lrt_status lrtddft_dsf_vjp(lrt_ctx* ctx, const double* dL_dS, double grad[5]);
+
 /* Attenuation of narrow-band fluctuations (Sec. 3).  Defaults (fields <= 0) in brackets. */
 typedef struct {
   int d_min, d_max;         /* polynomial degrees searched [1, 4] */

@@ -86,6 +86,10 @@ SIGNATURES = {
     "lrtddft_dsf_device": (C.c_int, [_P, _P, _P]),
     "lrtddft_itcf_laplace": (C.c_int, [_P, C.c_int, _D, C.c_int, _D, _D]),
     "lrtddft_itcf_laplace_device": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "lrtddft_set_params": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(lrt_kernel)]),
+    "lrtddft_jacobian": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "lrtddft_itcf_vjp": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "lrtddft_dsf_vjp": (C.c_int, [_P, _D, _D]),
     "lrtddft_attenuate": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D, C.POINTER(lrt_atten_report)]),
     "lrtddft_attenuate_noalloc": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D,
                                             C.POINTER(lrt_atten_report)]),
@@ -216,6 +220,39 @@ class Context:
     def itcf_device(self, ntau: int, tau_ptr: int, F_ptr: int, metrics_ptr: int, mode="fold", stream: int = 0):
         _check("lrtddft_itcf_laplace_device", self.lib.lrtddft_itcf_laplace_device(
             self.h, ntau, _P(tau_ptr), ITCF[mode], _P(F_ptr), _P(metrics_ptr), _P(stream)))
+
+    def set_params(self, T: float, eta: float, kernel: Optional[str] = None, fxc_params=None):
+        """New T, eta (Ha) and kernel without new eigensolves; chi0 and chi must be recomputed."""
+        kern = lrt_kernel(KERNEL[kernel or self.wl.kernel],
+                          *[float(x) for x in (fxc_params if fxc_params is not None else self.wl.fxc_params)])
+        _check("lrtddft_set_params", self.lib.lrtddft_set_params(self.h, float(T), float(eta), C.byref(kern)))
+        self.wl = self.wl.replace(T=float(T), eta=float(eta), kernel=kernel or self.wl.kernel,
+                                  fxc_params=tuple(float(x) for x in (fxc_params if fxc_params is not None
+                                                                      else self.wl.fxc_params)))
+
+    def jacobian(self, tau=None):
+        """(dS [nq][nw][5], dF [nq][ntau][5] or None) with respect to (T, eta, A, B, C)."""
+        dS = np.zeros((self.nq, self.nw, 5))
+        if tau is None:
+            _check("lrtddft_jacobian", self.lib.lrtddft_jacobian(self.h, 0, None, _dp(dS), None))
+            return dS, None
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        dF = np.zeros((self.nq, len(tau), 5))
+        _check("lrtddft_jacobian", self.lib.lrtddft_jacobian(self.h, len(tau), _dp(tau), _dp(dS), _dp(dF)))
+        return dS, dF
+
+    def itcf_vjp(self, tau, dL_dF):
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        g = np.ascontiguousarray(dL_dF, dtype=np.float64).reshape(self.nq, len(tau))
+        out = np.zeros(5)
+        _check("lrtddft_itcf_vjp", self.lib.lrtddft_itcf_vjp(self.h, len(tau), _dp(tau), _dp(g), _dp(out)))
+        return out
+
+    def dsf_vjp(self, dL_dS):
+        g = np.ascontiguousarray(dL_dS, dtype=np.float64).reshape(self.nq, self.nw)
+        out = np.zeros(5)
+        _check("lrtddft_dsf_vjp", self.lib.lrtddft_dsf_vjp(self.h, _dp(g), _dp(out)))
+        return out
 
     def attenuate(self, params: Optional[lrt_atten_params] = None):
         p = params if params is not None else atten_params()

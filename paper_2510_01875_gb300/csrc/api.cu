@@ -268,6 +268,7 @@ extern "C" lrt_status lrtddft_chi0_assemble(lrt_ctx* c, int q_begin, int q_end, 
       LRT_TRY(launch_chi0_split(c, Q, s));
     Q.have_chi0 = true;
     Q.have_chi = false;
+    Q.have_dchi = false;
   }
   c->have_S = false;
   return LRT_OK;
@@ -288,6 +289,7 @@ extern "C" lrt_status lrtddft_dyson_solve(lrt_ctx* c, int q_begin, int q_end, vo
     if (!Q.chi) LRT_CUDA(cudaMalloc(&Q.chi, (size_t)c->nwi * Q.nG * sizeof(double2)));
     LRT_TRY(launch_dyson(c, Q, iq, s));
     Q.have_chi = true;
+    Q.have_dchi = false;
   }
   c->have_S = false;
   return LRT_OK;
@@ -395,7 +397,7 @@ extern "C" lrt_status lrtddft_set_orbitals(lrt_ctx* c, int iq, const double* eps
   } else {
     LRT_TRY(set_occupations_fd(c, iq, eps));
   }
-  Q.have_chi0 = Q.have_chi = false;
+  Q.have_chi0 = Q.have_chi = Q.have_dchi = false;
   c->have_S = false;
   return LRT_OK;
 }
@@ -520,5 +522,185 @@ extern "C" lrt_status lrtddft_get_orbitals(const lrt_ctx* c, int iq, double* coe
   const QData& Q = c->qd[iq];
   LRT_CUDA(cudaMemcpy(coeff, Q.coeff, (size_t)2 * c->nk * c->nb * c->npw * sizeof(double2),
                       cudaMemcpyDeviceToHost));
+  return LRT_OK;
+}
+
+// ------------------------------------------------------------------ parameters and adjoint
+
+extern "C" lrt_status lrtddft_set_params(lrt_ctx* c, double T, double eta, const lrt_kernel* kernel) {
+  if (!c || !kernel) return bad("NULL argument");
+  if (!(T > 0) || !std::isfinite(T)) return bad("T must be > 0");
+  if (!(eta > 0) || !std::isfinite(eta)) return bad("eta must be > 0");
+  if (kernel->kind < LRT_KERNEL_RPA || kernel->kind > LRT_KERNEL_FXC_MODEL)
+    return bad("unknown kernel kind");
+  if (!std::isfinite(kernel->A) || !std::isfinite(kernel->B) || !std::isfinite(kernel->C))
+    return bad("kernel parameters must be finite");
+  LRT_TRY(need_device(c));
+  LRT_CUDA(cudaSetDevice(c->device));
+  LRT_CUDA(cudaDeviceSynchronize());
+  c->T = T;
+  c->eta = eta;
+  c->kernel = *kernel;
+  const size_t ne = (size_t)2 * c->nk * c->nb;
+  std::vector<double> eps(ne);
+  for (int iq = 0; iq < c->nq; ++iq) {
+    QData& Q = c->qd[iq];
+    kernel_diag(c, Q);
+    LRT_CUDA(cudaMemcpy(Q.Kdev, Q.K.data(), Q.nG * sizeof(double), cudaMemcpyHostToDevice));
+    if (!std::isnan(Q.mu)) {   // Fermi-Dirac occupations (not supplied by the caller)
+      LRT_CUDA(cudaMemcpy(eps.data(), Q.eps, ne * sizeof(double), cudaMemcpyDeviceToHost));
+      LRT_TRY(set_occupations_fd(c, iq, eps.data()));
+    }
+    Q.have_chi0 = Q.have_chi = Q.have_dchi = false;
+  }
+  c->have_S = false;
+  return LRT_OK;
+}
+
+// d chi_00/d theta of every q (cached until chi0, chi or the parameters change)
+static lrt_status ensure_dchi(lrt_ctx* c) {
+  LRT_TRY(need_all_chi(c));
+  LRT_CUDA(cudaSetDevice(c->device));
+  LRT_CUDA(cudaDeviceSynchronize());
+  bool any = false;
+  for (auto& Q : c->qd) any = any || !Q.have_dchi;
+  if (!any) return LRT_OK;
+  LRT_TRY(ensure_rho(c));
+  for (int iq = 0; iq < c->nq; ++iq) {
+    QData& Q = c->qd[iq];
+    if (Q.have_dchi) continue;
+    LRT_TRY(launch_pair_density(c, Q, c->dw.rho, c->precision != LRT_PREC_FP64, 0));
+    LRT_TRY(launch_adjoint_q(c, Q, iq, Q.dchi, 0));
+    LRT_TRY(check_status_word(c));
+    Q.have_dchi = true;
+  }
+  return LRT_OK;
+}
+
+// S of q iq on the caller's grid and dS/dtheta [nw][5] (Eq. 8 and its w -> 0 form)
+static lrt_status s_and_jacobian(lrt_ctx* c, int iq, std::vector<double>& S, std::vector<double>& dS,
+                                 double& S0, double dS0[5]) {
+  const QData& Q = c->qd[iq];
+  std::vector<double2> chi00(c->nwi);
+  LRT_CUDA(cudaMemcpy2D(chi00.data(), sizeof(double2), Q.chi, (size_t)Q.nG * sizeof(double2),
+                        sizeof(double2), c->nwi, cudaMemcpyDeviceToHost));
+  const double beta = 1.0 / c->T, pin = M_PI * c->density;
+  auto dim = [&](int w, int j) { return Q.dchi[(size_t)w * 10 + 2 * j + 1]; };
+  S.assign(c->nw, 0.0);
+  dS.assign((size_t)c->nw * 5, 0.0);
+  const double h = kHZero;
+  S0 = -chi00[c->hcol].y * c->T / (pin * h);
+  for (int j = 0; j < 5; ++j) dS0[j] = -dim(c->hcol, j) * c->T / (pin * h);
+  dS0[0] += -chi00[c->hcol].y / (pin * h);
+  for (int w = 0; w < c->nw; ++w) {
+    const double om = c->omega[w];
+    if (om == 0.0) {
+      S[w] = S0;
+      for (int j = 0; j < 5; ++j) dS[(size_t)w * 5 + j] = dS0[j];
+      continue;
+    }
+    const double g = 1.0 / (-std::expm1(-beta * om));
+    S[w] = -chi00[w].y * g / pin;
+    for (int j = 0; j < 5; ++j) dS[(size_t)w * 5 + j] = -dim(w, j) * g / pin;
+    // d/dT of 1/(1 - e^{-w/T})
+    const double dg = std::exp(-beta * om) * om / (c->T * c->T) * g * g;
+    dS[(size_t)w * 5] += -chi00[w].y * dg / pin;
+  }
+  return LRT_OK;
+}
+
+static lrt_status check_tau(const lrt_ctx* c, int ntau, const double* tau) {
+  if (ntau < 1) return bad("ntau must be >= 1");
+  for (int i = 0; i < ntau; ++i)
+    if (!(tau[i] >= 0.0) || tau[i] > 1.0 / c->T * (1.0 + 1e-12)) return bad("tau outside [0, beta]");
+  return LRT_OK;
+}
+
+// dF/dtheta [ntau][5] of q iq (FOLD form of Eq. 1 at fixed absolute tau)
+static void f_jacobian(const lrt_ctx* c, const std::vector<double>& S, const std::vector<double>& dS,
+                       double S0, const double dS0[5], int ntau, const double* tau, double* dF) {
+  // positive branch: w >= 0 in grid order, with w = 0 prepended (value S0) when absent
+  std::vector<double> wp, sp, dsp;
+  for (int w = 0; w < c->nw; ++w)
+    if (c->omega[w] >= 0.0) {
+      if (wp.empty() && c->omega[w] != 0.0) {
+        wp.push_back(0.0);
+        sp.push_back(S0);
+        for (int j = 0; j < 5; ++j) dsp.push_back(dS0[j]);
+      }
+      wp.push_back(c->omega[w]);
+      sp.push_back(S[w]);
+      for (int j = 0; j < 5; ++j) dsp.push_back(dS[(size_t)w * 5 + j]);
+    }
+  if (wp.empty()) {
+    wp.push_back(0.0);
+    sp.push_back(S0);
+    for (int j = 0; j < 5; ++j) dsp.push_back(dS0[j]);
+  }
+  const size_t m = wp.size();
+  std::vector<double> wt(m, 0.0);
+  for (size_t i = 0; i + 1 < m; ++i) {
+    const double dx = wp[i + 1] - wp[i];
+    wt[i] += 0.5 * dx;
+    wt[i + 1] += 0.5 * dx;
+  }
+  const double beta = 1.0 / c->T;
+  for (int t = 0; t < ntau; ++t) {
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (size_t i = 0; i < m; ++i) {
+      const double e1 = std::exp(-tau[t] * wp[i]), e2 = std::exp(-(beta - tau[t]) * wp[i]);
+      for (int j = 0; j < 5; ++j) acc[j] += wt[i] * (e1 + e2) * dsp[i * 5 + j];
+      acc[0] += wt[i] * sp[i] * wp[i] * e2 / (c->T * c->T);
+    }
+    for (int j = 0; j < 5; ++j) dF[(size_t)t * 5 + j] = acc[j];
+  }
+}
+
+extern "C" lrt_status lrtddft_jacobian(lrt_ctx* c, int ntau, const double* tau, double* dS,
+                                       double* dF) {
+  if (!c || (!dS && !dF)) return bad("NULL argument");
+  if (dF) {
+    if (!tau) return bad("NULL argument");
+    LRT_TRY(check_tau(c, ntau, tau));
+  }
+  LRT_TRY(ensure_dchi(c));
+  std::vector<double> S, J;
+  double S0, dS0[5];
+  for (int iq = 0; iq < c->nq; ++iq) {
+    LRT_TRY(s_and_jacobian(c, iq, S, J, S0, dS0));
+    if (dS) std::copy(J.begin(), J.end(), dS + (size_t)iq * c->nw * 5);
+    if (dF) f_jacobian(c, S, J, S0, dS0, ntau, tau, dF + (size_t)iq * ntau * 5);
+  }
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_itcf_vjp(lrt_ctx* c, int ntau, const double* tau, const double* dL_dF,
+                                       double grad[5]) {
+  if (!c || !tau || !dL_dF || !grad) return bad("NULL argument");
+  LRT_TRY(check_tau(c, ntau, tau));
+  LRT_TRY(ensure_dchi(c));
+  std::vector<double> S, J, jf((size_t)ntau * 5);
+  double S0, dS0[5];
+  for (int j = 0; j < 5; ++j) grad[j] = 0.0;
+  for (int iq = 0; iq < c->nq; ++iq) {
+    LRT_TRY(s_and_jacobian(c, iq, S, J, S0, dS0));
+    f_jacobian(c, S, J, S0, dS0, ntau, tau, jf.data());
+    for (int t = 0; t < ntau; ++t)
+      for (int j = 0; j < 5; ++j) grad[j] += dL_dF[(size_t)iq * ntau + t] * jf[(size_t)t * 5 + j];
+  }
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_dsf_vjp(lrt_ctx* c, const double* dL_dS, double grad[5]) {
+  if (!c || !dL_dS || !grad) return bad("NULL argument");
+  LRT_TRY(ensure_dchi(c));
+  std::vector<double> S, J;
+  double S0, dS0[5];
+  for (int j = 0; j < 5; ++j) grad[j] = 0.0;
+  for (int iq = 0; iq < c->nq; ++iq) {
+    LRT_TRY(s_and_jacobian(c, iq, S, J, S0, dS0));
+    for (int w = 0; w < c->nw; ++w)
+      for (int j = 0; j < 5; ++j) grad[j] += dL_dS[(size_t)iq * c->nw + w] * J[(size_t)w * 5 + j];
+  }
   return LRT_OK;
 }

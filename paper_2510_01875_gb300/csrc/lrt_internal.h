@@ -28,6 +28,7 @@ struct QData {
   int nG = 0;
   std::vector<int32_t> gset;      // [nG][3], G = 0 first
   std::vector<double> K;          // [nG]
+  std::vector<double> qg2;        // [nG] |q+G|^2
   double* Kdev = nullptr;         // device [nG]
   std::vector<double> kpts;       // [2][nk][3] Cartesian
   std::vector<int32_t> miller;    // [2][nk][npw][3], padding INT32_MIN
@@ -44,6 +45,8 @@ struct QData {
   double2* chi = nullptr;         // device [nwi][nG]  (chi_{G,0})
   bool have_chi0 = false;
   bool have_chi = false;
+  std::vector<double> dchi;       // [nwi][5] complex: d chi_00/d(T, eta, A, B, C) (adjoint)
+  bool have_dchi = false;
 };
 
 struct DeviceWork {
@@ -150,6 +153,8 @@ lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host);
 lrt_status reset_band_weights(lrt_ctx* c, int iq, const double* eps_host);
 double fxc_alda(double n);
 double fxc_model(double qg, double n, double A, double B, double C);
+// K_GG = 4 pi/|q+G|^2 + f_xc for the context's kernel, from Q.qg2 (host vector only).
+void kernel_diag(const lrt_ctx* c, QData& Q);
 
 // Power-of-two factor carried by the FP32 pair densities of the split-precision path (FP16
 // parts: keeps the products rho rho* clear of the FP16 subnormal range; exact in binary).
@@ -172,6 +177,11 @@ lrt_status launch_dyson(const lrt_ctx* c, QData& q, int iq, cudaStream_t s);
 lrt_status launch_dsf(const lrt_ctx* c, double* S_dev, cudaStream_t s);
 lrt_status launch_itcf(const lrt_ctx* c, const double* S_dev, int ntau, const double* tau_dev,
                        int mode, double* F_dev, double* metrics_dev, cudaStream_t s);
+
+// adjoint.cu: d chi_00/d(T, eta, A, B, C) at every internal frequency of one q, out[nwi][10]
+// (complex pairs); needs the q's chi0, chi and pair densities (in dw.rho)
+lrt_status launch_adjoint_q(const lrt_ctx* c, QData& q, int iq, std::vector<double>& out,
+                            cudaStream_t s);
 
 // attenuate.cu
 lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* p, const double* S_dev,

@@ -181,6 +181,18 @@ double fxc_model(double qg, double n, double A, double B, double C) {
   return A * fxc_alda(n) * (1.0 + B * qg * qg) * std::exp(-C * qg * qg);
 }
 
+void kernel_diag(const lrt_ctx* c, QData& Q) {
+  Q.K.resize(Q.nG);
+  for (int g = 0; g < Q.nG; ++g) {
+    const double qg2 = Q.qg2[g];
+    double Kv = 4.0 * M_PI / qg2;
+    if (c->kernel.kind == LRT_KERNEL_RPA_ALDA) Kv += c->fxc;
+    if (c->kernel.kind == LRT_KERNEL_FXC_MODEL)
+      Kv += fxc_model(std::sqrt(qg2), c->density, c->kernel.A, c->kernel.B, c->kernel.C);
+    Q.K[g] = Kv;
+  }
+}
+
 lrt_status build_geometry(lrt_ctx* c, const int* nG) {
   // reciprocal vectors b_j = 2 pi (a_k x a_l) / Omega
   const double(*a)[3] = c->lattice;
@@ -224,17 +236,13 @@ lrt_status build_geometry(lrt_ctx* c, const int* nG) {
     Q.nG = nG[iq];
     LRT_TRY(response_gset(c, qv, Q.nG, Q.gset));
     c->nGmax = std::max(c->nGmax, Q.nG);
-    Q.K.resize(Q.nG);
+    Q.qg2.resize(Q.nG);
     for (int g = 0; g < Q.nG; ++g) {
       V3 G = gvec(c, Q.gset[3 * g], Q.gset[3 * g + 1], Q.gset[3 * g + 2]);
       double x = qv[0] + G.x, y = qv[1] + G.y, z = qv[2] + G.z;
-      double qg2 = x * x + y * y + z * z;
-      double Kv = 4.0 * M_PI / qg2;
-      if (c->kernel.kind == LRT_KERNEL_RPA_ALDA) Kv += c->fxc;
-      if (c->kernel.kind == LRT_KERNEL_FXC_MODEL)
-        Kv += fxc_model(std::sqrt(qg2), c->density, c->kernel.A, c->kernel.B, c->kernel.C);
-      Q.K[g] = Kv;
+      Q.qg2[g] = x * x + y * y + z * z;
     }
+    kernel_diag(c, Q);
     // meshes: k in M (+ shift), k+q = k + q
     double shift[3] = {0, 0, 0};
     if (c->kscheme == LRT_K_TR_SYMMETRIC)

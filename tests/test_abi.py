@@ -99,6 +99,31 @@ def test_host_only_context_refuses_compute(lib):
     lib.lrtddft_destroy(h)
 
 
+def test_params_and_adjoint_validation(lib):
+    st, h = _host_ctx(W.tiny(kernel="fxc_model"))
+    assert st == 0
+    D = C.POINTER(C.c_double)
+    k = binding.lrt_kernel(2, 1.0, 0.1, 0.05)
+    for T, eta in ((0.0, 0.01), (-1.0, 0.01), (0.1, 0.0), (float("nan"), 0.01), (0.1, float("inf"))):
+        assert lib.lrtddft_set_params(h, T, eta, C.byref(k)) == binding.LRT_EINVAL
+    assert lib.lrtddft_set_params(h, 0.1, 0.01, C.byref(binding.lrt_kernel(7, 0, 0, 0))) == binding.LRT_EINVAL
+    assert lib.lrtddft_set_params(h, 0.1, 0.01, C.byref(binding.lrt_kernel(2, float("nan"), 0, 0))) \
+        == binding.LRT_EINVAL
+    assert lib.lrtddft_set_params(h, 0.1, 0.01, None) == binding.LRT_EINVAL
+    # valid parameters on a context without a GPU: refused by state, not by the arguments
+    assert lib.lrtddft_set_params(h, 0.1, 0.01, C.byref(k)) == binding.LRT_ESTATE
+    tau = np.linspace(0.0, 1.0, 4)
+    g = np.zeros(5)
+    gF = np.zeros((2, 4))
+    assert lib.lrtddft_itcf_vjp(h, 4, tau.ctypes.data_as(D), None, g.ctypes.data_as(D)) == binding.LRT_EINVAL
+    big = np.array([0.0, 1e9])
+    assert lib.lrtddft_itcf_vjp(h, 2, big.ctypes.data_as(D), gF.ctypes.data_as(D),
+                                g.ctypes.data_as(D)) == binding.LRT_EINVAL
+    assert lib.lrtddft_jacobian(h, 0, None, None, None) == binding.LRT_EINVAL
+    assert lib.lrtddft_dsf_vjp(h, gF.ctypes.data_as(D), g.ctypes.data_as(D)) == binding.LRT_ESTATE
+    lib.lrtddft_destroy(h)
+
+
 @pytest.mark.parametrize("wl", [W.tiny(), W.tiny(kscheme="commensurate", nq=1), W.config0(),
                                 W.tiny(basis="fixed", seed=3), W.tiny(kernel="fxc_model", seed=4)])
 def test_host_geometry_matches_oracle(lib, wl):
