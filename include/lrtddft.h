@@ -165,6 +165,34 @@ lrt_status lrtddft_itcf_laplace(lrt_ctx* ctx, int ntau, const double* tau, int m
 lrt_status lrtddft_itcf_laplace_device(lrt_ctx* ctx, int ntau, const double* tau_dev, int mode,
                                        double* F_dev, double* metrics_dev, void* stream);
 
+/* ---- Scheduling of the tensor-core contraction (FP16X3 / BF16X3; no effect on FP64).
+ * chi0_assemble runs all requested q in one persistent launch when their pair densities fit
+ * next to each other in device memory (q of different N_G mix freely: the launch walks a list
+ * of (q, row super-tile pair, column tile, pair range) units); otherwise q by q.  Each unit
+ * covers a fixed number of 32-pair stages ("unit size"), and two kernel variants differ in
+ * their shared-memory ring depths (0: 4 operand / 2 prefetch stages, 1: 3 / 4).
+ *   flags: LRT_TUNE_AUTO      time each (variant, unit size) candidate on the first units of
+ *                             the first launch of each shape and keep the fastest (results
+ *                             then differ from the defaults at the rounding of the split form);
+ *          LRT_TUNE_SINGLE_Q  one launch per q.
+ *   variant: -1 (tuned or default 0), 0 or 1;  unit_stages: 0 (tuned or default 4096) or a
+ *   positive multiple of 64.  LRT_EINVAL otherwise.  Invalidates a captured graph. */
+enum { LRT_TUNE_AUTO = 1, LRT_TUNE_SINGLE_Q = 2 };
+lrt_status lrtddft_set_tuning(lrt_ctx* ctx, int flags, int variant, int unit_stages);
+/* The variant and unit size used by the last tensor-core launch (-1 and 0 before any). */
+lrt_status lrtddft_get_tuning(lrt_ctx* ctx, int* variant, int* unit_stages);
+
+/* CUDA graph of the forward path for every q: chi0_assemble, dyson_solve, dsf_device and
+ * itcf_laplace_device into the given device buffers (S_dev [nq][nw], F_dev [nq][ntau],
+ * metrics_dev [nq][5], tau_dev [ntau]; they must stay allocated).  One ordinary pass runs
+ * first (it builds the tables, allocates, tunes), then the same calls are captured on a
+ * private stream and instantiated.  graph_launch replays it on `stream`; it returns
+ * LRT_ESTATE when there is no graph or after set_params, set_orbitals or set_tuning (capture
+ * again).  Attenuation is not part of the graph (its candidate search runs on the host). */
+lrt_status lrtddft_graph_capture(lrt_ctx* ctx, int ntau, const double* tau_dev, int mode,
+                                 double* S_dev, double* F_dev, double* metrics_dev);
+lrt_status lrtddft_graph_launch(lrt_ctx* ctx, void* stream);
+
 /* ---- Parameters and adjoint.  theta = (T, eta, A, B, C): temperature, broadening and the
  * three parameters of the FXC_MODEL kernel (for RPA and RPA_ALDA the A, B, C components are
  * 0).  The paper fits none of these by gradients; these calls serve fitting T and kernel

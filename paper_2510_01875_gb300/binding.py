@@ -87,6 +87,10 @@ SIGNATURES = {
     "lrtddft_itcf_laplace": (C.c_int, [_P, C.c_int, _D, C.c_int, _D, _D]),
     "lrtddft_itcf_laplace_device": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
     "lrtddft_set_params": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(lrt_kernel)]),
+    "lrtddft_set_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "lrtddft_get_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lrtddft_graph_capture": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "lrtddft_graph_launch": (C.c_int, [_P, _P]),
     "lrtddft_jacobian": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "lrtddft_itcf_vjp": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "lrtddft_dsf_vjp": (C.c_int, [_P, _D, _D]),
@@ -220,6 +224,22 @@ class Context:
     def itcf_device(self, ntau: int, tau_ptr: int, F_ptr: int, metrics_ptr: int, mode="fold", stream: int = 0):
         _check("lrtddft_itcf_laplace_device", self.lib.lrtddft_itcf_laplace_device(
             self.h, ntau, _P(tau_ptr), ITCF[mode], _P(F_ptr), _P(metrics_ptr), _P(stream)))
+
+    def set_tuning(self, auto: bool = False, single_q: bool = False, variant: int = -1, unit_stages: int = 0):
+        flags = (1 if auto else 0) | (2 if single_q else 0)
+        _check("lrtddft_set_tuning", self.lib.lrtddft_set_tuning(self.h, flags, variant, unit_stages))
+
+    def get_tuning(self):
+        v, u = C.c_int(), C.c_int()
+        _check("lrtddft_get_tuning", self.lib.lrtddft_get_tuning(self.h, C.byref(v), C.byref(u)))
+        return v.value, u.value
+
+    def graph_capture(self, ntau: int, tau_ptr: int, S_ptr: int, F_ptr: int, metrics_ptr: int, mode="fold"):
+        _check("lrtddft_graph_capture", self.lib.lrtddft_graph_capture(
+            self.h, ntau, _P(tau_ptr), ITCF[mode], _P(S_ptr), _P(F_ptr), _P(metrics_ptr)))
+
+    def graph_launch(self, stream: int = 0):
+        _check("lrtddft_graph_launch", self.lib.lrtddft_graph_launch(self.h, _P(stream)))
 
     def set_params(self, T: float, eta: float, kernel: Optional[str] = None, fxc_params=None):
         """New T, eta (Ha) and kernel without new eigensolves; chi0 and chi must be recomputed."""

@@ -40,7 +40,10 @@ void free_ctx(lrt_ctx* c) {
     return;
   }
   cudaSetDevice(c->device);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  free_tc_state(c);
   for (auto& q : c->qd) {
+    free_split_plan(q.sp);
     cudaFree(q.Kdev);
     cudaFree(q.eps);
     cudaFree(q.occ);
@@ -76,6 +79,8 @@ lrt_status check_status_word(lrt_ctx* c) {
   return LRT_OK;
 }
 
+}  // namespace
+
 lrt_status ensure_rho(lrt_ctx* c) {
   size_t elem = (c->precision == LRT_PREC_FP64) ? sizeof(double2) : sizeof(float2);
   size_t need = (size_t)(c->rho_gpad ? c->rho_gpad : c->nGmax) * c->rho_ld * elem;
@@ -90,7 +95,6 @@ lrt_status ensure_rho(lrt_ctx* c) {
   return LRT_OK;
 }
 
-}  // namespace
 }  // namespace lrt
 
 using namespace lrt;
@@ -256,16 +260,23 @@ extern "C" lrt_status lrtddft_chi0_assemble(lrt_ctx* c, int q_begin, int q_end, 
   if (q_begin < 0 || q_end > c->nq || q_begin >= q_end) return bad("q range");
   cudaStream_t s = (cudaStream_t)stream;
   LRT_CUDA(cudaSetDevice(c->device));
-  LRT_TRY(ensure_rho(c));
   for (int iq = q_begin; iq < q_end; ++iq) {
     QData& Q = c->qd[iq];
     if (!Q.chi0) LRT_CUDA(cudaMalloc(&Q.chi0, (size_t)c->nwi * Q.nG * Q.nG * sizeof(double2)));
-    if (c->precision == LRT_PREC_FP64) LRT_TRY(launch_pair_weights(c, Q, s));
-    LRT_TRY(launch_pair_density(c, Q, c->dw.rho, c->precision != LRT_PREC_FP64, s));
-    if (c->precision == LRT_PREC_FP64)
+  }
+  if (c->precision == LRT_PREC_FP64) {
+    LRT_TRY(ensure_rho(c));
+    for (int iq = q_begin; iq < q_end; ++iq) {
+      QData& Q = c->qd[iq];
+      LRT_TRY(launch_pair_weights(c, Q, s));
+      LRT_TRY(launch_pair_density(c, Q, c->dw.rho, false, s));
       LRT_TRY(launch_chi0_fp64(c, Q, s));
-    else
-      LRT_TRY(launch_chi0_split(c, Q, s));
+    }
+  } else {
+    LRT_TRY(launch_chi0_split_range(c, q_begin, q_end, s));
+  }
+  for (int iq = q_begin; iq < q_end; ++iq) {
+    QData& Q = c->qd[iq];
     Q.have_chi0 = true;
     Q.have_chi = false;
     Q.have_dchi = false;
@@ -399,6 +410,7 @@ extern "C" lrt_status lrtddft_set_orbitals(lrt_ctx* c, int iq, const double* eps
   }
   Q.have_chi0 = Q.have_chi = Q.have_dchi = false;
   c->have_S = false;
+  c->graph_valid = false;
   return LRT_OK;
 }
 
@@ -541,6 +553,7 @@ extern "C" lrt_status lrtddft_set_params(lrt_ctx* c, double T, double eta, const
   c->T = T;
   c->eta = eta;
   c->kernel = *kernel;
+  c->graph_valid = false;
   const size_t ne = (size_t)2 * c->nk * c->nb;
   std::vector<double> eps(ne);
   for (int iq = 0; iq < c->nq; ++iq) {
@@ -701,6 +714,106 @@ extern "C" lrt_status lrtddft_dsf_vjp(lrt_ctx* c, const double* dL_dS, double gr
     LRT_TRY(s_and_jacobian(c, iq, S, J, S0, dS0));
     for (int w = 0; w < c->nw; ++w)
       for (int j = 0; j < 5; ++j) grad[j] += dL_dS[(size_t)iq * c->nw + w] * J[(size_t)w * 5 + j];
+  }
+  return LRT_OK;
+}
+
+// ------------------------------------------------------------------ tuning and graphs
+
+extern "C" lrt_status lrtddft_set_tuning(lrt_ctx* c, int flags, int variant, int unit_stages) {
+  if (!c) return bad("NULL context");
+  if (flags & ~(LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q)) return bad("unknown tuning flags");
+  if (variant < -1 || variant > 1) return bad("variant must be -1, 0 or 1");
+  if (unit_stages != 0 && (unit_stages < 64 || unit_stages % 64 != 0))
+    return bad("unit_stages must be 0 or a positive multiple of 64");
+  c->autotune = (flags & LRT_TUNE_AUTO) != 0;
+  c->multi_q = (flags & LRT_TUNE_SINGLE_Q) == 0;
+  c->tune_variant = variant;
+  c->tune_unit_stages = unit_stages;
+  c->graph_valid = false;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_tuning(lrt_ctx* c, int* variant, int* unit_stages) {
+  if (!c || !variant || !unit_stages) return bad("NULL argument");
+  *variant = c->last_tc_variant;
+  *unit_stages = c->last_tc_unit_stages;
+  return LRT_OK;
+}
+
+static lrt_status forward_all(lrt_ctx* c, int ntau, const double* tau_dev, int mode, double* S_dev,
+                              double* F_dev, double* metrics_dev, cudaStream_t s) {
+  LRT_TRY(lrtddft_chi0_assemble(c, 0, c->nq, s));
+  LRT_TRY(lrtddft_dyson_solve(c, 0, c->nq, s));
+  LRT_TRY(lrtddft_dsf_device(c, S_dev, s));
+  LRT_TRY(lrtddft_itcf_laplace_device(c, ntau, tau_dev, mode, F_dev, metrics_dev, s));
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_graph_capture(lrt_ctx* c, int ntau, const double* tau_dev, int mode,
+                                            double* S_dev, double* F_dev, double* metrics_dev) {
+  if (!c || !tau_dev || !S_dev || !F_dev || !metrics_dev) return bad("NULL argument");
+  if (ntau < 1) return bad("ntau must be >= 1");
+  if (mode != LRT_ITCF_FOLD && mode != LRT_ITCF_DIRECT) return bad("unknown ITCF mode");
+  LRT_TRY(need_device(c));
+  LRT_CUDA(cudaDeviceSynchronize());
+  cudaStream_t st = nullptr;
+  LRT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  auto done = [&](lrt_status r) {
+    cudaStreamDestroy(st);
+    return r;
+  };
+  // an ordinary pass first: plans, buffers, attributes and tuning all settle here
+  lrt_status r = forward_all(c, ntau, tau_dev, mode, S_dev, F_dev, metrics_dev, st);
+  if (r != LRT_OK) return done(r);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return done(LRT_ECUDA);
+  r = check_status_word(c);
+  if (r != LRT_OK) return done(r);
+  const bool prof = c->profiling;
+  c->profiling = false;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    c->profiling = prof;
+    set_error("stream capture did not start");
+    return done(LRT_ECUDA);
+  }
+  r = forward_all(c, ntau, tau_dev, mode, S_dev, F_dev, metrics_dev, st);
+  cudaError_t ee = cudaStreamEndCapture(st, &g);
+  c->profiling = prof;
+  if (r != LRT_OK || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (r == LRT_OK) {
+      set_error(std::string("stream capture: ") + cudaGetErrorString(ee));
+      r = LRT_ECUDA;
+    }
+    return done(r);
+  }
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    c->graph = nullptr;
+    set_error(std::string("graph instantiation: ") + cudaGetErrorString(ie));
+    return done(LRT_ECUDA);
+  }
+  c->graph_valid = true;
+  return done(LRT_OK);
+}
+
+extern "C" lrt_status lrtddft_graph_launch(lrt_ctx* c, void* stream) {
+  if (!c) return bad("NULL context");
+  if (!c->graph || !c->graph_valid) {
+    set_error("no valid captured graph (capture again after set_params, set_orbitals or set_tuning)");
+    return LRT_ESTATE;
+  }
+  LRT_CUDA(cudaSetDevice(c->device));
+  LRT_CUDA(cudaGraphLaunch(c->graph, (cudaStream_t)stream));
+  for (auto& Q : c->qd) {
+    Q.have_chi0 = Q.have_chi = true;
+    Q.have_dchi = false;
   }
   return LRT_OK;
 }

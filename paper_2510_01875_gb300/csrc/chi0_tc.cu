@@ -36,6 +36,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <map>
 #include <vector>
 
 #include "lrt_internal.h"
@@ -48,8 +50,6 @@ constexpr int NACC = 2;            // accumulators (row tiles) per CTA
 constexpr int TN = 256;            // MMA N: columns per tile (128 frequencies), shared by the pair
 constexpr int TNH = TN / 2;        // B columns built by each CTA of the pair
 constexpr int KS = 32;             // pairs (K) per pipeline stage
-constexpr int NS = 4;              // operand (A/B) stages
-constexpr int NSR = 2;             // prefetch stages of rho blocks and pair weights
 constexpr int GBLK = 8;            // G per block of the blocked rho layout
 constexpr int MAXBLK = 6;          // G blocks one row super-tile may touch
 constexpr int RROWS = MAXBLK * GBLK;
@@ -72,7 +72,8 @@ constexpr unsigned long long kTimeoutNs = 2000000000ull;
 constexpr int kFlushStages = 64;   // FP32 accumulation period: 64 stages = 2048 pairs
 constexpr int NCHUNK = NACC * TN / 16;  // 16-column pieces of the accumulators per lane
 
-struct Params {
+// One q of a launch: its pair densities, weights, tables and FP64 sums.
+struct QDesc {
   const float2* rho;          // blocked [ld/32][gpad][32]
   const float4* pw;           // [np rounded up to 32] {Delta_hi, Delta_lo, df sB, 0}
   const int2* rowtab;         // [n_st * NSUB] ring rows of the G quads of each sub-block
@@ -80,15 +81,19 @@ struct Params {
   const float4* wtab;         // [n_n * 64] per frequency pair {hi_f, hi_f+1, lo_f, lo_f+1}
                               // (CTA r of a pair builds the columns of pairs 32 r .. 32 r + 31)
   double* C;                  // [n_n * TN][ldr] FP64 sums, column-major
-  float4* stage;              // [gridDim.x][4 warps][NCHUNK][4][32 lanes] accumulator staging
-  int* status;
   long long np;
   long long ldr;              // = n_st * NACC * TM (n_st even: super-tile 2 st2 + r is CTA r's)
-  int gpad;
-  int rows_valid;             // 2 * row pairs
-  int cols_valid;             // 2 * nwi
-  int n_st2, n_n, n_split;    // super-tile pairs, column tiles, pair ranges
   long long k_per_split;      // multiple of KS
+  int gpad;
+  int n_st2, n_n, n_split;    // super-tile pairs, column tiles, pair ranges
+};
+
+struct Params {
+  const QDesc* qd;            // [nq of the launch]
+  const int2* units;          // [nunits] (q of the launch, unit within the q), q-major
+  int nunits;
+  float4* stage;              // [gridDim.x][4 warps][NCHUNK][4][32 lanes] accumulator staging
+  int* status;
   int flush;                  // stages per accumulator period
   float eta;
 };
@@ -321,17 +326,18 @@ struct Unit {
   int st2, nt;
   long long kb, ke;
 };
-__device__ __forceinline__ Unit unit_of(const Params& P, int u) {
+__device__ __forceinline__ Unit unit_of(const QDesc& D, int u) {
   Unit U;
-  int tile = u / P.n_split, ks = u % P.n_split;
-  U.st2 = tile / P.n_n;
-  U.nt = tile % P.n_n;
-  U.kb = (long long)ks * P.k_per_split;
-  U.ke = min(P.np, U.kb + P.k_per_split);
+  int tile = u / D.n_split, ks = u % D.n_split;
+  U.st2 = tile / D.n_n;
+  U.nt = tile % D.n_n;
+  U.kb = (long long)ks * D.k_per_split;
+  U.ke = min(D.np, U.kb + D.k_per_split);
   return U;
 }
 
-template <bool BF>
+// NS: operand (A/B) stages; NSR: prefetch stages of rho blocks and pair weights.
+template <bool BF, int NS, int NSR>
 __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   extern __shared__ uint8_t smem_raw[];
   // full[s]: this CTA's producers arrive; in the even CTA also the odd CTA's relay.
@@ -379,26 +385,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
   const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
-  const int nunits = P.n_st2 * P.n_n * P.n_split;
+  const int nunits = P.nunits;
   const uint32_t idesc = (1u << 4) | ((BF ? 1u : 0u) << 7) | ((BF ? 1u : 0u) << 10) | (1u << 15) |
                          (1u << 16) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)((2 * TM) >> 4) << 24);
 
   uint32_t it = 0;   // stage counter (producers, loader, MMA)
   uint32_t pc = 0;   // accumulator period counter (MMA and epilogue)
   for (int u = cid; u < nunits; u += ncl) {
-    const Unit U = unit_of(P, u);
+    const int2 uu = P.units[u];
+    const QDesc& D = P.qd[uu.x];
+    const Unit U = unit_of(D, uu.y);
     const int st = 2 * U.st2 + (int)rank;   // this CTA's row super-tile
     // per-unit tables (row pairs and G blocks of the super-tile, frequencies of the column tile)
     __syncthreads();
     if (threadIdx.x < NSUB) {
-      const int2 g = P.rowtab[st * NSUB + threadIdx.x];
+      const int2 g = D.rowtab[st * NSUB + threadIdx.x];
       rowtab_s[threadIdx.x] = make_int2(g.x * KS * 8, g.y * KS * 8);
     }
-    if (threadIdx.x < TNH / 4) wtab_s[threadIdx.x] = P.wtab[U.nt * 64 + rank * (TNH / 4) + threadIdx.x];
-    if (threadIdx.x < MAXBLK) blk_s[threadIdx.x] = P.blk[st * MAXBLK + threadIdx.x];
+    if (threadIdx.x < TNH / 4) wtab_s[threadIdx.x] = D.wtab[U.nt * 64 + rank * (TNH / 4) + threadIdx.x];
+    if (threadIdx.x < MAXBLK) blk_s[threadIdx.x] = D.blk[st * MAXBLK + threadIdx.x];
     if (threadIdx.x == 0) {
       int n = 0;
-      while (n < MAXBLK && P.blk[st * MAXBLK + n] >= 0) ++n;
+      while (n < MAXBLK && D.blk[st * MAXBLK + n] >= 0) ++n;
       nblk_s = n;
     }
     __syncthreads();
@@ -506,16 +514,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       if (lane == 0) {
         const int nb = nblk_s;
         const uint32_t bytes = (uint32_t)(nb * RBLK_BYTES + KS * 16);
+        const float2* rho = D.rho;
+        const float4* pwg = D.pw;
+        const long long gpad = D.gpad;
         for (int st_ = 0; st_ < nstage; ++st_, ++it) {
           const int sr = it % NSR;
           if (!mbar_wait(&rempty[sr], ((it / NSR) & 1) ^ 1, &abort_s, P.status)) break;
           const long long p0 = U.kb + (long long)st_ * KS;
           mbar_expect_tx(&rfull[sr], bytes);
           const uint32_t dst = rbase + sr * R_STAGE;
-          const float2* src = P.rho + (size_t)(p0 >> 5) * P.gpad * KS;
+          const float2* src = rho + (size_t)(p0 >> 5) * gpad * KS;
           for (int i = 0; i < nb; ++i)
             bulk_g2s(dst + i * RBLK_BYTES, src + (size_t)blk_s[i] * GBLK * KS, RBLK_BYTES, &rfull[sr]);
-          bulk_g2s(dst + PW_OFF, P.pw + p0, KS * 16, &rfull[sr]);
+          bulk_g2s(dst + PW_OFF, pwg + p0, KS * 16, &rfull[sr]);
         }
       }
       it = __shfl_sync(0xffffffffu, it, 0);
@@ -594,7 +605,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       const int q = warp & 3;            // tensor-memory lane quadrant of this warp
       float4* stg = P.stage + ((size_t)blockIdx.x * 4 + q) * (NCHUNK * 4 * 32) + lane;
       const long long grow0 = (long long)st * (NACC * TM) + q * 32 + lane;
-      double* cbase = P.C + (size_t)(U.nt * TN) * P.ldr;
+      const size_t ldr = (size_t)D.ldr;
+      double* cbase = D.C + (size_t)(U.nt * TN) * ldr;
       const uint32_t acc_empty0 = cluster_addr(&acc_empty[0], 0);
       for (int per = 0; per < nper; ++per, ++pc) {
         bool ok = true;
@@ -634,8 +646,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
           float4 v[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) v[k] = sp[32 * k];
-          double* cp = cbase + (size_t)(c * 16) * P.ldr + grow0 + a * TM;
-          const size_t ldr = (size_t)P.ldr;
+          double* cp = cbase + (size_t)(c * 16) * ldr + grow0 + a * TM;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             red_add_f64(cp, (double)v[k].x);
@@ -718,12 +729,109 @@ __global__ void pair_weights_split(const double* __restrict__ eps, const double*
 
 }  // namespace
 
-lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
-  const int nG = q.nG;
-  if (c->np <= 0) {
-    set_error("no pairs to contract");
-    return LRT_EINVAL;
+// ------------------------------------------------------------------ host side
+namespace {
+
+// Kernel variants (ring depths) the tuner chooses from, and the unit sizes (stages per unit).
+struct Variant {
+  int ns, nsr;
+};
+constexpr Variant kVariants[] = {{4, 2}, {3, 4}};
+constexpr int kNumVariants = 2;
+constexpr int kUnitStages[] = {4096, 1024, 16384};
+constexpr int kNumUnitStages = 3;
+
+size_t smem_of(int v) {
+  return (size_t)kVariants[v].ns * STAGE_BYTES + (size_t)kVariants[v].nsr * R_STAGE + 1024;
+}
+typedef void (*KernFn)(Params);
+KernFn kernel_of(bool bf, int v) {
+  if (bf) return v == 0 ? chi0_tc_kernel<true, 4, 2> : chi0_tc_kernel<true, 3, 4>;
+  return v == 0 ? chi0_tc_kernel<false, 4, 2> : chi0_tc_kernel<false, 3, 4>;
+}
+
+// Per-context state of the tensor path (owned through lrt_ctx::tc).
+struct TcState {
+  QDesc* d_qdesc = nullptr;
+  int qdesc_cap = 0;
+  int2* d_units = nullptr;
+  int units_cap = 0;
+  std::vector<QDesc> qdesc_h;      // what d_qdesc holds
+  std::vector<int2> units_h;       // what d_units holds
+  float4* stage = nullptr;
+  size_t stage_bytes = 0;
+  int ncl[2][kNumVariants] = {{0, 0}, {0, 0}};   // resident CTA pairs per (bf, variant)
+  std::map<std::vector<long long>, std::pair<int, int>> tuned;   // shape -> (variant, unit idx)
+};
+
+TcState* tc_of(const lrt_ctx* c) {
+  lrt_ctx* cc = const_cast<lrt_ctx*>(c);
+  if (!cc->tc) cc->tc = new TcState();
+  return static_cast<TcState*>(cc->tc);
+}
+
+lrt_status cluster_capacity(const lrt_ctx* c, bool bf, int v, int* out) {
+  TcState* T = tc_of(c);
+  if (T->ncl[bf][v] > 0) {
+    *out = T->ncl[bf][v];
+    return LRT_OK;
   }
+  KernFn kern = kernel_of(bf, v);
+  const size_t smem = smem_of(v);
+  LRT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int dev = 0, nsm = 0, n = 0;
+  LRT_CUDA(cudaGetDevice(&dev));
+  LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  cfg.gridDim = dim3(2 * (nsm / 2));
+  LRT_CUDA(cudaOccupancyMaxActiveClusters(&n, (const void*)kern, &cfg));
+  if (n < 1) {
+    set_error("the chi0 tensor kernel cannot be resident as a CTA pair");
+    return LRT_EUNSUPPORTED;
+  }
+  T->ncl[bf][v] = n;
+  *out = n;
+  return LRT_OK;
+}
+
+}  // namespace
+
+void free_tc_state(lrt_ctx* c) {
+  if (!c->tc) return;
+  TcState* T = static_cast<TcState*>(c->tc);
+  cudaFree(T->d_qdesc);
+  cudaFree(T->d_units);
+  cudaFree(T->stage);
+  delete T;
+  c->tc = nullptr;
+}
+
+void free_split_plan(SplitPlan& sp) {
+  cudaFree(sp.rowtab);
+  cudaFree(sp.blk);
+  cudaFree(sp.rp_of);
+  cudaFree(sp.wtab);
+  cudaFree(sp.pw);
+  cudaFree(sp.C);
+  cudaFree(sp.rho);
+  sp = SplitPlan();
+}
+
+// Tables of one q, built once: row super-tiles (4 x 4 sub-blocks of G quads), G blocks,
+// frequency pairs, the unpack map, and the weight and FP64-sum buffers.
+static lrt_status build_plan(const lrt_ctx* c, QData& q) {
+  SplitPlan& P = q.sp;
+  if (P.built) return LRT_OK;
+  const int nG = q.nG;
   if (c->rho_gpad < (nG + GBLK - 1) / GBLK * GBLK) {
     set_error("pair densities are not in the blocked layout");
     return LRT_ESTATE;
@@ -745,7 +853,6 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
   // an even number of super-tiles: CTA r of a pair takes super-tile 2 st2 + r (a padding
   // super-tile reads G block 0 and fills rows that are never read)
   const int n_st = ((nsub + NSUB - 1) / NSUB + 1) / 2 * 2;
-  const int n_st2 = n_st / 2;
   std::vector<int2> rowtab((size_t)n_st * NSUB, make_int2(0, 0));
   std::vector<int> blk((size_t)n_st * MAXBLK, -1);
   std::vector<int> rp_of((size_t)nG * nG, 0);
@@ -753,13 +860,13 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
     int* bl = &blk[(size_t)t * MAXBLK];
     int n = 0;
     if (t * NSUB >= nsub) bl[0] = 0;
-    auto slot = [&](int q) {   // ring row of the first G of quad q
-      const int b = q / 2;
+    auto slot = [&](int qq) {   // ring row of the first G of quad qq
+      const int b = qq / 2;
       for (int i = 0; i < n; ++i)
-        if (bl[i] == b) return i * GBLK + 4 * (q % 2);
+        if (bl[i] == b) return i * GBLK + 4 * (qq % 2);
       if (n == MAXBLK) return -1;
       bl[n] = b;
-      return (n++) * GBLK + 4 * (q % 2);
+      return (n++) * GBLK + 4 * (qq % 2);
     };
     for (int w = 0; w < NSUB && t * NSUB + w < nsub; ++w) {
       const int2 qq = sub[t * NSUB + w];
@@ -779,8 +886,7 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
         }
     }
   }
-  const int ncols = 2 * c->nwi;
-  const int n_n = (ncols + TN - 1) / TN;
+  const int n_n = (2 * c->nwi + TN - 1) / TN;
   std::vector<float4> wtab((size_t)n_n * 64, make_float4(0.f, 0.f, 0.f, 0.f));
   for (int j = 0; j < c->nwi; ++j) {
     // frequency pair j / 2 of its column tile: {hi_f, hi_f+1, lo_f, lo_f+1}
@@ -789,130 +895,312 @@ lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s) {
     w4[j % 2] = h;
     w4[2 + j % 2] = l;
   }
-  const bool bf = c->precision == LRT_PREC_BF16X3;
-  // power-of-two scales that keep the FP16 low parts clear of the subnormal range: the pair
-  // densities carry split_rho_scale() (so P carries its square, sA) and df carries sB
-  const float sA = split_rho_scale(c->precision) * split_rho_scale(c->precision);
-  float sB = 1.0f;
-  if (!bf) sB = std::ldexp(1.0f, (int)std::floor(std::log2(16384.0 * c->eta)));
-  const int ldc = n_n * TN;
-
-  const size_t smem = (size_t)NS * STAGE_BYTES + (size_t)NSR * R_STAGE + 1024;
-  auto kern = bf ? chi0_tc_kernel<true> : chi0_tc_kernel<false>;
-  LRT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  cudaLaunchAttribute cl_attr[1];
-  cl_attr[0].id = cudaLaunchAttributeClusterDimension;
-  cl_attr[0].val.clusterDim.x = 2;
-  cl_attr[0].val.clusterDim.y = 1;
-  cl_attr[0].val.clusterDim.z = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(NTHREADS);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cfg.attrs = cl_attr;
-  cfg.numAttrs = 1;
-  int dev = 0, nsm = 0, ncl_max = 0;
-  LRT_CUDA(cudaGetDevice(&dev));
-  LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  cfg.gridDim = dim3(2 * (nsm / 2));
-  LRT_CUDA(cudaOccupancyMaxActiveClusters(&ncl_max, (const void*)kern, &cfg));
-  if (ncl_max < 1) {
-    set_error("the chi0 tensor kernel cannot be resident as a CTA pair");
-    return LRT_EUNSUPPORTED;
-  }
-  const long long tiles = (long long)n_st2 * n_n;
-  // pair splits: at least 4 units per CTA pair, chosen to fill the last round
-  long long best_split = 1;
-  double best_eff = 0.0;
-  const long long max_split = std::max<long long>(1, c->np / (KS * 64));
-  for (long long sp = std::max<long long>(1, (4LL * ncl_max + tiles - 1) / tiles);
-       sp <= 8LL * ncl_max / std::max<long long>(1, tiles) + 8 && sp <= max_split; ++sp) {
-    long long units = tiles * sp;
-    double eff = (double)units / (double)(((units + ncl_max - 1) / ncl_max) * ncl_max);
-    if (eff > best_eff + 1e-9) {
-      best_eff = eff;
-      best_split = sp;
-    }
-  }
-  long long kps = (c->np + best_split - 1) / best_split;
-  kps = (kps + KS - 1) / KS * KS;
-  const int n_split = (int)((c->np + kps - 1) / kps);
-
-  // device buffer: C (column-major FP64 sums)
-  const long long ldr = (long long)n_st * NACC * TM;
-  const long long units = tiles * n_split;
-  const int grid = 2 * (int)std::min<long long>(ncl_max, units);
-  const size_t c_bytes = (size_t)ldr * ldc * sizeof(double);
-  const size_t stage_bytes = (size_t)grid * 4 * NCHUNK * 4 * 32 * sizeof(float4);
-  const size_t need = c_bytes + stage_bytes;
-  DeviceWork& dw = const_cast<DeviceWork&>(c->dw);
-  if (dw.scratch_bytes < need) {
-    cudaFree(dw.scratch);
-    dw.scratch = nullptr;
-    dw.scratch_bytes = 0;
-    LRT_CUDA(cudaMalloc(&dw.scratch, need));
-    dw.scratch_bytes = need;
-  }
-  int2* d_rowtab = nullptr;
-  int* d_blk = nullptr;
-  int* d_rp = nullptr;
-  float4* d_wtab = nullptr;
-  float4* d_pw = nullptr;
-  // pair weights padded to whole 32-pair stages (the bulk copies read full stages)
-  const size_t npw_pad = (size_t)((c->np + KS - 1) / KS * KS);
-  LRT_CUDA(cudaMallocAsync(&d_rowtab, rowtab.size() * sizeof(int2), s));
-  LRT_CUDA(cudaMallocAsync(&d_blk, blk.size() * sizeof(int), s));
-  LRT_CUDA(cudaMallocAsync(&d_rp, rp_of.size() * sizeof(int), s));
-  LRT_CUDA(cudaMallocAsync(&d_wtab, wtab.size() * sizeof(float4), s));
-  LRT_CUDA(cudaMallocAsync(&d_pw, npw_pad * sizeof(float4), s));
-  LRT_CUDA(cudaMemsetAsync(d_pw, 0, npw_pad * sizeof(float4), s));
-  LRT_CUDA(cudaMemcpyAsync(d_rowtab, rowtab.data(), rowtab.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-  LRT_CUDA(cudaMemcpyAsync(d_blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  LRT_CUDA(cudaMemcpyAsync(d_rp, rp_of.data(), rp_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  LRT_CUDA(cudaMemcpyAsync(d_wtab, wtab.data(), wtab.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
-  pair_weights_split<<<4 * nsm, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, sB, d_pw);
-  LRT_CUDA(cudaGetLastError());
-  LRT_CUDA(cudaMemsetAsync(dw.scratch, 0, c_bytes, s));
-
-  Params P;
-  P.rho = (const float2*)dw.rho;
-  P.pw = d_pw;
-  P.rowtab = d_rowtab;
-  P.blk = d_blk;
-  P.wtab = d_wtab;
-  P.C = dw.scratch;
-  P.stage = reinterpret_cast<float4*>(dw.scratch + (size_t)ldr * ldc);
-  P.status = dw.status;
-  P.np = c->np;
-  P.ldr = ldr;
-  P.gpad = c->rho_gpad;
-  P.rows_valid = 2 * nsub * 16;
-  P.cols_valid = ncols;
-  P.n_st2 = n_st2;
+  P.nsub = nsub;
+  P.n_st2 = n_st / 2;
   P.n_n = n_n;
-  P.n_split = n_split;
-  P.k_per_split = kps;
+  P.ldc = n_n * TN;
+  P.ldr = (long long)n_st * NACC * TM;
+  P.pw_n = (size_t)((c->np + KS - 1) / KS * KS);
+  auto fail = [&](cudaError_t e) {
+    free_split_plan(P);
+    set_error(std::string("chi0 plan: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LRT_ENOMEM : LRT_ECUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&P.rowtab, rowtab.size() * sizeof(int2))) != cudaSuccess ||
+      (e = cudaMalloc(&P.blk, blk.size() * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&P.rp_of, rp_of.size() * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&P.wtab, wtab.size() * sizeof(float4))) != cudaSuccess ||
+      (e = cudaMalloc(&P.pw, P.pw_n * sizeof(float4))) != cudaSuccess ||
+      (e = cudaMalloc(&P.C, (size_t)P.ldr * P.ldc * sizeof(double))) != cudaSuccess)
+    return fail(e);
+  if ((e = cudaMemcpy(P.rowtab, rowtab.data(), rowtab.size() * sizeof(int2), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(P.blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(P.rp_of, rp_of.data(), rp_of.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(P.wtab, wtab.data(), wtab.size() * sizeof(float4), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemset(P.pw, 0, P.pw_n * sizeof(float4))) != cudaSuccess)
+    return fail(e);
+  P.built = true;
+  return LRT_OK;
+}
+
+// power-of-two scales that keep the FP16 low parts clear of the subnormal range: the pair
+// densities carry split_rho_scale() (so P carries its square, sA) and df carries sB
+static double scale_A(const lrt_ctx* c) {
+  const double r = split_rho_scale(c->precision);
+  return r * r;
+}
+static float scale_B(const lrt_ctx* c) {
+  if (c->precision == LRT_PREC_BF16X3) return 1.0f;
+  return std::ldexp(1.0f, (int)std::floor(std::log2(16384.0 * c->eta)));
+}
+
+// Units of one q for a target of `stages` per unit (a multiple of the accumulator period).
+static void split_q(const lrt_ctx* c, const SplitPlan& P, int stages, int* n_split, long long* kps) {
+  const long long nst = (c->np + KS - 1) / KS;
+  long long sp = std::max<long long>(1, (nst + stages / 2) / stages);
+  long long k = (c->np + sp - 1) / sp;
+  k = (k + (long long)KS * kFlushStages - 1) / ((long long)KS * kFlushStages) * ((long long)KS * kFlushStages);
+  *kps = k;
+  *n_split = (int)((c->np + k - 1) / k);
+  (void)P;
+}
+
+// Descriptor and unit tables of a launch (q-major), uploaded when they changed.
+static lrt_status upload_tables(const lrt_ctx* c, const std::vector<int>& qs,
+                                const std::vector<const void*>& rhos, int stages, int limit_units,
+                                int* nunits, cudaStream_t s) {
+  TcState* T = tc_of(c);
+  std::vector<QDesc> qd(qs.size());
+  std::vector<int2> units;
+  for (size_t i = 0; i < qs.size(); ++i) {
+    const QData& q = c->qd[qs[i]];
+    const SplitPlan& P = q.sp;
+    QDesc& D = qd[i];
+    D.rho = (const float2*)rhos[i];
+    D.pw = P.pw;
+    D.rowtab = P.rowtab;
+    D.blk = P.blk;
+    D.wtab = P.wtab;
+    D.C = P.C;
+    D.np = c->np;
+    D.ldr = P.ldr;
+    D.gpad = c->rho_gpad;
+    D.n_st2 = P.n_st2;
+    D.n_n = P.n_n;
+    split_q(c, P, stages, &D.n_split, &D.k_per_split);
+    const int nu = D.n_st2 * D.n_n * D.n_split;
+    for (int u = 0; u < nu; ++u) units.push_back(make_int2((int)i, u));
+  }
+  if (limit_units > 0 && (int)units.size() > limit_units) units.resize(limit_units);
+  *nunits = (int)units.size();
+  const bool same = qd.size() == T->qdesc_h.size() && units.size() == T->units_h.size() &&
+                    std::memcmp(qd.data(), T->qdesc_h.data(), qd.size() * sizeof(QDesc)) == 0 &&
+                    std::memcmp(units.data(), T->units_h.data(), units.size() * sizeof(int2)) == 0;
+  if (same) return LRT_OK;
+  if ((int)qd.size() > T->qdesc_cap) {
+    cudaFree(T->d_qdesc);
+    T->d_qdesc = nullptr;
+    T->qdesc_cap = 0;
+    LRT_CUDA(cudaMalloc(&T->d_qdesc, qd.size() * sizeof(QDesc)));
+    T->qdesc_cap = (int)qd.size();
+  }
+  if ((int)units.size() > T->units_cap) {
+    cudaFree(T->d_units);
+    T->d_units = nullptr;
+    T->units_cap = 0;
+    LRT_CUDA(cudaMalloc(&T->d_units, units.size() * sizeof(int2)));
+    T->units_cap = (int)units.size();
+  }
+  // the host copies stay in the state, so a captured graph may refer to them
+  T->qdesc_h = qd;
+  T->units_h = units;
+  LRT_CUDA(cudaMemcpyAsync(T->d_qdesc, T->qdesc_h.data(), qd.size() * sizeof(QDesc),
+                           cudaMemcpyHostToDevice, s));
+  LRT_CUDA(cudaMemcpyAsync(T->d_units, T->units_h.data(), units.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, s));
+  return LRT_OK;
+}
+
+static lrt_status launch_tables(const lrt_ctx* c, bool bf, int v, int nunits, cudaStream_t s,
+                                bool timed) {
+  TcState* T = tc_of(c);
+  int ncl = 0;
+  LRT_TRY(cluster_capacity(c, bf, v, &ncl));
+  const int grid = 2 * std::min(ncl, std::max(1, nunits));
+  const size_t need = (size_t)grid * 4 * NCHUNK * 4 * 32 * sizeof(float4);
+  if (T->stage_bytes < need) {
+    cudaFree(T->stage);
+    T->stage = nullptr;
+    T->stage_bytes = 0;
+    LRT_CUDA(cudaMalloc(&T->stage, need));
+    T->stage_bytes = need;
+  }
+  Params P;
+  P.qd = T->d_qdesc;
+  P.units = T->d_units;
+  P.nunits = nunits;
+  P.stage = T->stage;
+  P.status = c->dw.status;
   P.flush = kFlushStages;
   P.eta = (float)c->eta;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  {
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem_of(v);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (timed) {
     TimedLaunch tl(c, &c->ev_chi0, s);
-    LRT_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
+    LRT_CUDA(cudaLaunchKernelEx(&cfg, kernel_of(bf, v), P));
+  } else {
+    LRT_CUDA(cudaLaunchKernelEx(&cfg, kernel_of(bf, v), P));
   }
-  count_launch(c, 2);   // pair_weights_split + the contraction
-  if (c->profiling) c->timed_cmac += (double)nG * nG * c->nw * (double)c->np;
-  LRT_CUDA(cudaGetLastError());
-  const double scale = 2.0 / (c->nk * c->volume) / ((double)sA * (double)sB);
-  long long total = (long long)c->nwi * nG * nG;
-  chi0_unpack<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dw.scratch, ldr, d_rp, nG, c->nwi, scale,
-                                                             q.chi0);
+  return LRT_OK;
+}
+
+// Variant and unit size for a launch: forced by the caller, tuned once per shape (each
+// candidate timed on the first units of the launch), or the defaults.
+static lrt_status choose(const lrt_ctx* c, const std::vector<int>& qs,
+                         const std::vector<const void*>& rhos, bool bf, cudaStream_t s, int* v,
+                         int* ui) {
+  *v = c->tune_variant >= 0 ? c->tune_variant : 0;
+  *ui = 0;
+  if (c->tune_unit_stages > 0) {
+    // forced unit size: use it directly (index -1 means "the forced value")
+    *ui = -1;
+  }
+  if (!c->autotune || c->tune_variant >= 0 || c->tune_unit_stages > 0) return LRT_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  LRT_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return LRT_OK;   // no timing inside a capture
+  TcState* T = tc_of(c);
+  std::vector<long long> key = {bf ? 1 : 0, c->np, c->nwi};
+  for (int qi : qs) key.push_back(c->qd[qi].nG);
+  auto it = T->tuned.find(key);
+  if (it != T->tuned.end()) {
+    *v = it->second.first;
+    *ui = it->second.second;
+    return LRT_OK;
+  }
+  cudaEvent_t e0, e1;
+  LRT_CUDA(cudaEventCreate(&e0));
+  LRT_CUDA(cudaEventCreate(&e1));
+  double best = 1e300;
+  for (int cv = 0; cv < kNumVariants; ++cv) {
+    int ncl = 0;
+    LRT_TRY(cluster_capacity(c, bf, cv, &ncl));
+    for (int cu = 0; cu < kNumUnitStages; ++cu) {
+      int nunits = 0;
+      LRT_TRY(upload_tables(c, qs, rhos, kUnitStages[cu], 2 * ncl, &nunits, s));
+      // time per stage of the first 2 rounds of units (a warm-up launch first)
+      LRT_TRY(launch_tables(c, bf, cv, nunits, s, false));
+      LRT_CUDA(cudaEventRecord(e0, s));
+      LRT_TRY(launch_tables(c, bf, cv, nunits, s, false));
+      LRT_CUDA(cudaEventRecord(e1, s));
+      LRT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      LRT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      long long stages = 0;
+      TcState* TT = tc_of(c);
+      for (int u = 0; u < nunits; ++u) {
+        const QDesc& D = TT->qdesc_h[TT->units_h[u].x];
+        const long long kb = (long long)(TT->units_h[u].y % D.n_split) * D.k_per_split;
+        stages += (std::min(D.np, kb + D.k_per_split) - kb + KS - 1) / KS;
+      }
+      const double per = ms / (double)std::max(1LL, stages);
+      if (per < best) {
+        best = per;
+        *v = cv;
+        *ui = cu;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  T->tuned[key] = std::make_pair(*v, *ui);
+  // the trial launches added into the sums: clear them
+  for (int qi : qs) {
+    const SplitPlan& P = c->qd[qi].sp;
+    LRT_CUDA(cudaMemsetAsync(P.C, 0, (size_t)P.ldr * P.ldc * sizeof(double), s));
+  }
+  return LRT_OK;
+}
+
+// One tensor launch for the q's `qs` (pair densities in rhos[i]), then the unpack of each.
+static lrt_status launch_group(const lrt_ctx* c, const std::vector<int>& qs,
+                               const std::vector<const void*>& rhos, cudaStream_t s) {
+  const bool bf = c->precision == LRT_PREC_BF16X3;
+  int v = 0, ui = 0;
+  LRT_TRY(choose(c, qs, rhos, bf, s, &v, &ui));
+  const int stages = ui < 0 ? c->tune_unit_stages : kUnitStages[ui];
+  int nunits = 0;
+  LRT_TRY(upload_tables(c, qs, rhos, stages, 0, &nunits, s));
+  LRT_TRY(launch_tables(c, bf, v, nunits, s, true));
   count_launch(c);
-  LRT_CUDA(cudaGetLastError());
-  LRT_CUDA(cudaFreeAsync(d_rowtab, s));
-  LRT_CUDA(cudaFreeAsync(d_blk, s));
-  LRT_CUDA(cudaFreeAsync(d_rp, s));
-  LRT_CUDA(cudaFreeAsync(d_wtab, s));
-  LRT_CUDA(cudaFreeAsync(d_pw, s));
+  if (c->profiling)
+    for (int qi : qs) c->timed_cmac += (double)c->qd[qi].nG * c->qd[qi].nG * c->nw * (double)c->np;
+  const double scale = 2.0 / (c->nk * c->volume) / (scale_A(c) * (double)scale_B(c));
+  for (int qi : qs) {
+    QData& q = const_cast<lrt_ctx*>(c)->qd[qi];
+    const int nG = q.nG;
+    long long total = (long long)c->nwi * nG * nG;
+    chi0_unpack<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(q.sp.C, q.sp.ldr, q.sp.rp_of, nG,
+                                                               c->nwi, scale, q.chi0);
+    count_launch(c);
+    LRT_CUDA(cudaGetLastError());
+  }
+  const_cast<lrt_ctx*>(c)->last_tc_variant = v;
+  const_cast<lrt_ctx*>(c)->last_tc_unit_stages = stages;
+  return LRT_OK;
+}
+
+// chi0 of q_begin .. q_end - 1 on the tensor path.  q's whose pair densities fit in their own
+// buffers next to the others' run in one launch; the rest run one at a time in the shared
+// pair-density buffer.
+lrt_status launch_chi0_split_range(lrt_ctx* c, int q_begin, int q_end, cudaStream_t s) {
+  if (c->np <= 0) {
+    set_error("no pairs to contract");
+    return LRT_EINVAL;
+  }
+  const float sB = scale_B(c);
+  const size_t rho_bytes = (size_t)c->rho_gpad * c->rho_ld * sizeof(float2);
+  std::vector<int> grp, solo;
+  bool fresh = false;
+  for (int iq = q_begin; iq < q_end; ++iq) {
+    QData& q = c->qd[iq];
+    LRT_TRY(build_plan(c, q));
+    if (!q.sp.rho && c->multi_q) {
+      size_t fr = 0, tot = 0;
+      LRT_CUDA(cudaMemGetInfo(&fr, &tot));
+      // keep 8 GB free for everything else
+      if (fr > rho_bytes + ((size_t)8 << 30)) {
+        if (cudaMalloc(&q.sp.rho, rho_bytes) == cudaSuccess) {
+          if (cudaMemset(q.sp.rho, 0, rho_bytes) != cudaSuccess) return LRT_ECUDA;
+          fresh = true;
+        } else {
+          cudaGetLastError();
+          q.sp.rho = nullptr;
+        }
+      }
+    }
+    (q.sp.rho ? grp : solo).push_back(iq);
+  }
+  if (!solo.empty()) LRT_TRY(ensure_rho(c));
+  if (fresh) LRT_CUDA(cudaDeviceSynchronize());   // the zeroed new buffers are ready
+  int dev = 0, nsm = 0;
+  LRT_CUDA(cudaGetDevice(&dev));
+  LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  auto prep = [&](int iq, void* rho) -> lrt_status {
+    QData& q = c->qd[iq];
+    pair_weights_split<<<4 * nsm, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, sB, q.sp.pw);
+    count_launch(c);
+    LRT_CUDA(cudaGetLastError());
+    LRT_TRY(launch_pair_density(c, q, rho, true, s));
+    LRT_CUDA(cudaMemsetAsync(q.sp.C, 0, (size_t)q.sp.ldr * q.sp.ldc * sizeof(double), s));
+    return LRT_OK;
+  };
+  if (!grp.empty()) {
+    std::vector<const void*> rhos;
+    for (int iq : grp) {
+      LRT_TRY(prep(iq, c->qd[iq].sp.rho));
+      rhos.push_back(c->qd[iq].sp.rho);
+    }
+    LRT_TRY(launch_group(c, grp, rhos, s));
+  }
+  for (int iq : solo) {
+    LRT_TRY(prep(iq, c->dw.rho));
+    LRT_TRY(launch_group(c, std::vector<int>{iq}, std::vector<const void*>{c->dw.rho}, s));
+  }
   return LRT_OK;
 }
 

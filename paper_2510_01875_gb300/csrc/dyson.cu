@@ -129,8 +129,16 @@ lrt_status launch_dyson(const lrt_ctx* c, QData& q, int iq, cudaStream_t s) {
     lrt::set_error("Dyson: nG too large for the one-block solver");
     return LRT_EUNSUPPORTED;
   }
-  LRT_CUDA(cudaFuncSetAttribute(dyson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  // raised only when a call needs more than any earlier one on this device, so repeated
+  // calls (and a graph capture after a first pass) make no attribute call
+  static size_t attr_set[64] = {0};
+  int dev = 0;
+  LRT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || attr_set[dev] < smem) {
+    LRT_CUDA(cudaFuncSetAttribute(dyson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    if (dev >= 0 && dev < 64) attr_set[dev] = smem;
+  }
   dyson_kernel<<<c->nwi, 256, smem, s>>>(q.chi0, q.Kdev, N, q.chi, c->dw.status);
   count_launch(c);
   LRT_CUDA(cudaGetLastError());

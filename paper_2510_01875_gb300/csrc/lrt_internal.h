@@ -23,6 +23,22 @@ constexpr int kExtraBands = 8;         // eigenpairs kept beyond nbands to see s
 void set_error(const std::string& msg);
 const char* last_error();
 
+// Tables and buffers of one q on the tensor path, built on first use and kept (they depend on
+// the geometry and the frequency list only; weights and sums are refilled per assemble).
+struct SplitPlan {
+  bool built = false;
+  int nsub = 0, n_st2 = 0, n_n = 0, ldc = 0;
+  long long ldr = 0;
+  size_t pw_n = 0;
+  int2* rowtab = nullptr;         // [2 n_st2][8] ring rows of the G quads of each sub-block
+  int* blk = nullptr;             // [2 n_st2][6] G blocks per super-tile
+  int* rp_of = nullptr;           // [nG][nG] row pair of (G, G')
+  float4* wtab = nullptr;         // [n_n][64] frequency pairs (hi, hi, lo, lo)
+  float4* pw = nullptr;           // [pw_n] (Delta_hi, Delta_lo, df sB, 0)
+  double* C = nullptr;            // [ldc][ldr] FP64 sums, column-major
+  void* rho = nullptr;            // this q's own pair densities (multi-q launches), or null
+};
+
 // Per-q data.  Meshes are indexed s = 0 (k points) and s = 1 (k+q points).
 struct QData {
   int nG = 0;
@@ -47,6 +63,7 @@ struct QData {
   bool have_chi = false;
   std::vector<double> dchi;       // [nwi][5] complex: d chi_00/d(T, eta, A, B, C) (adjoint)
   bool have_dchi = false;
+  SplitPlan sp;                   // tensor-path tables of this q
 };
 
 struct DeviceWork {
@@ -109,6 +126,16 @@ struct lrt_ctx {
   bool profiling = false;
   mutable std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_chi0, ev_rho;
   mutable double timed_cmac = 0.0;
+  // tensor path: launch state, tuning (lrtddft_set_tuning) and the last choice made
+  void* tc = nullptr;
+  bool autotune = false;
+  bool multi_q = true;
+  int tune_variant = -1;          // forced kernel variant, -1: tuned or default
+  int tune_unit_stages = 0;       // forced stages per unit, 0: tuned or default
+  int last_tc_variant = -1, last_tc_unit_stages = 0;
+  // captured forward graph (lrtddft_graph_capture)
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
 };
 
 namespace lrt {
@@ -167,8 +194,13 @@ lrt_status launch_pair_weights(const lrt_ctx* c, const QData& q, cudaStream_t s)
 
 // chi0_fp64.cu
 lrt_status launch_chi0_fp64(const lrt_ctx* c, QData& q, cudaStream_t s);
-// chi0_tc.cu
-lrt_status launch_chi0_split(const lrt_ctx* c, QData& q, cudaStream_t s);
+// chi0_tc.cu: chi0 of q_begin .. q_end - 1 on the tensor path (one launch for all q whose
+// pair densities fit in their own buffers)
+lrt_status launch_chi0_split_range(lrt_ctx* c, int q_begin, int q_end, cudaStream_t s);
+void free_split_plan(SplitPlan& sp);
+void free_tc_state(lrt_ctx* c);
+// api.cu: the shared pair-density buffer
+lrt_status ensure_rho(lrt_ctx* c);
 
 // dyson.cu
 lrt_status launch_dyson(const lrt_ctx* c, QData& q, int iq, cudaStream_t s);
