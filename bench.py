@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--kmesh", type=int, default=0,
                     help="k mesh n^3 instead of 12^3 (small cases for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--autotune", action="store_true", help="let the library time its kernel variants")
+    ap.add_argument("--variant", type=int, default=-1, help="force a tensor-kernel variant (0, 1)")
+    ap.add_argument("--unit-stages", type=int, default=0, help="force the stages per work unit")
     return ap.parse_args()
 
 
@@ -184,6 +187,8 @@ def run_ours(args, world, rank, local, pg):
     t0 = time.time()
     ctx = binding.Context(wl, args.precision, device=local)
     setup_s = time.time() - t0
+    if args.precision != "fp64":
+        ctx.set_tuning(auto=args.autotune, variant=args.variant, unit_stages=args.unit_stages)
     dev = torch.device("cuda", local)
     ntau = wl.ntau
     tau = torch.linspace(0.0, 0.5 / wl.T, ntau, dtype=torch.float64, device=dev)
@@ -240,9 +245,13 @@ def run_ours(args, world, rank, local, pg):
     chi0_tflops = flops_per_cmac * prof["chi0_cmac"] / (prof["chi0_ms"] / 1e3) / 1e12
     roofline = {"bound": bound, "achieved": chi0_tflops, "peak": peak, "unit": unit,
                 "frac": chi0_tflops / peak,
-                "traffic": profiled_traffic(args.precision, ctx.nk * ctx.nb * ctx.nb),
+                # one launch covers every q of a chi0_assemble call when they fit together
+                "traffic": profiled_traffic(args.precision, ctx.nk * ctx.nb * ctx.nb * wl.nq * args.steps
+                                            / max(prof["chi0_launches"], 1)),
                 "kernel": "chi0_tc_kernel" if args.precision != "fp64" else "chi0_fp64_kernel",
                 "launch_ms": chi0_ms, "peak_source": peak_note,
+                "chi0_launches_per_step": prof["chi0_launches"] / args.steps,
+                "kernel_variant_and_unit_stages": list(ctx.get_tuning()) if args.precision != "fp64" else None,
                 "pair_density_ms_per_launch": prof["rho_ms"] / max(prof["rho_launches"], 1),
                 "chi0_share_of_step": prof["chi0_ms"] / (ms * args.steps)}
 

@@ -972,8 +972,11 @@ static lrt_status upload_tables(const lrt_ctx* c, const std::vector<int>& qs,
     D.n_st2 = P.n_st2;
     D.n_n = P.n_n;
     split_q(c, P, stages, &D.n_split, &D.k_per_split);
-    const int nu = D.n_st2 * D.n_n * D.n_split;
-    for (int u = 0; u < nu; ++u) units.push_back(make_int2((int)i, u));
+    // pair range by pair range, all tiles of a range together: the clusters running at the
+    // same time then read the same pair-density blocks (shared through L2 by the column tiles)
+    const int ntile = D.n_st2 * D.n_n;
+    for (int ks = 0; ks < D.n_split; ++ks)
+      for (int t = 0; t < ntile; ++t) units.push_back(make_int2((int)i, t * D.n_split + ks));
   }
   if (limit_units > 0 && (int)units.size() > limit_units) units.resize(limit_units);
   *nunits = (int)units.size();
