@@ -174,10 +174,13 @@ lrt_status lrtddft_itcf_laplace_device(lrt_ctx* ctx, int ntau, const double* tau
  *   flags: LRT_TUNE_AUTO      time each (variant, unit size) candidate on the first units of
  *                             the first launch of each shape and keep the fastest (results
  *                             then differ from the defaults at the rounding of the split form);
- *          LRT_TUNE_SINGLE_Q  one launch per q.
+ *          LRT_TUNE_SINGLE_Q  one launch per q;
+ *          LRT_TUNE_PAIR_SIMT pair densities on the FP32 SIMT kernel instead of the tensor
+ *                             cores (which need at most 128 bands; above that the SIMT kernel
+ *                             runs anyway).
  *   variant: -1 (tuned or default 0), 0 or 1;  unit_stages: 0 (tuned or default 4096) or a
  *   positive multiple of 64.  LRT_EINVAL otherwise.  Invalidates a captured graph. */
-enum { LRT_TUNE_AUTO = 1, LRT_TUNE_SINGLE_Q = 2 };
+enum { LRT_TUNE_AUTO = 1, LRT_TUNE_SINGLE_Q = 2, LRT_TUNE_PAIR_SIMT = 4 };
 lrt_status lrtddft_set_tuning(lrt_ctx* ctx, int flags, int variant, int unit_stages);
 /* The variant and unit size used by the last tensor-core launch (-1 and 0 before any). */
 lrt_status lrtddft_get_tuning(lrt_ctx* ctx, int* variant, int* unit_stages);
@@ -319,6 +322,11 @@ lrt_status lrtddft_get_gset(const lrt_ctx* ctx, int iq, int32_t* miller, double*
 /* chi0 of q index iq: [nw_int][nG][nG] complex, at the internal frequencies
  * (lrtddft_get_frequencies).  Requires chi0_assemble on iq. */
 lrt_status lrtddft_get_chi0(const lrt_ctx* ctx, int iq, double* chi0);
+/* Pair densities rho_p(G) of q index iq as the contraction receives them: [N_p][nG] complex,
+ * p = (k nb + n) nb + n', computed by the context's pair-density kernel (FP64 for the FP64
+ * precision; FP32 on the tensor cores, or the FP32 SIMT kernel under LRT_TUNE_PAIR_SIMT, for
+ * the split precisions).  Test hook; depends on the orbitals' phases (not gauge invariant). */
+lrt_status lrtddft_get_pair_densities(lrt_ctx* ctx, int iq, double* rho);
 /* chi_{G,0} of q index iq: [nw_int][nG] complex.  Requires dyson_solve on iq. */
 lrt_status lrtddft_get_chi_col0(const lrt_ctx* ctx, int iq, double* chi);
 /* Internal frequencies [nw_int] and the index of the w -> 0 column. */

@@ -105,6 +105,7 @@ SIGNATURES = {
     "lrtddft_get_ground_state": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
     "lrtddft_get_gset": (C.c_int, [_P, C.c_int, _I32, _D]),
     "lrtddft_get_chi0": (C.c_int, [_P, C.c_int, _D]),
+    "lrtddft_get_pair_densities": (C.c_int, [_P, C.c_int, _D]),
     "lrtddft_get_chi_col0": (C.c_int, [_P, C.c_int, _D]),
     "lrtddft_get_frequencies": (C.c_int, [_P, _D, C.POINTER(C.c_int)]),
 }
@@ -225,8 +226,9 @@ class Context:
         _check("lrtddft_itcf_laplace_device", self.lib.lrtddft_itcf_laplace_device(
             self.h, ntau, _P(tau_ptr), ITCF[mode], _P(F_ptr), _P(metrics_ptr), _P(stream)))
 
-    def set_tuning(self, auto: bool = False, single_q: bool = False, variant: int = -1, unit_stages: int = 0):
-        flags = (1 if auto else 0) | (2 if single_q else 0)
+    def set_tuning(self, auto: bool = False, single_q: bool = False, variant: int = -1, unit_stages: int = 0,
+                   pair_simt: bool = False):
+        flags = (1 if auto else 0) | (2 if single_q else 0) | (4 if pair_simt else 0)
         _check("lrtddft_set_tuning", self.lib.lrtddft_set_tuning(self.h, flags, variant, unit_stages))
 
     def get_tuning(self):
@@ -342,6 +344,14 @@ class Context:
         nG = int(self.wl.nG[iq])
         out = np.zeros((self.nwi, nG, nG), dtype=np.complex128)
         _check("lrtddft_get_chi0", self.lib.lrtddft_get_chi0(self.h, iq, out.ctypes.data_as(_D)))
+        return out
+
+    def get_pair_densities(self, iq: int) -> np.ndarray:
+        """rho[p][G] of q index iq from the context's pair-density kernel (test hook)."""
+        nG = int(self.wl.nG[iq])
+        out = np.zeros((self.nk * self.nb * self.nb, nG), dtype=np.complex128)
+        _check("lrtddft_get_pair_densities",
+               self.lib.lrtddft_get_pair_densities(self.h, iq, out.ctypes.data_as(_D)))
         return out
 
     def get_chi_col0(self, iq: int) -> np.ndarray:

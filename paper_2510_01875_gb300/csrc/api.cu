@@ -62,6 +62,7 @@ void free_ctx(lrt_ctx* c) {
   cudaFree(c->dw.chi00);
   cudaFree(c->dw.status);
   cudaFree(c->dw.scratch);
+  cudaFree(c->dw.pd_work);
   delete c;
 }
 
@@ -722,12 +723,13 @@ extern "C" lrt_status lrtddft_dsf_vjp(lrt_ctx* c, const double* dL_dS, double gr
 
 extern "C" lrt_status lrtddft_set_tuning(lrt_ctx* c, int flags, int variant, int unit_stages) {
   if (!c) return bad("NULL context");
-  if (flags & ~(LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q)) return bad("unknown tuning flags");
+  if (flags & ~(LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q | LRT_TUNE_PAIR_SIMT)) return bad("unknown tuning flags");
   if (variant < -1 || variant > 1) return bad("variant must be -1, 0 or 1");
   if (unit_stages != 0 && (unit_stages < 64 || unit_stages % 64 != 0))
     return bad("unit_stages must be 0 or a positive multiple of 64");
   c->autotune = (flags & LRT_TUNE_AUTO) != 0;
   c->multi_q = (flags & LRT_TUNE_SINGLE_Q) == 0;
+  c->pair_simt = (flags & LRT_TUNE_PAIR_SIMT) != 0;
   c->tune_variant = variant;
   c->tune_unit_stages = unit_stages;
   c->graph_valid = false;
@@ -815,5 +817,39 @@ extern "C" lrt_status lrtddft_graph_launch(lrt_ctx* c, void* stream) {
     Q.have_chi0 = Q.have_chi = true;
     Q.have_dchi = false;
   }
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_pair_densities(lrt_ctx* c, int iq, double* rho) {
+  if (!c || !rho) return bad("NULL argument");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  LRT_TRY(need_device(c));
+  LRT_CUDA(cudaDeviceSynchronize());
+  LRT_TRY(ensure_rho(c));
+  const QData& Q = c->qd[iq];
+  const bool fp32 = c->precision != LRT_PREC_FP64;
+  LRT_TRY(launch_pair_density(c, Q, c->dw.rho, fp32, 0));
+  LRT_CUDA(cudaDeviceSynchronize());
+  LRT_TRY(check_status_word(c));
+  const int nG = Q.nG;
+  if (!fp32) {
+    std::vector<double2> h((size_t)nG * c->rho_ld);
+    LRT_CUDA(cudaMemcpy(h.data(), c->dw.rho, h.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    for (int64_t p = 0; p < c->np; ++p)
+      for (int g = 0; g < nG; ++g) {
+        rho[2 * (p * nG + g)] = h[(size_t)g * c->rho_ld + p].x;
+        rho[2 * (p * nG + g) + 1] = h[(size_t)g * c->rho_ld + p].y;
+      }
+    return LRT_OK;
+  }
+  std::vector<float2> h((size_t)c->rho_gpad * c->rho_ld);
+  LRT_CUDA(cudaMemcpy(h.data(), c->dw.rho, h.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+  const double inv = 1.0 / split_rho_scale(c->precision);
+  for (int64_t p = 0; p < c->np; ++p)
+    for (int g = 0; g < nG; ++g) {
+      const float2 v = h[(((size_t)(p >> 5) * c->rho_gpad + g) << 5) + (size_t)(p & 31)];
+      rho[2 * (p * nG + g)] = v.x * inv;
+      rho[2 * (p * nG + g) + 1] = v.y * inv;
+    }
   return LRT_OK;
 }

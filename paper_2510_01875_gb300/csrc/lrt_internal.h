@@ -79,6 +79,8 @@ struct DeviceWork {
   int* status = nullptr;          // device status word (0 ok, bit 1 singular, bit 2 timeout)
   double* scratch = nullptr;      // tensor path: FP64 sums of the contraction
   size_t scratch_bytes = 0;
+  void* pd_work = nullptr;        // tensor-core pair densities: prepared operands of one q
+  size_t pd_bytes = 0;
 };
 
 }  // namespace lrt
@@ -130,6 +132,7 @@ struct lrt_ctx {
   void* tc = nullptr;
   bool autotune = false;
   bool multi_q = true;
+  bool pair_simt = false;         // split-path pair densities on the FP32 SIMT kernel
   int tune_variant = -1;          // forced kernel variant, -1: tuned or default
   int tune_unit_stages = 0;       // forced stages per unit, 0: tuned or default
   int last_tc_variant = -1, last_tc_unit_stages = 0;
@@ -191,6 +194,8 @@ inline float split_rho_scale(int precision) { return precision == LRT_PREC_FP16X
 lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool fp32,
                                cudaStream_t s);
 lrt_status launch_pair_weights(const lrt_ctx* c, const QData& q, cudaStream_t s);
+// pairdens_tc.cu: split-path (blocked FP32) pair densities on the tensor cores
+lrt_status launch_pair_density_tc(const lrt_ctx* c, const QData& q, void* rho, cudaStream_t s);
 
 // chi0_fp64.cu
 lrt_status launch_chi0_fp64(const lrt_ctx* c, QData& q, cudaStream_t s);

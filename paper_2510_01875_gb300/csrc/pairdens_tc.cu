@@ -1,0 +1,410 @@
+// Pair densities on the 5th-generation tensor cores (tcgen05, single CTA per SM) for the
+// split-precision path:
+//   rho_p(G) = sum_g c*_nk(g) c_n'k+q(idx_G(g)),   p = (k, n, n'),
+// with idx_G(g) the position of G1_g + G in the k+q basis (the gather table).  For each
+// (k, G) this is a complex GEMM over the plane waves, run as one real GEMM
+//   C'[n][n']       = sum_g Re c_nk(g) Re c'_n'(j) + Im c_nk(g) Im c'_n'(j)   = Re rho
+//   C'[n][128 + n'] = sum_g Re c_nk(g) Im c'_n'(j) - Im c_nk(g) Re c'_n'(j)   = Im rho
+// i.e. A'[n][K] = (Re c_nk | Im c_nk) over K = (g | N_pwp + g) and, for the Re tile, B' rows
+// Re c'(j) for K = g and Im c'(j) for K = N_pwp + g; for the Im tile Im c'(j) and -Re c'(j)
+// (j = idx_G(g)).  Each (k, G) is two tiles, M = 128 (bands), N = 128, K = 2 N_pwp.
+//
+// Precision.  The tensor core's FP32 accumulation drops bits below the accumulator's last place
+// at every update, always toward zero, so an ordinary FP16 hi/lo split loses about one unit in
+// the last place per 16 K (a bias, not noise).  Here every coefficient x (|x| <= 1: the orbitals
+// have unit norm) is split on a fixed grid instead: hi = rint(2^11 x), an integer of at most 11
+// bits (exact in FP16), and lo = 2^11 x - hi in [-1/2, 1/2] (rounded to FP16).  Every hi hi
+// product is then an integer, and by Cauchy-Schwarz every partial sum of them is at most
+// |hi_n| |hi_n'| ~ 2^22 in magnitude, so the FP32 accumulator holds each sum exactly.  The
+// three small products hi lo + lo hi + lo lo (together ~1e-2 of the total) go into a second
+// accumulator, whose truncation is ~1e-2 times smaller; the two are added once at the end.
+//
+// Operands: A' depends on k only; a preparation kernel writes it once per q in the exact
+// shared-memory tile layout (MN-major, 128-byte swizzle, hi and lo), so each 32-K stage is one
+// 16 KB bulk copy.  The k+q orbitals are written once per q as split rows (Re | Im) of 256
+// values; per stage, gatherer warps load the half of the 32 rows idx_G(g) that the tile needs
+// (negated where it needs -Re) and store it into the swizzled B tile.  Two accumulator pairs
+// (512 TMEM columns) alternate between tiles, so four epilogue warps write the previous
+// tile's Re or Im parts of rho (scaled, into the blocked layout rho[p/32][G][p%32]) while the
+// next one runs.  Every wait is bounded; on expiry bit 2 of the status word is set and the kernel
+// drains and returns.
+#include <algorithm>
+#include <cmath>
+
+#include "lrt_internal.h"
+#include "tc_ptx.cuh"
+
+namespace lrt {
+namespace {
+
+using namespace tcx;
+
+constexpr int PM = 128;                      // bands per tile (M)
+constexpr int PN = 128;                      // bands (N) of one tile (its Re or Im part)
+constexpr int PROW = 256;                    // values per prepared k+q row: (Re | Im) x bands
+constexpr int PK = 32;                       // K per stage
+constexpr int PNS = 6;                       // stages in the ring
+constexpr int PA_BYTES = PM * PK * 2;        // 8 KB, one 16-bit A tile
+constexpr int PB_BYTES = PN * PK * 2;        // 8 KB
+constexpr int PSTAGE = 2 * PA_BYTES + 2 * PB_BYTES;   // 32 KB
+constexpr int PA_SBO = (PM / 64) * 1024;
+constexpr int PB_SBO = (PN / 64) * 1024;
+constexpr int PW_MMA = 0, PW_LOAD = 1, PW_G0 = 2, PW_E0 = 10;   // warps; gatherers 2..9, epilogue 10..13
+constexpr int PTHREADS = 14 * 32;
+constexpr double kGrid = 2048.0;             // 2^11: hi = rint(kGrid x), lo = kGrid x - hi
+
+// Fixed-grid split of 8 coefficients (already multiplied by kGrid) into FP16 hi and lo.
+__device__ __forceinline__ void grid_split(const double* x, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double a = rint(x[2 * i]), b = rint(x[2 * i + 1]);
+    __half2 hh = __floats2half2_rn((float)a, (float)b);   // integers of at most 2^11: exact
+    __half2 ll = __floats2half2_rn((float)(x[2 * i] - a), (float)(x[2 * i + 1] - b));
+    h[i] = *reinterpret_cast<uint32_t*>(&hh);
+    l[i] = *reinterpret_cast<uint32_t*>(&ll);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+struct PParams {
+  const uint4* A;             // [nk][nst][hi | lo tile] prepared A' (16 KB per stage)
+  const uint4* B;             // [nk][npw + 1][hi | lo][PROW fp16] k+q rows, last row zero
+  const int32_t* gather;      // [nk][nG][npw]
+  float2* rho;                // blocked [ld/32][gpad][32]
+  int* status;
+  int nk, nb, nG, npw, npwp, nst, gpad;
+  float scale;                // applied to C' when storing rho
+};
+
+// A'[k][stage][hi|lo]: thread per (k, stage, K in stage, chunk of 8 bands).
+__global__ void pd_prep_a(const double2* __restrict__ ck, int nk, int nb, int npw, int npwp, int nst,
+                          uint4* __restrict__ A) {
+  const long long total = (long long)nk * nst * PK * (PM / 8);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t % (PM / 8));
+    const int kk = (int)((t / (PM / 8)) % PK);
+    const int s = (int)((t / (PM / 8 * PK)) % nst);
+    const int k = (int)(t / ((long long)PM / 8 * PK * nst));
+    const int K = s * PK + kk;
+    const bool im = K >= npwp;
+    const int g = im ? K - npwp : K;
+    double v[8];
+    for (int i = 0; i < 8; ++i) {
+      const int n = 8 * c + i;
+      double x = 0.0;
+      if (n < nb && g < npw) {
+        const double2 z = ck[((size_t)k * nb + n) * npw + g];
+        x = (im ? z.y : z.x) * kGrid;
+      }
+      v[i] = x;
+    }
+    uint4 hi, lo;
+    grid_split(v, hi, lo);
+    uint8_t* tile = reinterpret_cast<uint8_t*>(A) + ((size_t)k * nst + s) * 2 * PA_BYTES;
+    *reinterpret_cast<uint4*>(tile + mn_chunk(kk, c, PA_SBO)) = hi;
+    *reinterpret_cast<uint4*>(tile + PA_BYTES + mn_chunk(kk, c, PA_SBO)) = lo;
+  }
+}
+
+// k+q rows: thread per (k, row j, chunk of 8 columns); row npw is zero.
+__global__ void pd_prep_b(const double2* __restrict__ ckq, int nk, int nb, int npw, uint4* __restrict__ B) {
+  const long long total = (long long)nk * (npw + 1) * (PROW / 8);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t % (PROW / 8));
+    const int j = (int)((t / (PROW / 8)) % (npw + 1));
+    const int k = (int)(t / ((long long)(PROW / 8) * (npw + 1)));
+    double v[8];
+    for (int i = 0; i < 8; ++i) {
+      const int col = 8 * c + i;
+      const int n = col & (PM - 1);
+      double x = 0.0;
+      if (n < nb && j < npw) {
+        const double2 z = ckq[((size_t)k * nb + n) * npw + j];
+        x = (col < PM ? z.x : z.y) * kGrid;
+      }
+      v[i] = x;
+    }
+    uint4 hi, lo;
+    grid_split(v, hi, lo);
+    uint4* row = B + ((size_t)k * (npw + 1) + j) * (2 * PROW / 8);
+    row[c] = hi;
+    row[PROW / 8 + c] = lo;
+  }
+}
+
+__device__ __forceinline__ uint4 neg16(uint4 v) {   // negate 8 packed fp16 values
+  return make_uint4(v.x ^ 0x80008000u, v.y ^ 0x80008000u, v.z ^ 0x80008000u, v.w ^ 0x80008000u);
+}
+
+__global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[PNS], empty[PNS], acc_full[2], acc_empty[2], final_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PNS; ++s) {
+      mbar_init(&full[s], 1 + 4);   // the loader's expect_tx arrive + 4 gatherer warps
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(&final_bar, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == PW_MMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(4 * PN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+  const int ntiles = 2 * P.nk * P.nG;   // (k, G, Re | Im)
+  const int nst = P.nst;
+  const uint32_t idesc = (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(PN >> 3) << 17) |
+                         ((uint32_t)(PM >> 4) << 24);
+  // tile t: (k, G) = t / 2 as k nG + G, part t % 2 (0: Re rho, 1: Im rho)
+
+  if (warp == PW_LOAD) {
+    // ---------------- A' stages: one 16 KB bulk copy each ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int k = (t >> 1) / P.nG;
+        for (int s = 0; s < nst; ++s, ++it) {
+          const int slot = it % PNS;
+          if (!(ok = mbar_wait(&empty[slot], ((it / PNS) & 1) ^ 1, &abort_s, P.status))) break;
+          mbar_expect_tx(&full[slot], 2 * PA_BYTES);
+          bulk_g2s(base + slot * PSTAGE,
+                   reinterpret_cast<const uint8_t*>(P.A) + ((size_t)k * nst + s) * 2 * PA_BYTES,
+                   2 * PA_BYTES, &full[slot]);
+        }
+      }
+      // wait (bounded) for the last copies before the shared memory goes away
+      for (uint32_t j = (it > (uint32_t)PNS ? it - PNS : 0u); j < it; ++j)
+        mbar_drain(&full[j % PNS], (j / PNS) & 1, P.status);
+    }
+  } else if (warp >= PW_G0 && warp < PW_E0) {
+    // ---------------- gatherers: group (warp - 2) / 4 takes every other stage ----------------
+    const int grp = (warp - PW_G0) >> 2, gt = (threadIdx.x - PW_G0 * 32) & 127;
+    const int kk = gt >> 2, c0 = (gt & 3) * 4;   // this thread's K row in the stage and 4 chunks
+    uint32_t it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int k = (t >> 1) / P.nG, G = (t >> 1) % P.nG, part = t & 1;
+      const int32_t* tab = P.gather + ((size_t)k * P.nG + G) * P.npw;
+      const uint4* Bk = P.B + (size_t)k * (P.npw + 1) * (2 * PROW / 8);
+      for (int s = 0; s < nst; ++s, ++it) {
+        if ((int)(it & 1) != grp) continue;
+        const int slot = it % PNS;
+        if (!__all_sync(0xffffffffu, mbar_wait(&empty[slot], ((it / PNS) & 1) ^ 1, &abort_s, P.status))) {
+          ok = false;
+          break;
+        }
+        const int K = s * PK + kk;
+        const bool im = K >= P.npwp;
+        const int g = im ? K - P.npwp : K;
+        int j = g < P.npw ? tab[g] : -1;
+        if (j < 0) j = P.npw;                    // the zero row
+        const uint4* row = Bk + (size_t)j * (2 * PROW / 8);
+        // Re tile: Re c' (first K half), Im c' (second); Im tile: Im c', then -Re c'
+        const int off = (part ^ (im ? 1 : 0)) ? PN / 8 : 0;
+        const bool neg = part && im;
+        uint4 h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          h[i] = row[off + c0 + i];
+          l[i] = row[PROW / 8 + off + c0 + i];
+        }
+        const uint32_t bt = base + slot * PSTAGE + 2 * PA_BYTES;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = c0 + i;
+          st_shared_v4(bt + mn_chunk(kk, c, PB_SBO), neg ? neg16(h[i]) : h[i]);
+          st_shared_v4(bt + PB_BYTES + mn_chunk(kk, c, PB_SBO), neg ? neg16(l[i]) : l[i]);
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[slot]);
+      }
+    }
+  } else if (warp == PW_MMA) {
+    // ---------------- MMA issuer ----------------
+    uint32_t it = 0, tc = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
+      const int buf = tc & 1;
+      if (lane == 0) ok = mbar_wait(&acc_empty[buf], ((tc >> 1) & 1) ^ 1, &abort_s, P.status);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t d = tmem + buf * 2 * PN, dsm = d + PN;   // hi hi | hi lo + lo hi + lo lo
+      for (int s = 0; s < nst; ++s, ++it) {
+        const int slot = it % PNS;
+        if (lane == 0) ok = mbar_wait(&full[slot], (it / PNS) & 1, &abort_s, P.status);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t sa = base + slot * PSTAGE, sb = sa + 2 * PA_BYTES;
+#pragma unroll
+          for (int kq = 0; kq < PK / 16; ++kq) {
+            const uint64_t dAh = sdesc(sa + kq * 2 * PA_SBO, 1024, PA_SBO);
+            const uint64_t dAl = sdesc(sa + PA_BYTES + kq * 2 * PA_SBO, 1024, PA_SBO);
+            const uint64_t dBh = sdesc(sb + kq * 2 * PB_SBO, 1024, PB_SBO);
+            const uint64_t dBl = sdesc(sb + PB_BYTES + kq * 2 * PB_SBO, 1024, PB_SBO);
+            const uint32_t acc = (s > 0 || kq > 0) ? 1u : 0u;
+            mma1(d, dAh, dBh, idesc, acc);
+            mma1(dsm, dAh, dBl, idesc, acc);
+            mma1(dsm, dAl, dBh, idesc, 1u);
+            mma1(dsm, dAl, dBl, idesc, 1u);
+          }
+          mma1_commit(&empty[slot]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) mma1_commit(&acc_full[buf]);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      mma1_commit(&final_bar);
+      mbar_drain(&final_bar, 0, P.status);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: tensor memory -> rho (blocked layout) ----------------
+    const int q = warp & 3;
+    const int n = q * 32 + lane;   // band n of the nk state (row of the tile)
+    uint32_t tc = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+      const int buf = tc & 1;
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(&acc_full[buf], (tc >> 1) & 1, &abort_s, P.status);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const int k = (t >> 1) / P.nG, G = (t >> 1) % P.nG, part = t & 1;
+      const long long p0 = ((long long)k * P.nb + n) * P.nb;
+      float* out = reinterpret_cast<float*>(P.rho) + part;
+#pragma unroll 1
+      for (int c = 0; c < PN / 16; ++c) {
+        uint32_t re[16], im[16];   // the two accumulators' columns 16 c .. 16 c + 15
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + buf * 2 * PN + c * 16;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];"
+            : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]),
+              "=r"(re[6]), "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]),
+              "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
+            : "r"(ta));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];"
+            : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]),
+              "=r"(im[6]), "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]),
+              "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
+            : "r"(ta + PN));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (n < P.nb) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int np_ = c * 16 + j;
+            if (np_ < P.nb) {
+              const long long p = p0 + np_;
+              out[2 * (((size_t)((p >> 5) * P.gpad + G) << 5) + (size_t)(p & 31))] =
+                  (__uint_as_float(re[j]) + __uint_as_float(im[j])) * P.scale;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == PW_MMA)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * PN));
+}
+
+}  // namespace
+
+// Tensor-core pair densities of one q into the blocked FP32 layout.  Returns LRT_EUNSUPPORTED
+// (nothing launched) when the shape does not fit the kernel (more than 128 bands).
+lrt_status launch_pair_density_tc(const lrt_ctx* c, const QData& q, void* rho, cudaStream_t s) {
+  if (c->nb > PM) {
+    set_error("tensor-core pair densities: more than 128 bands");
+    return LRT_EUNSUPPORTED;
+  }
+  const int npw = c->npw;
+  const int npwp = (npw + PK - 1) / PK * PK;
+  const int nst = 2 * npwp / PK;
+  lrt_ctx* cc = const_cast<lrt_ctx*>(c);
+  const size_t a_bytes = (size_t)c->nk * nst * 2 * PA_BYTES;
+  const size_t b_bytes = (size_t)c->nk * (npw + 1) * 2 * PROW * 2;
+  if (cc->dw.pd_bytes < a_bytes + b_bytes) {
+    cudaFree(cc->dw.pd_work);
+    cc->dw.pd_work = nullptr;
+    cc->dw.pd_bytes = 0;
+    LRT_CUDA(cudaMalloc(&cc->dw.pd_work, a_bytes + b_bytes));
+    cc->dw.pd_bytes = a_bytes + b_bytes;
+  }
+  uint4* A = reinterpret_cast<uint4*>(cc->dw.pd_work);
+  uint4* B = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(cc->dw.pd_work) + a_bytes);
+  int dev = 0, nsm = 0;
+  LRT_CUDA(cudaGetDevice(&dev));
+  LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const double2* ck = q.coeff;
+  const double2* ckq = q.coeff + (size_t)c->nk * c->nb * npw;
+  pd_prep_a<<<8 * nsm, 256, 0, s>>>(ck, c->nk, c->nb, npw, npwp, nst, A);
+  pd_prep_b<<<8 * nsm, 256, 0, s>>>(ckq, c->nk, c->nb, npw, B);
+  count_launch(c, 2);
+  LRT_CUDA(cudaGetLastError());
+  PParams P;
+  P.A = A;
+  P.B = B;
+  P.gather = q.gather;
+  P.rho = (float2*)rho;
+  P.status = c->dw.status;
+  P.nk = c->nk;
+  P.nb = c->nb;
+  P.nG = q.nG;
+  P.npw = npw;
+  P.npwp = npwp;
+  P.nst = nst;
+  P.gpad = c->rho_gpad;
+  P.scale = (float)(split_rho_scale(c->precision) / (kGrid * kGrid));
+  const size_t smem = (size_t)PNS * PSTAGE + 1024;
+  // raised once per device (repeated calls and graph captures make no attribute call)
+  static size_t attr_set[64] = {0};
+  if (dev < 0 || dev >= 64 || attr_set[dev] < smem) {
+    LRT_CUDA(cudaFuncSetAttribute(pair_density_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    if (dev >= 0 && dev < 64) attr_set[dev] = smem;
+  }
+  const int grid = std::min(nsm, 2 * c->nk * q.nG);
+  {
+    TimedLaunch tl(c, &c->ev_rho, s);
+    pair_density_tc_kernel<<<grid, PTHREADS, smem, s>>>(P);
+  }
+  count_launch(c);
+  LRT_CUDA(cudaGetLastError());
+  return LRT_OK;
+}
+
+}  // namespace lrt

@@ -1,0 +1,62 @@
+"""GPU: pair densities of the split path on the tensor cores against the FP32 SIMT kernel and
+the FP64 kernel, element by element on the same orbitals (through the C ABI test hook
+lrtddft_get_pair_densities).
+
+The tensor-core form splits every orbital coefficient on a fixed grid (hi = rint(2^11 x),
+exact in FP16, lo = the FP16 rest) so that the FP32 accumulator sums the hi*hi products exactly;
+what is left is the FP16 rounding of lo and the truncation of the small-product accumulator,
+~1e-7 of the largest |rho|, held to 1e-6.  The FP32 SIMT kernel (round-to-nearest FMA) is held
+to 2e-6.  Cases span several tiles with ragged band counts, G counts and plane-wave padding,
+up to the 128-band limit of the tensor-core tile; above it the SIMT kernel runs.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_01875_gb300 import binding, build
+from paper_2510_01875_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "tiny": dict(seed=41, nq=2, nw=16),
+    "ragged": dict(seed=42, nq=1, nw=16, nbands=13, nG=11, kmesh=(3, 2, 2)),
+    "bands_near_tile": dict(seed=43, nq=1, nw=16, nbands=110, ecut=6.0, kmesh=(2, 2, 2), nG=15),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    return binding.load()
+
+
+def rho_of(wl, prec, **tune):
+    c = binding.Context(wl, prec)
+    if tune:
+        c.set_tuning(**tune)
+    out = [c.get_pair_densities(iq) for iq in range(wl.nq)]
+    nb = c.nb
+    c.close()
+    return out, nb
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_tensor_core_pair_densities(name):
+    wl = W.tiny(**CASES[name])
+    ref, nb = rho_of(wl, "fp64")
+    tc, nb2 = rho_of(wl, "fp16x3")
+    simt, _ = rho_of(wl, "fp16x3", pair_simt=True)
+    assert nb == nb2
+    for iq in range(wl.nq):
+        scale = np.abs(ref[iq]).max()
+        assert np.abs(tc[iq] - ref[iq]).max() <= 1e-6 * scale, (name, iq)
+        assert np.abs(simt[iq] - ref[iq]).max() <= 2e-6 * scale, (name, iq)
+
+
+def test_repeat_calls_agree():
+    wl = W.tiny(**CASES["ragged"])
+    c = binding.Context(wl, "fp16x3")
+    a = c.get_pair_densities(0)
+    b = c.get_pair_densities(0)
+    c.close()
+    assert np.array_equal(a, b)
