@@ -750,11 +750,15 @@ static lrt_status upload_tables(const lrt_ctx* c, const std::vector<int>& qs,
     D.n_st2 = P.n_st2;
     D.n_n = P.n_n;
     split_q(c, P, stages, &D.n_split, &D.k_per_split);
-    // pair range by pair range, all tiles of a range together: the clusters running at the
-    // same time then read the same pair-density blocks (shared through L2 by the column tiles)
-    const int ntile = D.n_st2 * D.n_n;
-    for (int ks = 0; ks < D.n_split; ++ks)
-      for (int t = 0; t < ntile; ++t) units.push_back(make_int2((int)i, t * D.n_split + ks));
+    // super-tile pair, then pair range, then column tile: the clusters running at the same
+    // time share one super-tile pair, so the column tiles of a pair range read the same
+    // pair-density blocks (through L2) and only n_n tiles of FP64 sums (1 MB each) are being
+    // reduced into at once; ordering by pair range alone keeps all n_st2 n_n of them live,
+    // which with the staging areas overflows L2
+    for (int st2 = 0; st2 < D.n_st2; ++st2)
+      for (int ks = 0; ks < D.n_split; ++ks)
+        for (int nt = 0; nt < D.n_n; ++nt)
+          units.push_back(make_int2((int)i, (st2 * D.n_n + nt) * D.n_split + ks));
   }
   if (limit_units > 0 && (int)units.size() > limit_units) units.resize(limit_units);
   *nunits = (int)units.size();
