@@ -4,7 +4,8 @@
 // With M = 1 - chi0 K (K diagonal), chi_{:,0} = M^{-1} chi0_{:,0} and a change d of chi0 and K,
 //   d chi_00 = u^T d chi0 v + u^T chi0 dK chi_{:,0},   M^T u = e_0,   v = K chi_{:,0} + e_0.
 // The Dyson LU is recomputed from the stored chi0 (one block per frequency, Mᵀ u = e_0 by
-// Gaussian elimination with partial pivoting), which also gives the f_xc-model terms
+// Gaussian elimination with partial pivoting; Mᵀ in shared memory up to N_G = 118, above that
+// in a per-block slice of a global workspace), which also gives the f_xc-model terms
 // u^T chi0 dK chi_{:,0} for A, B, C.  The T and eta terms need the weight tangents inside the
 // pair sum:
 //   u^T d chi0 v = (2/(N_k Omega)) sum_p a_p(w) b_p(w) dw_p(w),
@@ -14,6 +15,7 @@
 //   df/dT = f (1 - f) ((eps - mu)/T^2 + mu'/T),  mu' from the conserved electron count.
 // The projections are computed for every (p, w) on the fly from the pair densities (2 N_G
 // complex MACs each) and reduced over p; nothing of size N_p x N_w is stored.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -30,25 +32,30 @@ __device__ inline double2 cdiv(double2 a, double2 b) {
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// grid.x = frequency.  Shared memory: N x (N+1) matrix M^T, then rhs[N], fac[N].
-// Outputs per frequency: u[N], v[N] and the A, B, C tangents of chi_00 (dK holds the three
-// tangents of the kernel diagonal, [3][N]).
+// Block loop over frequencies w = blockIdx.x, blockIdx.x + gridDim.x, ...  GM: M^T in ws
+// (N x (N+1) per block) and shared memory rhs[N], fac[N]; otherwise shared memory N x (N+1)
+// matrix M^T, then rhs[N], fac[N].  Outputs per frequency: u[N], v[N] and the A, B, C tangents
+// of chi_00 (dK holds the three tangents of the kernel diagonal, [3][N]).
+template <bool GM>
 __global__ void __launch_bounds__(256) dyson_adjoint_kernel(
     const double2* __restrict__ chi0, const double* __restrict__ K, const double* __restrict__ dK,
-    const double2* __restrict__ chi, int N, double2* __restrict__ u_out,
-    double2* __restrict__ v_out, double2* __restrict__ dk_out, int* __restrict__ status) {
+    const double2* __restrict__ chi, int N, int nw, double2* __restrict__ u_out,
+    double2* __restrict__ v_out, double2* __restrict__ dk_out, int* __restrict__ status,
+    double2* ws) {
   extern __shared__ double2 sm[];
   const int ld = N + 1;
-  double2* A = sm;
-  double2* b = sm + (size_t)N * ld;
+  double2* A = GM ? ws + (size_t)blockIdx.x * N * ld : sm;
+  double2* b = GM ? sm : sm + (size_t)N * ld;
   double2* fac = b + N;
   __shared__ int piv_s;
   __shared__ int bad;
-  const int w = blockIdx.x;
-  const double2* X = chi0 + (size_t)w * N * N;
-  const double2* x = chi + (size_t)w * N;
+  __shared__ double2 red_s[8];   // per-warp partials (256 threads)
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) bad = 0;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+  const double2* X = chi0 + (size_t)w * N * N;
+  const double2* x = chi + (size_t)w * N;
+  __syncthreads();   // the previous frequency is done with A, b and fac
   // A = M^T: A[r][j] = M[j][r] = delta_jr - chi0[j][r] K[r]
   for (int e = tid; e < N * N; e += nt) {
     int j = e / N, r = e % N;
@@ -151,7 +158,7 @@ __global__ void __launch_bounds__(256) dyson_adjoint_kernel(
       acc[j].y += rx.y * dK[j * N + gp];
     }
   }
-  // block reduction of the three sums (fac is free again)
+  // block reduction of the three sums (one partial per warp)
   for (int j = 0; j < 3; ++j) {
     double2 v = acc[j];
     for (int off = 16; off > 0; off >>= 1) {
@@ -159,16 +166,17 @@ __global__ void __launch_bounds__(256) dyson_adjoint_kernel(
       v.y += __shfl_down_sync(0xffffffffu, v.y, off);
     }
     __syncthreads();
-    if ((tid & 31) == 0) fac[tid >> 5] = v;
+    if ((tid & 31) == 0) red_s[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
       double2 s = make_double2(0, 0);
       for (int i = 0; i < (nt >> 5); ++i) {
-        s.x += fac[i].x;
-        s.y += fac[i].y;
+        s.x += red_s[i].x;
+        s.y += red_s[i].y;
       }
       dk_out[(size_t)w * 3 + j] = s;
     }
+  }
   }
   if (tid == 0 && bad) atomicOr(status, 1);
 }
@@ -212,6 +220,7 @@ struct CT<double> {
 
 constexpr int PCH = 32;    // pairs per chunk (one per lane)
 constexpr int OG = 8;      // frequency groups (warps) per block
+constexpr size_t kProjSmem = 200 * 1024;   // shared-memory budget of the projection tiles
 
 // Projections and the pair sum for the T and eta tangents.
 // grid: x = pair split, y = frequency tile of WT.  Block: 256 threads = 8 warps; lane = pair of
@@ -345,7 +354,7 @@ lrt_status launch_project(const lrt_ctx* c, const QData& q, const double2* du, c
   using T2 = typename CT<R>::T2;
   const int nG = q.nG;
   const size_t smem = (size_t)nG * (PCH + 2 * WT) * sizeof(T2);
-  if (smem > 200 * 1024) {
+  if (smem > kProjSmem) {
     set_error("adjoint projections: N_G too large");
     return LRT_EUNSUPPORTED;
   }
@@ -403,7 +412,7 @@ lrt_status launch_adjoint_q(const lrt_ctx* c, QData& q, int iq, std::vector<doub
     }
   }
   double *d_dK = nullptr, *d_dl = nullptr, *d_df = nullptr, *d_ddf = nullptr, *d_g = nullptr;
-  double2 *d_u = nullptr, *d_v = nullptr, *d_k3 = nullptr;
+  double2 *d_u = nullptr, *d_v = nullptr, *d_k3 = nullptr, *d_ws = nullptr;
   auto freeall = [&]() {
     cudaFree(d_dK);
     cudaFree(d_dl);
@@ -413,6 +422,7 @@ lrt_status launch_adjoint_q(const lrt_ctx* c, QData& q, int iq, std::vector<doub
     cudaFree(d_u);
     cudaFree(d_v);
     cudaFree(d_k3);
+    cudaFree(d_ws);
   };
   auto fail = [&](cudaError_t e) {
     freeall();
@@ -433,26 +443,43 @@ lrt_status launch_adjoint_q(const lrt_ctx* c, QData& q, int iq, std::vector<doub
           cudaSuccess ||
       (e = cudaMemsetAsync(d_g, 0, (size_t)nwi * 4 * sizeof(double), s)) != cudaSuccess)
     return fail(e);
-  const size_t smem = ((size_t)N * (N + 1) + 2 * N) * sizeof(double2);
+  const size_t mat = (size_t)N * (N + 1) * sizeof(double2);
+  const size_t smem = mat + 2 * (size_t)N * sizeof(double2);
   if (smem > 227 * 1024) {
-    freeall();
-    set_error("adjoint Dyson: nG too large for the one-block solver");
-    return LRT_EUNSUPPORTED;
+    // M^T in global memory: one slice per block, two blocks per SM
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return fail(e);
+    const int grid = std::max(1, std::min(nwi, 2 * nsm));
+    if ((e = cudaMalloc(&d_ws, (size_t)grid * mat)) != cudaSuccess) return fail(e);
+    dyson_adjoint_kernel<true><<<grid, 256, 2 * (size_t)N * sizeof(double2), s>>>(
+        q.chi0, q.Kdev, d_dK, q.chi, N, nwi, d_u, d_v, d_k3, c->dw.status, d_ws);
+  } else {
+    if ((e = cudaFuncSetAttribute(dyson_adjoint_kernel<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return fail(e);
+    dyson_adjoint_kernel<false><<<nwi, 256, smem, s>>>(q.chi0, q.Kdev, d_dK, q.chi, N, nwi, d_u,
+                                                       d_v, d_k3, c->dw.status, nullptr);
   }
-  if ((e = cudaFuncSetAttribute(dyson_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem)) != cudaSuccess)
-    return fail(e);
-  dyson_adjoint_kernel<<<nwi, 256, smem, s>>>(q.chi0, q.Kdev, d_dK, q.chi, N, d_u, d_v, d_k3,
-                                              c->dw.status);
   count_launch(c);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
   adjoint_pair_weights<<<1216, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, q.mu, c->T, mup,
                                             fixed ? 1 : 0, d_dl, d_df, d_ddf);
   count_launch(c);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
-  lrt_status st = (c->precision == LRT_PREC_FP64)
-                      ? launch_project<double, 16>(c, q, d_u, d_v, d_dl, d_df, d_ddf, d_g, s)
-                      : launch_project<float, 32>(c, q, d_u, d_v, d_dl, d_df, d_ddf, d_g, s);
+  // frequency tiles of 16 (FP64) or 32 (split) while the tile fits the shared memory, half
+  // that above (N_G up to 266 for FP64, 400 for the split path)
+  const bool wide64 = (size_t)N * (PCH + 2 * 16) * sizeof(double2) <= kProjSmem;
+  const bool wide32 = (size_t)N * (PCH + 2 * 32) * sizeof(float2) <= kProjSmem;
+  lrt_status st;
+  if (c->precision == LRT_PREC_FP64)
+    st = wide64 ? launch_project<double, 16>(c, q, d_u, d_v, d_dl, d_df, d_ddf, d_g, s)
+                : launch_project<double, 8>(c, q, d_u, d_v, d_dl, d_df, d_ddf, d_g, s);
+  else
+    st = wide32 ? launch_project<float, 32>(c, q, d_u, d_v, d_dl, d_df, d_ddf, d_g, s)
+                : launch_project<float, 16>(c, q, d_u, d_v, d_dl, d_df, d_ddf, d_g, s);
   if (st != LRT_OK) {
     freeall();
     return st;

@@ -63,6 +63,7 @@ void free_ctx(lrt_ctx* c) {
   cudaFree(c->dw.status);
   cudaFree(c->dw.scratch);
   cudaFree(c->dw.pd_work);
+  cudaFree(c->dw.dyson_ws);
   delete c;
 }
 

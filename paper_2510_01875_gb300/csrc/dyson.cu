@@ -1,8 +1,12 @@
 // Dyson equation chi = (1 - chi0 K)^{-1} chi0 with K diagonal, FP64: for each frequency one
-// block loads M = 1 - chi0 K (M_GG' = delta_GG' - chi0_GG' K_G') into shared memory and
-// solves M x = chi0_{:,0} by Gaussian elimination with partial pivoting (pivot = largest
-// modulus, first on ties) and back substitution; x = chi_{G,0}.  A zero pivot sets bit 1 of
-// the device status word and leaves NaN in x.
+// block loads M = 1 - chi0 K (M_GG' = delta_GG' - chi0_GG' K_G') and solves M x = chi0_{:,0} by
+// Gaussian elimination with partial pivoting (pivot = largest modulus, first on ties) and back
+// substitution; x = chi_{G,0}.  M sits in shared memory while it fits (N_G <= 118); above that
+// each block keeps it in its own slice of a global workspace (L2-resident for the sizes of
+// interest) and loops over frequencies.  Both forms run the same operations in the same order.
+// A zero pivot sets bit 1 of the device status word and leaves NaN in x.
+#include <algorithm>
+
 #include "lrt_internal.h"
 
 namespace lrt {
@@ -16,22 +20,26 @@ __device__ inline double2 cdiv(double2 a, double2 b) {
   return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// grid.x = frequency; dynamic shared memory: N x (N+1) matrix, then rhs[N], fac[N].
+// Block loop over frequencies w = blockIdx.x, blockIdx.x + gridDim.x, ...  GM: M in ws
+// (N x (N+1) per block), shared memory rhs[N], fac[N]; otherwise shared memory N x (N+1)
+// matrix, then rhs[N], fac[N].
+template <bool GM>
 __global__ void __launch_bounds__(256) dyson_kernel(const double2* __restrict__ chi0,
-                                                    const double* __restrict__ K, int N,
+                                                    const double* __restrict__ K, int N, int nw,
                                                     double2* __restrict__ chi,
-                                                    int* __restrict__ status) {
+                                                    int* __restrict__ status, double2* ws) {
   extern __shared__ double2 sm[];
   const int ld = N + 1;
-  double2* M = sm;
-  double2* b = sm + (size_t)N * ld;
+  double2* M = GM ? ws + (size_t)blockIdx.x * N * ld : sm;
+  double2* b = GM ? sm : sm + (size_t)N * ld;
   double2* fac = b + N;
   __shared__ int piv_s;
   __shared__ int bad;
-  const int w = blockIdx.x;
-  const double2* X = chi0 + (size_t)w * N * N;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) bad = 0;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+  const double2* X = chi0 + (size_t)w * N * N;
+  __syncthreads();   // the previous frequency's back substitution is done with M and b
   for (int e = tid; e < N * N; e += nt) {
     int r = e / N, j = e % N;
     double2 v = X[e];
@@ -116,6 +124,7 @@ __global__ void __launch_bounds__(256) dyson_kernel(const double2* __restrict__ 
     __syncthreads();
   }
   for (int r = tid; r < N; r += nt) chi[(size_t)w * N + r] = b[r];
+  }
   if (tid == 0 && bad) atomicOr(status, 1);
 }
 
@@ -123,23 +132,41 @@ __global__ void __launch_bounds__(256) dyson_kernel(const double2* __restrict__ 
 
 lrt_status launch_dyson(const lrt_ctx* c, QData& q, int iq, cudaStream_t s) {
   (void)iq;
-  int N = q.nG;
-  size_t smem = ((size_t)N * (N + 1) + 2 * N) * sizeof(double2);
+  const int N = q.nG, nw = c->nwi;
+  const size_t mat = (size_t)N * (N + 1) * sizeof(double2);
+  const size_t smem = mat + 2 * (size_t)N * sizeof(double2);
+  int dev = 0;
+  LRT_CUDA(cudaGetDevice(&dev));
   if (smem > 227 * 1024) {
-    lrt::set_error("Dyson: nG too large for the one-block solver");
-    return LRT_EUNSUPPORTED;
+    // global-memory form: one matrix slice per block, two blocks per SM; the workspace is
+    // allocated on the first call that needs it (before any graph capture: the capture
+    // follows an ordinary pass)
+    int nsm = 0;
+    LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::max(1, std::min(nw, 2 * nsm));
+    lrt_ctx* cc = const_cast<lrt_ctx*>(c);
+    if (cc->dw.dyson_bytes < (size_t)grid * mat) {
+      cudaFree(cc->dw.dyson_ws);
+      cc->dw.dyson_ws = nullptr;
+      cc->dw.dyson_bytes = 0;
+      LRT_CUDA(cudaMalloc(&cc->dw.dyson_ws, (size_t)grid * mat));
+      cc->dw.dyson_bytes = (size_t)grid * mat;
+    }
+    dyson_kernel<true><<<grid, 256, 2 * (size_t)N * sizeof(double2), s>>>(
+        q.chi0, q.Kdev, N, nw, q.chi, c->dw.status, (double2*)cc->dw.dyson_ws);
+    count_launch(c);
+    LRT_CUDA(cudaGetLastError());
+    return LRT_OK;
   }
   // raised only when a call needs more than any earlier one on this device, so repeated
   // calls (and a graph capture after a first pass) make no attribute call
   static size_t attr_set[64] = {0};
-  int dev = 0;
-  LRT_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64 || attr_set[dev] < smem) {
-    LRT_CUDA(cudaFuncSetAttribute(dyson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LRT_CUDA(cudaFuncSetAttribute(dyson_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     if (dev >= 0 && dev < 64) attr_set[dev] = smem;
   }
-  dyson_kernel<<<c->nwi, 256, smem, s>>>(q.chi0, q.Kdev, N, q.chi, c->dw.status);
+  dyson_kernel<false><<<nw, 256, smem, s>>>(q.chi0, q.Kdev, N, nw, q.chi, c->dw.status, nullptr);
   count_launch(c);
   LRT_CUDA(cudaGetLastError());
   return LRT_OK;

@@ -81,6 +81,8 @@ struct DeviceWork {
   size_t scratch_bytes = 0;
   void* pd_work = nullptr;        // tensor-core pair densities: prepared operands of one q
   size_t pd_bytes = 0;
+  void* dyson_ws = nullptr;       // Dyson matrices of N_G too large for shared memory
+  size_t dyson_bytes = 0;
 };
 
 }  // namespace lrt

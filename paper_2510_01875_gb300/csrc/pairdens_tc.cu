@@ -13,17 +13,22 @@
 // at every update, always toward zero, so an ordinary FP16 hi/lo split loses about one unit in
 // the last place per 16 K (a bias, not noise).  Here every coefficient x (|x| <= 1: the orbitals
 // have unit norm) is split on a fixed grid instead: hi = rint(2^11 x), an integer of at most 11
-// bits (exact in FP16), and lo = 2^11 x - hi in [-1/2, 1/2] (rounded to FP16).  Every hi hi
-// product is then an integer, and by Cauchy-Schwarz every partial sum of them is at most
-// |hi_n| |hi_n'| ~ 2^22 in magnitude, so the FP32 accumulator holds each sum exactly.  The
-// three small products hi lo + lo hi + lo lo (together ~1e-2 of the total) go into a second
-// accumulator, whose truncation is ~1e-2 times smaller; the two are added once at the end.
+// bits (exact in FP16), and the rest r = 2^11 x - hi in [-1/2, 1/2] is carried as a classic FP16
+// pair r1 = fp16(2^12 r), r2 = fp16(2^12 r - r1) (about 22 bits of r), plus r11 = fp16(r).
+// Every hi hi product is an integer, and by Cauchy-Schwarz every partial sum of them is at most
+// |hi_n| |hi_n'| ~ 2^22 in magnitude, so the FP32 accumulator holds each sum exactly.  The small
+// products hi (r1 + r2)' + (r1 + r2) hi' + r11 r1' (all at scale 2^34; ~1e-3 of the total) go
+// into a second accumulator, whose truncation is ~1e-3 times smaller; the two are added once at
+// the end.  A single rounded remainder (lo = fp16(r)) would leave every coefficient with an
+// absolute error up to 2^-24, large against small coefficients: the relative error of the small
+// interband densities would then be ~10x that of FP32 arithmetic.
 //
 // Operands: A' depends on k only; a preparation kernel writes it once per q in the exact
-// shared-memory tile layout (MN-major, 128-byte swizzle, hi and lo), so each 32-K stage is one
-// 16 KB bulk copy.  The k+q orbitals are written once per q as split rows (Re | Im) of 256
-// values; per stage, gatherer warps load the half of the 32 rows idx_G(g) that the tile needs
-// (negated where it needs -Re) and store it into the swizzled B tile.  Two accumulator pairs
+// shared-memory tile layout (MN-major, 128-byte swizzle, parts hi, r1, r2, r11), so each 32-K
+// stage is one 32 KB bulk copy.  The k+q orbitals are written once per q as split rows (Re | Im)
+// of 256 values per part (hi, r1, r2); per stage, gatherer warps load the half of the 32 rows
+// idx_G(g) that the tile needs (negated where it needs -Re) and store it into the swizzled B
+// tiles.  Two accumulator pairs
 // (512 TMEM columns) alternate between tiles, so four epilogue warps write the previous
 // tile's Re or Im parts of rho (scaled, into the blocked layout rho[p/32][G][p%32]) while the
 // next one runs.  Every wait is bounded; on expiry bit 2 of the status word is set and the kernel
@@ -43,34 +48,49 @@ constexpr int PM = 128;                      // bands per tile (M)
 constexpr int PN = 128;                      // bands (N) of one tile (its Re or Im part)
 constexpr int PROW = 256;                    // values per prepared k+q row: (Re | Im) x bands
 constexpr int PK = 32;                       // K per stage
-constexpr int PNS = 6;                       // stages in the ring
+constexpr int PNS = 4;                       // stages in the ring
+constexpr int NPA = 4, NPB = 3;              // operand parts: A hi, r1, r2, r11; B hi, r1, r2
 constexpr int PA_BYTES = PM * PK * 2;        // 8 KB, one 16-bit A tile
 constexpr int PB_BYTES = PN * PK * 2;        // 8 KB
-constexpr int PSTAGE = 2 * PA_BYTES + 2 * PB_BYTES;   // 32 KB
+constexpr int PSTAGE = NPA * PA_BYTES + NPB * PB_BYTES;   // 56 KB
 constexpr int PA_SBO = (PM / 64) * 1024;
 constexpr int PB_SBO = (PN / 64) * 1024;
 constexpr int PW_MMA = 0, PW_LOAD = 1, PW_G0 = 2, PW_E0 = 10;   // warps; gatherers 2..9, epilogue 10..13
 constexpr int PTHREADS = 14 * 32;
-constexpr double kGrid = 2048.0;             // 2^11: hi = rint(kGrid x), lo = kGrid x - hi
+constexpr double kGrid = 2048.0;             // 2^11: hi = rint(kGrid x), r = kGrid x - hi
+constexpr double kRest = 4096.0;             // 2^12: r1 = fp16(kRest r), r2 = fp16(kRest r - r1)
+constexpr float kSmall = 1.0f / 4096.0f;     // small-product accumulator (scale 2^34) -> 2^22
 
-// Fixed-grid split of 8 coefficients (already multiplied by kGrid) into FP16 hi and lo.
-__device__ __forceinline__ void grid_split(const double* x, uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
+// Fixed-grid split of 8 coefficients (already multiplied by kGrid): part[0] hi, part[1] r1,
+// part[2] r2, part[3] r11, each 8 x FP16.
+__device__ __forceinline__ void grid_split(const double* x, uint4* part) {
+  uint32_t o[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const double a = rint(x[2 * i]), b = rint(x[2 * i + 1]);
-    __half2 hh = __floats2half2_rn((float)a, (float)b);   // integers of at most 2^11: exact
-    __half2 ll = __floats2half2_rn((float)(x[2 * i] - a), (float)(x[2 * i + 1] - b));
-    h[i] = *reinterpret_cast<uint32_t*>(&hh);
-    l[i] = *reinterpret_cast<uint32_t*>(&ll);
+    double hv[2], rv[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      hv[e] = rint(x[2 * i + e]);
+      rv[e] = x[2 * i + e] - hv[e];   // exact
+    }
+    __half2 h = __floats2half2_rn((float)hv[0], (float)hv[1]);   // integers <= 2^11: exact
+    const double s0 = rv[0] * kRest, s1 = rv[1] * kRest;
+    __half2 r1 = __floats2half2_rn((float)s0, (float)s1);
+    const float2 r1f = __half22float2(r1);
+    __half2 r2 = __floats2half2_rn((float)(s0 - (double)r1f.x), (float)(s1 - (double)r1f.y));
+    __half2 r11 = __floats2half2_rn((float)rv[0], (float)rv[1]);
+    o[0][i] = *reinterpret_cast<uint32_t*>(&h);
+    o[1][i] = *reinterpret_cast<uint32_t*>(&r1);
+    o[2][i] = *reinterpret_cast<uint32_t*>(&r2);
+    o[3][i] = *reinterpret_cast<uint32_t*>(&r11);
   }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) part[j] = make_uint4(o[j][0], o[j][1], o[j][2], o[j][3]);
 }
 
 struct PParams {
-  const uint4* A;             // [nk][nst][hi | lo tile] prepared A' (16 KB per stage)
-  const uint4* B;             // [nk][npw + 1][hi | lo][PROW fp16] k+q rows, last row zero
+  const uint4* A;             // [nk][nst][hi | r1 | r2 | r11 tile] prepared A' (32 KB per stage)
+  const uint4* B;             // [nk][npw + 1][hi | r1 | r2][PROW fp16] k+q rows, last row zero
   const int32_t* gather;      // [nk][nG][npw]
   float2* rho;                // blocked [ld/32][gpad][32]
   int* status;
@@ -78,7 +98,7 @@ struct PParams {
   float scale;                // applied to C' when storing rho
 };
 
-// A'[k][stage][hi|lo]: thread per (k, stage, K in stage, chunk of 8 bands).
+// A'[k][stage][part]: thread per (k, stage, K in stage, chunk of 8 bands).
 __global__ void pd_prep_a(const double2* __restrict__ ck, int nk, int nb, int npw, int npwp, int nst,
                           uint4* __restrict__ A) {
   const long long total = (long long)nk * nst * PK * (PM / 8);
@@ -101,11 +121,12 @@ __global__ void pd_prep_a(const double2* __restrict__ ck, int nk, int nb, int np
       }
       v[i] = x;
     }
-    uint4 hi, lo;
-    grid_split(v, hi, lo);
-    uint8_t* tile = reinterpret_cast<uint8_t*>(A) + ((size_t)k * nst + s) * 2 * PA_BYTES;
-    *reinterpret_cast<uint4*>(tile + mn_chunk(kk, c, PA_SBO)) = hi;
-    *reinterpret_cast<uint4*>(tile + PA_BYTES + mn_chunk(kk, c, PA_SBO)) = lo;
+    uint4 part[4];
+    grid_split(v, part);
+    uint8_t* tile = reinterpret_cast<uint8_t*>(A) + ((size_t)k * nst + s) * NPA * PA_BYTES;
+#pragma unroll
+    for (int j = 0; j < NPA; ++j)
+      *reinterpret_cast<uint4*>(tile + j * PA_BYTES + mn_chunk(kk, c, PA_SBO)) = part[j];
   }
 }
 
@@ -128,11 +149,11 @@ __global__ void pd_prep_b(const double2* __restrict__ ckq, int nk, int nb, int n
       }
       v[i] = x;
     }
-    uint4 hi, lo;
-    grid_split(v, hi, lo);
-    uint4* row = B + ((size_t)k * (npw + 1) + j) * (2 * PROW / 8);
-    row[c] = hi;
-    row[PROW / 8 + c] = lo;
+    uint4 part[4];
+    grid_split(v, part);
+    uint4* row = B + ((size_t)k * (npw + 1) + j) * (NPB * PROW / 8);
+#pragma unroll
+    for (int p = 0; p < NPB; ++p) row[p * (PROW / 8) + c] = part[p];
   }
 }
 
@@ -186,10 +207,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
         for (int s = 0; s < nst; ++s, ++it) {
           const int slot = it % PNS;
           if (!(ok = mbar_wait(&empty[slot], ((it / PNS) & 1) ^ 1, &abort_s, P.status))) break;
-          mbar_expect_tx(&full[slot], 2 * PA_BYTES);
+          mbar_expect_tx(&full[slot], NPA * PA_BYTES);
           bulk_g2s(base + slot * PSTAGE,
-                   reinterpret_cast<const uint8_t*>(P.A) + ((size_t)k * nst + s) * 2 * PA_BYTES,
-                   2 * PA_BYTES, &full[slot]);
+                   reinterpret_cast<const uint8_t*>(P.A) + ((size_t)k * nst + s) * NPA * PA_BYTES,
+                   NPA * PA_BYTES, &full[slot]);
         }
       }
       // wait (bounded) for the last copies before the shared memory goes away
@@ -205,7 +226,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const int k = (t >> 1) / P.nG, G = (t >> 1) % P.nG, part = t & 1;
       const int32_t* tab = P.gather + ((size_t)k * P.nG + G) * P.npw;
-      const uint4* Bk = P.B + (size_t)k * (P.npw + 1) * (2 * PROW / 8);
+      const uint4* Bk = P.B + (size_t)k * (P.npw + 1) * (NPB * PROW / 8);
       for (int s = 0; s < nst; ++s, ++it) {
         if ((int)(it & 1) != grp) continue;
         const int slot = it % PNS;
@@ -218,23 +239,21 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
         const int g = im ? K - P.npwp : K;
         int j = g < P.npw ? tab[g] : -1;
         if (j < 0) j = P.npw;                    // the zero row
-        const uint4* row = Bk + (size_t)j * (2 * PROW / 8);
+        const uint4* row = Bk + (size_t)j * (NPB * PROW / 8);
         // Re tile: Re c' (first K half), Im c' (second); Im tile: Im c', then -Re c'
         const int off = (part ^ (im ? 1 : 0)) ? PN / 8 : 0;
         const bool neg = part && im;
-        uint4 h[4], l[4];
+        uint4 v[NPB][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          h[i] = row[off + c0 + i];
-          l[i] = row[PROW / 8 + off + c0 + i];
-        }
-        const uint32_t bt = base + slot * PSTAGE + 2 * PA_BYTES;
+        for (int p = 0; p < NPB; ++p)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int c = c0 + i;
-          st_shared_v4(bt + mn_chunk(kk, c, PB_SBO), neg ? neg16(h[i]) : h[i]);
-          st_shared_v4(bt + PB_BYTES + mn_chunk(kk, c, PB_SBO), neg ? neg16(l[i]) : l[i]);
-        }
+          for (int i = 0; i < 4; ++i) v[p][i] = row[p * (PROW / 8) + off + c0 + i];
+        const uint32_t bt = base + slot * PSTAGE + NPA * PA_BYTES;
+#pragma unroll
+        for (int p = 0; p < NPB; ++p)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            st_shared_v4(bt + p * PB_BYTES + mn_chunk(kk, c0 + i, PB_SBO), neg ? neg16(v[p][i]) : v[p][i]);
         fence_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[slot]);
@@ -250,7 +269,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       tc_fence_after();
-      const uint32_t d = tmem + buf * 2 * PN, dsm = d + PN;   // hi hi | hi lo + lo hi + lo lo
+      const uint32_t d = tmem + buf * 2 * PN, dsm = d + PN;   // hi hi | small products
       for (int s = 0; s < nst; ++s, ++it) {
         const int slot = it % PNS;
         if (lane == 0) ok = mbar_wait(&full[slot], (it / PNS) & 1, &abort_s, P.status);
@@ -258,18 +277,21 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
         if (!ok) break;
         tc_fence_after();
         if (lane == 0) {
-          const uint32_t sa = base + slot * PSTAGE, sb = sa + 2 * PA_BYTES;
+          const uint32_t sa = base + slot * PSTAGE, sb = sa + NPA * PA_BYTES;
 #pragma unroll
           for (int kq = 0; kq < PK / 16; ++kq) {
-            const uint64_t dAh = sdesc(sa + kq * 2 * PA_SBO, 1024, PA_SBO);
-            const uint64_t dAl = sdesc(sa + PA_BYTES + kq * 2 * PA_SBO, 1024, PA_SBO);
-            const uint64_t dBh = sdesc(sb + kq * 2 * PB_SBO, 1024, PB_SBO);
-            const uint64_t dBl = sdesc(sb + PB_BYTES + kq * 2 * PB_SBO, 1024, PB_SBO);
+            uint64_t dA[NPA], dB[NPB];
+#pragma unroll
+            for (int p = 0; p < NPA; ++p) dA[p] = sdesc(sa + p * PA_BYTES + kq * 2 * PA_SBO, 1024, PA_SBO);
+#pragma unroll
+            for (int p = 0; p < NPB; ++p) dB[p] = sdesc(sb + p * PB_BYTES + kq * 2 * PB_SBO, 1024, PB_SBO);
             const uint32_t acc = (s > 0 || kq > 0) ? 1u : 0u;
-            mma1(d, dAh, dBh, idesc, acc);
-            mma1(dsm, dAh, dBl, idesc, acc);
-            mma1(dsm, dAl, dBh, idesc, 1u);
-            mma1(dsm, dAl, dBl, idesc, 1u);
+            mma1(d, dA[0], dB[0], idesc, acc);     // hi hi (exact)
+            mma1(dsm, dA[0], dB[1], idesc, acc);   // hi r1'
+            mma1(dsm, dA[0], dB[2], idesc, 1u);    // hi r2'
+            mma1(dsm, dA[1], dB[0], idesc, 1u);    // r1 hi'
+            mma1(dsm, dA[2], dB[0], idesc, 1u);    // r2 hi'
+            mma1(dsm, dA[3], dB[1], idesc, 1u);    // r11 r1'
           }
           mma1_commit(&empty[slot]);
         }
@@ -301,21 +323,21 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
       float* out = reinterpret_cast<float*>(P.rho) + part;
 #pragma unroll 1
       for (int c = 0; c < PN / 16; ++c) {
-        uint32_t re[16], im[16];   // the two accumulators' columns 16 c .. 16 c + 15
+        uint32_t big[16], sml[16];   // the two accumulators' columns 16 c .. 16 c + 15
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + buf * 2 * PN + c * 16;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
             "%13,%14,%15}, [%16];"
-            : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]),
-              "=r"(re[6]), "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]),
-              "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
+            : "=r"(big[0]), "=r"(big[1]), "=r"(big[2]), "=r"(big[3]), "=r"(big[4]), "=r"(big[5]),
+              "=r"(big[6]), "=r"(big[7]), "=r"(big[8]), "=r"(big[9]), "=r"(big[10]), "=r"(big[11]),
+              "=r"(big[12]), "=r"(big[13]), "=r"(big[14]), "=r"(big[15])
             : "r"(ta));
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
             "%13,%14,%15}, [%16];"
-            : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]),
-              "=r"(im[6]), "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]),
-              "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
+            : "=r"(sml[0]), "=r"(sml[1]), "=r"(sml[2]), "=r"(sml[3]), "=r"(sml[4]), "=r"(sml[5]),
+              "=r"(sml[6]), "=r"(sml[7]), "=r"(sml[8]), "=r"(sml[9]), "=r"(sml[10]), "=r"(sml[11]),
+              "=r"(sml[12]), "=r"(sml[13]), "=r"(sml[14]), "=r"(sml[15])
             : "r"(ta + PN));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (n < P.nb) {
@@ -325,7 +347,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
             if (np_ < P.nb) {
               const long long p = p0 + np_;
               out[2 * (((size_t)((p >> 5) * P.gpad + G) << 5) + (size_t)(p & 31))] =
-                  (__uint_as_float(re[j]) + __uint_as_float(im[j])) * P.scale;
+                  __fmaf_rn(__uint_as_float(sml[j]), kSmall, __uint_as_float(big[j])) * P.scale;
             }
           }
         }
@@ -355,8 +377,8 @@ lrt_status launch_pair_density_tc(const lrt_ctx* c, const QData& q, void* rho, c
   const int npwp = (npw + PK - 1) / PK * PK;
   const int nst = 2 * npwp / PK;
   lrt_ctx* cc = const_cast<lrt_ctx*>(c);
-  const size_t a_bytes = (size_t)c->nk * nst * 2 * PA_BYTES;
-  const size_t b_bytes = (size_t)c->nk * (npw + 1) * 2 * PROW * 2;
+  const size_t a_bytes = (size_t)c->nk * nst * NPA * PA_BYTES;
+  const size_t b_bytes = (size_t)c->nk * (npw + 1) * NPB * PROW * 2;
   if (cc->dw.pd_bytes < a_bytes + b_bytes) {
     cudaFree(cc->dw.pd_work);
     cc->dw.pd_work = nullptr;

@@ -2,12 +2,15 @@
 the FP64 kernel, element by element on the same orbitals (through the C ABI test hook
 lrtddft_get_pair_densities).
 
-The tensor-core form splits every orbital coefficient on a fixed grid (hi = rint(2^11 x),
-exact in FP16, lo = the FP16 rest) so that the FP32 accumulator sums the hi*hi products exactly;
-what is left is the FP16 rounding of lo and the truncation of the small-product accumulator,
-~1e-7 of the largest |rho|, held to 1e-6.  The FP32 SIMT kernel (round-to-nearest FMA) is held
-to 2e-6.  Cases span several tiles with ragged band counts, G counts and plane-wave padding,
-up to the 128-band limit of the tensor-core tile; above it the SIMT kernel runs.
+The tensor-core form splits every orbital coefficient x into hi = rint(2^11 x) (exact in FP16)
+and a rest carried as a classic FP16 pair, so that the FP32 accumulator sums the hi*hi products
+exactly and the small products lose nothing that matters; what is left is the FP32 rounding
+of the output (~3e-8 of the largest |rho|).  Bounds: 2e-7 of the largest |rho| element-wise
+and, because small interband densities enter near-cancelling sums (the T tangent of the
+adjoint), a median relative error of 1e-7 over the elements above 1e-4 of the largest.  The
+FP32 SIMT kernel (round-to-nearest FMA) is held to 2e-6 and 5e-7.  Cases span several tiles
+with ragged band counts, G counts and plane-wave padding, up to the 128-band limit of the
+tensor-core tile; above it the SIMT kernel runs.
 """
 import numpy as np
 import pytest
@@ -49,8 +52,11 @@ def test_tensor_core_pair_densities(name):
     assert nb == nb2
     for iq in range(wl.nq):
         scale = np.abs(ref[iq]).max()
-        assert np.abs(tc[iq] - ref[iq]).max() <= 1e-6 * scale, (name, iq)
+        big = np.abs(ref[iq]) > 1e-4 * scale
+        assert np.abs(tc[iq] - ref[iq]).max() <= 2e-7 * scale, (name, iq)
+        assert np.median(np.abs(tc[iq] - ref[iq])[big] / np.abs(ref[iq][big])) <= 1e-7, (name, iq)
         assert np.abs(simt[iq] - ref[iq]).max() <= 2e-6 * scale, (name, iq)
+        assert np.median(np.abs(simt[iq] - ref[iq])[big] / np.abs(ref[iq][big])) <= 5e-7, (name, iq)
 
 
 def test_repeat_calls_agree():
