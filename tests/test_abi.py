@@ -156,3 +156,25 @@ def test_host_geometry_matches_oracle(lib, wl):
                 assert np.array_equal(got, ref)
                 assert np.all(mil[s, ik, npk[s, ik]:] == np.iinfo(np.int32).min)
     lib.lrtddft_destroy(h)
+
+
+def test_tuning_flags_and_hooks_on_host(lib):
+    st, h = _host_ctx(W.tiny())
+    assert st == 0
+    # LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q | LRT_TUNE_PAIR_SIMT are the known flags
+    for flags in (0, 1, 2, 4, 7):
+        assert lib.lrtddft_set_tuning(h, flags, -1, 0) == 0, flags
+    for flags in (8, 16, -1):
+        assert lib.lrtddft_set_tuning(h, flags, -1, 0) == binding.LRT_EINVAL, flags
+    for v, u in ((2, 0), (-2, 0), (0, 100), (0, -64)):
+        assert lib.lrtddft_set_tuning(h, 0, v, u) == binding.LRT_EINVAL, (v, u)
+    assert lib.lrtddft_set_tuning(h, 0, 1, 128) == 0
+    v, u = C.c_int(), C.c_int()
+    assert lib.lrtddft_get_tuning(h, C.byref(v), C.byref(u)) == 0
+    assert (v.value, u.value) == (-1, 0)   # no tensor-core launch has run
+    out = np.zeros(16)
+    D = C.POINTER(C.c_double)
+    assert lib.lrtddft_get_pair_densities(h, 0, out.ctypes.data_as(D)) == binding.LRT_ESTATE
+    assert lib.lrtddft_get_pair_densities(h, 5, out.ctypes.data_as(D)) == binding.LRT_EINVAL
+    assert lib.lrtddft_get_pair_densities(h, 0, None) == binding.LRT_EINVAL
+    lib.lrtddft_destroy(h)
