@@ -62,10 +62,13 @@ enum { LRT_POT_EMPTY_CORE = 0, LRT_POT_ZERO = 1 };
 enum { LRT_BASIS_SPHERE = 0, LRT_BASIS_FIXED = 1 };
 enum { LRT_K_COMMENSURATE = 0, LRT_K_TR_SYMMETRIC = 1 };
 enum { LRT_KERNEL_RPA = 0, LRT_KERNEL_RPA_ALDA = 1, LRT_KERNEL_FXC_MODEL = 2 };
-/* Precision of the chi0 contraction (the Dyson solve, S and F are always FP64):
- * FP64: FP64 products and sums;  FP16X3 / BF16X3: each operand split into a high and a low
- * 16-bit part, three tensor-core products (hi*hi + hi*lo + lo*hi) accumulated in FP32 and
- * flushed into FP64 partial sums. */
+/* Precision of the pair densities and the chi0 contraction (the Dyson solve, S and F are
+ * always FP64):
+ * FP64: FP64 products and sums;  FP16X3 / BF16X3: pair densities in FP32 (tensor cores with a
+ * fixed-grid FP16 split whose high products are summed exactly, N_b <= 128; else the FP32
+ * SIMT kernel), and each contraction operand split into a high and a low 16-bit part, three
+ * tensor-core products (hi*hi + hi*lo + lo*hi) accumulated in FP32 and flushed into FP64
+ * partial sums.  FP16X3 is the FP32-emulating form (hi + lo carry about 22 bits). */
 enum { LRT_PREC_FP64 = 0, LRT_PREC_FP16X3 = 1, LRT_PREC_BF16X3 = 2 };
 enum { LRT_ITCF_FOLD = 0, LRT_ITCF_DIRECT = 1 };
 
