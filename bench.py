@@ -33,7 +33,6 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-CONFIG_INDEX = 1
 METRIC = "chi0 complex MAC/s (split-precision chi0, FP64 Dyson/S/F, whole response path)"
 UNIT = "cMAC/s"
 
@@ -59,7 +58,7 @@ def parse():
 
 def workload(nq=0, kmesh=0):
     from paper_2510_01875_gb300 import workloads as W
-    wl = W.CONFIGS[CONFIG_INDEX]()
+    wl = W.al1_fcc_k12_b120()
     if nq:
         wl = wl.replace(q=wl.q[:nq], nG=wl.nG[:nq])
     if kmesh:
@@ -393,22 +392,22 @@ def run_extras(args, ctx_main, wl):
                         "split_rate_same_slice": sp["cmac"] / (sp["ms"] / 1e3),
                         "split_vs_fp64_chi0_err": err}
     # accuracy of the split form against FP64 on the 1-atom 8^3 workload (full S and F)
-    c0 = W.config0()
+    small = W.al1_fcc_k8_b24()
     res = {}
     for prec in ("fp64", args.precision if args.precision != "fp64" else "fp16x3"):
-        c = binding.Context(c0, prec)
+        c = binding.Context(small, prec)
         c.chi0_assemble()
         c.dyson_solve()
         S = c.dsf()
-        F, m = c.itcf(np.linspace(0.0, 0.5 / c0.T, c0.ntau))
+        F, m = c.itcf(np.linspace(0.0, 0.5 / small.T, small.ntau))
         res[prec] = (c.get_chi0(0), S, F)
         c.close()
     a = res["fp64"]
     b = res[[k for k in res if k != "fp64"][0]]
-    peaks = [j for j in range(1, c0.nw - 1) if a[1][0, j] > a[1][0, j - 1] and a[1][0, j] >= a[1][0, j + 1]
+    peaks = [j for j in range(1, small.nw - 1) if a[1][0, j] > a[1][0, j - 1] and a[1][0, j] >= a[1][0, j + 1]
              and a[1][0, j] > 0.1 * a[1][0].max()]
     out["split_accuracy"] = {
-        "workload": c0.name,
+        "workload": small.name,
         "chi0_maxnorm_rel": float(np.abs(b[0] - a[0]).max() / np.abs(a[0]).max()),
         "S_maxnorm_rel": float(np.abs(b[1] - a[1]).max() / np.abs(a[1]).max()),
         "S_peak_rel": float(max(abs(b[1][0, j] / a[1][0, j] - 1) for j in peaks)) if peaks else None,
@@ -451,8 +450,8 @@ def oracle_sample(wl, seconds=15.0):
     per_w = (time.perf_counter() - t0) / 4
     nw = int(max(4, min(len(freqs), seconds / max(per_w, 1e-6))))
     t0 = time.perf_counter()
-    c0 = response.chi0(rho, d, df, freqs[:nw], wl.eta, 1, om)
-    x = response.dyson_column0(c0, K)
+    chi0s = response.chi0(rho, d, df, freqs[:nw], wl.eta, 1, om)
+    x = response.dyson_column0(chi0s, K)
     S = -x[:, 0].imag
     dt = time.perf_counter() - t0 + t_rho
     cmac = float(len(gset)) ** 2 * nw * len(d)

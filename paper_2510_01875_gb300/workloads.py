@@ -153,7 +153,7 @@ class Workload:
         return dataclasses.replace(self, **kw)
 
 
-def config0(zero_potential: bool = False) -> Workload:
+def al1_fcc_k8_b24(zero_potential: bool = False) -> Workload:
     """fcc Al primitive cell, 8^3 Gamma mesh, 24 bands, T = 1 eV, one q = (0.5,0,0) 2pi/a
     (commensurate: (0,1/4,1/4) in reduced coordinates), 15 G, 256 omega on [0,60] eV."""
     a = AL_A
@@ -166,7 +166,7 @@ def config0(zero_potential: bool = False) -> Workload:
         omega=np.linspace(0.0, ev(60.0), 256), kernel="rpa_alda")
 
 
-def config1() -> Workload:
+def al1_fcc_k12_b120() -> Workload:
     """Same Al cell at T = 10 eV: 12^3 mesh, 120 bands (16 Ha cutoff), 59 G, 1024 omega on
     [-40,120] eV, eta = 0.5 eV, 8 q with |q| in [0.5,2.5] 1/A along x."""
     a = AL_A
@@ -179,7 +179,7 @@ def config1() -> Workload:
         omega=np.linspace(ev(-40.0), ev(120.0), 1024), kernel="rpa_alda")
 
 
-def config2() -> Workload:
+def al32_k4_b400() -> Workload:
     """32-atom fcc supercell (2x2x2 conventional) with sigma = 0.15 bohr displacements,
     T = 5 eV, 4^3 mesh, 400 bands, 24 detector-cone q (|q| = 1.5 1/A +- 5 %, 3 degrees),
     N_G per q seeded-uniform in [60,200], 2048 omega on [-50,150] eV, eta = 0.3 eV."""
@@ -196,7 +196,7 @@ def config2() -> Workload:
         omega=np.linspace(ev(-50.0), ev(150.0), 2048), kernel="rpa_alda")
 
 
-def config3() -> Workload:
+def al4_cubic_k6_b200() -> Workload:
     """4-atom conventional cubic Al cell, T = 20 eV, 6^3 mesh, 200 bands, 89 G, 16 q with
     |q| in [0.5,3] 1/A along x, 2048 omega on [-100,300] eV, eta = 0.5 eV,
     static f_xc(q) = A f_ALDA (1 + B q^2) exp(-C q^2) with (A,B,C) = (1, 0.1, 0.05)."""
@@ -210,7 +210,7 @@ def config3() -> Workload:
         kernel="fxc_model", fxc_params=(1.0, 0.1, 0.05))
 
 
-def config4() -> Workload:
+def al64_k2_b1600() -> Workload:
     """64-atom 4x4x4 primitive fcc supercell, sigma = 0.25 bohr, T = 50 eV, 2^3 mesh,
     1600 bands, 300 G, 48 detector-cone q, 4096 omega on [-200,600] eV, eta = 0.5 eV."""
     rng = SplitMix64(SEED_BASE + 4)
@@ -225,7 +225,7 @@ def config4() -> Workload:
         omega=np.linspace(ev(-200.0), ev(600.0), 4096), kernel="rpa_alda")
 
 
-CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3, 4: config4}
+ALL = (al1_fcc_k8_b24, al1_fcc_k12_b120, al32_k4_b400, al4_cubic_k6_b200, al64_k2_b1600)
 
 
 def tiny(seed: int = 7, nq: int = 2, kscheme: str = "tr_symmetric", potential: str = "empty_core",

@@ -124,7 +124,7 @@ def test_params_and_adjoint_validation(lib):
     lib.lrtddft_destroy(h)
 
 
-@pytest.mark.parametrize("wl", [W.tiny(), W.tiny(kscheme="commensurate", nq=1), W.config0(),
+@pytest.mark.parametrize("wl", [W.tiny(), W.tiny(kscheme="commensurate", nq=1), W.al1_fcc_k8_b24(),
                                 W.tiny(basis="fixed", seed=3), W.tiny(kernel="fxc_model", seed=4)])
 def test_host_geometry_matches_oracle(lib, wl):
     if wl.kscheme == "commensurate" and wl.name.startswith("tiny"):

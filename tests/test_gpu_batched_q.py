@@ -30,9 +30,9 @@ def lib():
 
 
 def cone24():
-    c2 = W.config2()
+    big = W.al32_k4_b400()
     wl = W.tiny(seed=61, nq=24, nbands=8, kmesh=(2, 2, 2))
-    return wl.replace(q=c2.q, nG=c2.nG, omega=c2.omega, T=c2.T, eta=c2.eta, name="cone24_tiny")
+    return wl.replace(q=big.q, nG=big.nG, omega=big.omega, T=big.T, eta=big.eta, name="cone24_tiny")
 
 
 WL = cone24()

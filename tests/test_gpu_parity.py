@@ -92,9 +92,9 @@ def test_fp64_parity_commensurate():
     compare(wl, gpu_run(wl))
 
 
-def test_fp64_parity_config0():
+def test_fp64_parity_al1_fcc_k8():
     """The fcc Al, 8^3 mesh, 24 bands, 15 G, 256 frequencies workload, in full."""
-    wl = W.config0()
+    wl = W.al1_fcc_k8_b24()
     compare(wl, gpu_run(wl))
 
 

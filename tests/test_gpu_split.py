@@ -18,7 +18,7 @@ CASES = {
     # ragged: 70 bands -> 2.9e5 pairs (not a multiple of the 32-pair stage), 19 G -> 190 row
     # pairs (3 row tiles, last one partial), 46 frequencies (one partial column tile)
     "ragged": W.tiny(seed=9, nq=1, nbands=70, ecut=5.0, nG=19, nw=45, kmesh=(2, 1, 2)),
-    "al1_k8": W.config0(),
+    "al1_k8": W.al1_fcc_k8_b24(),
 }
 BOUNDS = {"fp16x3": {"F": 1e-5, "S": 1e-4, "chi0": 3e-5},
           "bf16x3": {"F": 1e-4, "S": 1e-3, "chi0": 1e-4}}

@@ -15,22 +15,22 @@ def test_splitmix64_reference_outputs():
 
 
 def test_workloads_shapes():
-    c0, c1, c3 = W.config0(), W.config1(), W.config3()
-    assert (c0.nq, c0.nw, c0.nk, c0.nbands, int(c0.nG[0])) == (1, 256, 512, 24, 15)
-    assert (c1.nq, c1.nw, c1.nk, c1.nbands, int(c1.nG[0])) == (8, 1024, 1728, 120, 59)
-    assert (c3.nq, c3.nw, c3.nk, c3.natoms) == (16, 2048, 216, 4)
-    c2 = W.config2()
-    assert c2.natoms == 32 and c2.nq == 24 and 60 <= c2.nG.min() and c2.nG.max() <= 200
-    qm = np.linalg.norm(c2.q, axis=1)
+    small, full, adj = W.al1_fcc_k8_b24(), W.al1_fcc_k12_b120(), W.al4_cubic_k6_b200()
+    assert (small.nq, small.nw, small.nk, small.nbands, int(small.nG[0])) == (1, 256, 512, 24, 15)
+    assert (full.nq, full.nw, full.nk, full.nbands, int(full.nG[0])) == (8, 1024, 1728, 120, 59)
+    assert (adj.nq, adj.nw, adj.nk, adj.natoms) == (16, 2048, 216, 4)
+    batched = W.al32_k4_b400()
+    assert batched.natoms == 32 and batched.nq == 24 and 60 <= batched.nG.min() and batched.nG.max() <= 200
+    qm = np.linalg.norm(batched.q, axis=1)
     assert np.all(np.abs(qm / W.inv_ang(1.5) - 1.0) <= 0.05 + 1e-12)
-    ang = np.degrees(np.arccos(c2.q[:, 0] / qm))
+    ang = np.degrees(np.arccos(batched.q[:, 0] / qm))
     assert ang.max() <= 3.0 + 1e-9
     # the same seed gives the same cell
-    assert np.array_equal(W.config2().positions, c2.positions)
+    assert np.array_equal(W.al32_k4_b400().positions, batched.positions)
 
 
 def test_reciprocal_lattice():
-    for lat in (W.fcc_primitive(W.AL_A), W.AL_A * np.eye(3), W.config2().lattice):
+    for lat in (W.fcc_primitive(W.AL_A), W.AL_A * np.eye(3), W.al32_k4_b400().lattice):
         B = crystal.reciprocal(lat)
         assert np.allclose(lat @ B.T, 2 * math.pi * np.eye(3), atol=1e-12)
 
@@ -49,7 +49,7 @@ def test_fcc_shell_closures():
 
 def test_response_gset_order_and_zero_first():
     lat = W.fcc_primitive(W.AL_A)
-    q = W.config0().q[0]
+    q = W.al1_fcc_k8_b24().q[0]
     gs = crystal.response_gset(lat, q, 15)
     assert len(gs) == 15 and not gs[0].any()
     B = crystal.reciprocal(lat)
