@@ -387,8 +387,9 @@ def run_extras(args, ctx_main, wl):
     err = float(np.abs(sp["chi0"] - fp["chi0"]).max() / np.abs(fp["chi0"]).max())
     out["fp64_form"] = {"value": fp["cmac"] / (fp["ms"] / 1e3), "unit": UNIT,
                         "chi0_tflops": 4.0 * fp["cmac"] / (fp["ms"] / 1e3) / 1e12,
-                        "sample": "1 q, 16 frequencies (15-17.5 eV), all 2.49e7 pairs; rate is "
-                                  "K-dominated so it extrapolates linearly to the full workload",
+                        "sample": f"1 q, 16 frequencies (15-17.5 eV), all {ctx_main.nk * ctx_main.nb ** 2:.3g} "
+                                  "pairs; rate is K-dominated so it extrapolates linearly to the "
+                                  "full workload",
                         "split_rate_same_slice": sp["cmac"] / (sp["ms"] / 1e3),
                         "split_vs_fp64_chi0_err": err}
     # accuracy of the split form against FP64 on the 1-atom 8^3 workload (full S and F)
