@@ -228,6 +228,10 @@ class Context:
 
     def set_tuning(self, auto: bool = False, single_q: bool = False, variant: int = -1, unit_stages: int = 0,
                    pair_simt: bool = False):
+        """lrtddft_set_tuning: auto times the contraction's variants and unit sizes on the first
+        launch of each shape; single_q launches the contraction once per q; pair_simt computes
+        the split path's pair densities on the FP32 SIMT kernel instead of the tensor cores;
+        variant (-1, 0, 1) and unit_stages (0 or a multiple of 64) force a choice."""
         flags = (1 if auto else 0) | (2 if single_q else 0) | (4 if pair_simt else 0)
         _check("lrtddft_set_tuning", self.lib.lrtddft_set_tuning(self.h, flags, variant, unit_stages))
 
