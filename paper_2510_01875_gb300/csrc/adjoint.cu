@@ -53,130 +53,130 @@ __global__ void __launch_bounds__(256) dyson_adjoint_kernel(
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) bad = 0;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-  const double2* X = chi0 + (size_t)w * N * N;
-  const double2* x = chi + (size_t)w * N;
-  __syncthreads();   // the previous frequency is done with A, b and fac
-  // A = M^T: A[r][j] = M[j][r] = delta_jr - chi0[j][r] K[r]
-  for (int e = tid; e < N * N; e += nt) {
-    int j = e / N, r = e % N;
-    double2 v = X[e];
-    double2 m = make_double2(-v.x * K[r], -v.y * K[r]);
-    if (r == j) m.x += 1.0;
-    A[r * ld + j] = m;
-  }
-  for (int r = tid; r < N; r += nt) b[r] = make_double2(r == 0 ? 1.0 : 0.0, 0.0);
-  __syncthreads();
-  for (int c = 0; c < N; ++c) {
-    if (tid < 32) {
-      double best = -1.0;
-      int bi = c;
-      for (int r = c + tid; r < N; r += 32) {
-        double2 v = A[r * ld + c];
-        double a = v.x * v.x + v.y * v.y;
-        if (a > best) {
-          best = a;
-          bi = r;
+    const double2* X = chi0 + (size_t)w * N * N;
+    const double2* x = chi + (size_t)w * N;
+    __syncthreads();   // the previous frequency is done with A, b and fac
+    // A = M^T: A[r][j] = M[j][r] = delta_jr - chi0[j][r] K[r]
+    for (int e = tid; e < N * N; e += nt) {
+      int j = e / N, r = e % N;
+      double2 v = X[e];
+      double2 m = make_double2(-v.x * K[r], -v.y * K[r]);
+      if (r == j) m.x += 1.0;
+      A[r * ld + j] = m;
+    }
+    for (int r = tid; r < N; r += nt) b[r] = make_double2(r == 0 ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    for (int c = 0; c < N; ++c) {
+      if (tid < 32) {
+        double best = -1.0;
+        int bi = c;
+        for (int r = c + tid; r < N; r += 32) {
+          double2 v = A[r * ld + c];
+          double a = v.x * v.x + v.y * v.y;
+          if (a > best) {
+            best = a;
+            bi = r;
+          }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          double ob = __shfl_down_sync(0xffffffffu, best, off);
+          int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+          }
+        }
+        if (tid == 0) {
+          piv_s = bi;
+          if (!(best > 0.0)) bad = 1;
         }
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
+      __syncthreads();
+      const int p = piv_s;
+      if (p != c) {
+        for (int j = tid; j < N; j += nt) {
+          double2 t = A[c * ld + j];
+          A[c * ld + j] = A[p * ld + j];
+          A[p * ld + j] = t;
+        }
+        if (tid == 0) {
+          double2 t = b[c];
+          b[c] = b[p];
+          b[p] = t;
         }
       }
-      if (tid == 0) {
-        piv_s = bi;
-        if (!(best > 0.0)) bad = 1;
+      __syncthreads();
+      const double2 d = A[c * ld + c];
+      for (int r = c + 1 + tid; r < N; r += nt) fac[r] = cdiv(A[r * ld + c], d);
+      __syncthreads();
+      const int rows = N - c - 1, cols = N - c;
+      for (int e = tid; e < rows * cols; e += nt) {
+        int r = c + 1 + e / cols;
+        int jj = e % cols;
+        double2 f = fac[r];
+        if (jj == cols - 1) {
+          double2 t = cmul(f, b[c]);
+          b[r].x -= t.x;
+          b[r].y -= t.y;
+        } else {
+          int j = c + 1 + jj;
+          double2 t = cmul(f, A[c * ld + j]);
+          A[r * ld + j].x -= t.x;
+          A[r * ld + j].y -= t.y;
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
-    const int p = piv_s;
-    if (p != c) {
-      for (int j = tid; j < N; j += nt) {
-        double2 t = A[c * ld + j];
-        A[c * ld + j] = A[p * ld + j];
-        A[p * ld + j] = t;
-      }
-      if (tid == 0) {
-        double2 t = b[c];
-        b[c] = b[p];
-        b[p] = t;
-      }
-    }
-    __syncthreads();
-    const double2 d = A[c * ld + c];
-    for (int r = c + 1 + tid; r < N; r += nt) fac[r] = cdiv(A[r * ld + c], d);
-    __syncthreads();
-    const int rows = N - c - 1, cols = N - c;
-    for (int e = tid; e < rows * cols; e += nt) {
-      int r = c + 1 + e / cols;
-      int jj = e % cols;
-      double2 f = fac[r];
-      if (jj == cols - 1) {
-        double2 t = cmul(f, b[c]);
+    for (int c = N - 1; c >= 0; --c) {
+      if (tid == 0) b[c] = cdiv(b[c], A[c * ld + c]);
+      __syncthreads();
+      const double2 xc = b[c];
+      for (int r = tid; r < c; r += nt) {
+        double2 t = cmul(A[r * ld + c], xc);
         b[r].x -= t.x;
         b[r].y -= t.y;
-      } else {
-        int j = c + 1 + jj;
-        double2 t = cmul(f, A[c * ld + j]);
-        A[r * ld + j].x -= t.x;
-        A[r * ld + j].y -= t.y;
+      }
+      __syncthreads();
+    }
+    // u = b.  v = K x + e_0.  r_G' = sum_G u_G chi0[G][G'];  dchi_00/dtheta_j = sum_G' r_G' dK_j,G' x_G'
+    for (int r = tid; r < N; r += nt) {
+      u_out[(size_t)w * N + r] = b[r];
+      double2 xv = x[r];
+      v_out[(size_t)w * N + r] = make_double2(K[r] * xv.x + (r == 0 ? 1.0 : 0.0), K[r] * xv.y);
+    }
+    double2 acc[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    for (int gp = tid; gp < N; gp += nt) {
+      double2 rg = make_double2(0, 0);
+      for (int g = 0; g < N; ++g) {
+        double2 t = cmul(b[g], X[(size_t)g * N + gp]);
+        rg.x += t.x;
+        rg.y += t.y;
+      }
+      const double2 rx = cmul(rg, x[gp]);
+      for (int j = 0; j < 3; ++j) {
+        acc[j].x += rx.x * dK[j * N + gp];
+        acc[j].y += rx.y * dK[j * N + gp];
       }
     }
-    __syncthreads();
-  }
-  for (int c = N - 1; c >= 0; --c) {
-    if (tid == 0) b[c] = cdiv(b[c], A[c * ld + c]);
-    __syncthreads();
-    const double2 xc = b[c];
-    for (int r = tid; r < c; r += nt) {
-      double2 t = cmul(A[r * ld + c], xc);
-      b[r].x -= t.x;
-      b[r].y -= t.y;
-    }
-    __syncthreads();
-  }
-  // u = b.  v = K x + e_0.  r_G' = sum_G u_G chi0[G][G'];  dchi_00/dtheta_j = sum_G' r_G' dK_j,G' x_G'
-  for (int r = tid; r < N; r += nt) {
-    u_out[(size_t)w * N + r] = b[r];
-    double2 xv = x[r];
-    v_out[(size_t)w * N + r] = make_double2(K[r] * xv.x + (r == 0 ? 1.0 : 0.0), K[r] * xv.y);
-  }
-  double2 acc[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-  for (int gp = tid; gp < N; gp += nt) {
-    double2 rg = make_double2(0, 0);
-    for (int g = 0; g < N; ++g) {
-      double2 t = cmul(b[g], X[(size_t)g * N + gp]);
-      rg.x += t.x;
-      rg.y += t.y;
-    }
-    const double2 rx = cmul(rg, x[gp]);
+    // block reduction of the three sums (one partial per warp)
     for (int j = 0; j < 3; ++j) {
-      acc[j].x += rx.x * dK[j * N + gp];
-      acc[j].y += rx.y * dK[j * N + gp];
-    }
-  }
-  // block reduction of the three sums (one partial per warp)
-  for (int j = 0; j < 3; ++j) {
-    double2 v = acc[j];
-    for (int off = 16; off > 0; off >>= 1) {
-      v.x += __shfl_down_sync(0xffffffffu, v.x, off);
-      v.y += __shfl_down_sync(0xffffffffu, v.y, off);
-    }
-    __syncthreads();
-    if ((tid & 31) == 0) red_s[tid >> 5] = v;
-    __syncthreads();
-    if (tid == 0) {
-      double2 s = make_double2(0, 0);
-      for (int i = 0; i < (nt >> 5); ++i) {
-        s.x += red_s[i].x;
-        s.y += red_s[i].y;
+      double2 v = acc[j];
+      for (int off = 16; off > 0; off >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, off);
       }
-      dk_out[(size_t)w * 3 + j] = s;
+      __syncthreads();
+      if ((tid & 31) == 0) red_s[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double2 s = make_double2(0, 0);
+        for (int i = 0; i < (nt >> 5); ++i) {
+          s.x += red_s[i].x;
+          s.y += red_s[i].y;
+        }
+        dk_out[(size_t)w * 3 + j] = s;
+      }
     }
-  }
   }
   if (tid == 0 && bad) atomicOr(status, 1);
 }

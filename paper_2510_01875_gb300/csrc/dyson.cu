@@ -38,92 +38,92 @@ __global__ void __launch_bounds__(256) dyson_kernel(const double2* __restrict__ 
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) bad = 0;
   for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-  const double2* X = chi0 + (size_t)w * N * N;
-  __syncthreads();   // the previous frequency's back substitution is done with M and b
-  for (int e = tid; e < N * N; e += nt) {
-    int r = e / N, j = e % N;
-    double2 v = X[e];
-    double2 m = make_double2(-v.x * K[j], -v.y * K[j]);
-    if (r == j) m.x += 1.0;
-    M[r * ld + j] = m;
-    if (j == 0) b[r] = v;
-  }
-  __syncthreads();
-  for (int c = 0; c < N; ++c) {
-    if (tid < 32) {
-      double best = -1.0;
-      int bi = c;
-      for (int r = c + tid; r < N; r += 32) {
-        double2 v = M[r * ld + c];
-        double a = v.x * v.x + v.y * v.y;
-        if (a > best) {
-          best = a;
-          bi = r;
-        }
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (tid == 0) {
-        piv_s = bi;
-        if (!(best > 0.0)) bad = 1;
-      }
+    const double2* X = chi0 + (size_t)w * N * N;
+    __syncthreads();   // the previous frequency's back substitution is done with M and b
+    for (int e = tid; e < N * N; e += nt) {
+      int r = e / N, j = e % N;
+      double2 v = X[e];
+      double2 m = make_double2(-v.x * K[j], -v.y * K[j]);
+      if (r == j) m.x += 1.0;
+      M[r * ld + j] = m;
+      if (j == 0) b[r] = v;
     }
     __syncthreads();
-    const int p = piv_s;
-    if (p != c) {
-      for (int j = tid; j < N; j += nt) {
-        double2 t = M[c * ld + j];
-        M[c * ld + j] = M[p * ld + j];
-        M[p * ld + j] = t;
+    for (int c = 0; c < N; ++c) {
+      if (tid < 32) {
+        double best = -1.0;
+        int bi = c;
+        for (int r = c + tid; r < N; r += 32) {
+          double2 v = M[r * ld + c];
+          double a = v.x * v.x + v.y * v.y;
+          if (a > best) {
+            best = a;
+            bi = r;
+          }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          double ob = __shfl_down_sync(0xffffffffu, best, off);
+          int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+          }
+        }
+        if (tid == 0) {
+          piv_s = bi;
+          if (!(best > 0.0)) bad = 1;
+        }
       }
-      if (tid == 0) {
-        double2 t = b[c];
-        b[c] = b[p];
-        b[p] = t;
+      __syncthreads();
+      const int p = piv_s;
+      if (p != c) {
+        for (int j = tid; j < N; j += nt) {
+          double2 t = M[c * ld + j];
+          M[c * ld + j] = M[p * ld + j];
+          M[p * ld + j] = t;
+        }
+        if (tid == 0) {
+          double2 t = b[c];
+          b[c] = b[p];
+          b[p] = t;
+        }
       }
+      __syncthreads();
+      const double2 d = M[c * ld + c];
+      for (int r = c + 1 + tid; r < N; r += nt) fac[r] = cdiv(M[r * ld + c], d);
+      __syncthreads();
+      const int rows = N - c - 1;
+      const int cols = N - c;  // columns c+1..N-1 plus the rhs
+      for (int e = tid; e < rows * cols; e += nt) {
+        int r = c + 1 + e / cols;
+        int jj = e % cols;
+        double2 f = fac[r];
+        if (jj == cols - 1) {
+          double2 t = cmul(f, b[c]);
+          b[r].x -= t.x;
+          b[r].y -= t.y;
+        } else {
+          int j = c + 1 + jj;
+          double2 t = cmul(f, M[c * ld + j]);
+          M[r * ld + j].x -= t.x;
+          M[r * ld + j].y -= t.y;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const double2 d = M[c * ld + c];
-    for (int r = c + 1 + tid; r < N; r += nt) fac[r] = cdiv(M[r * ld + c], d);
-    __syncthreads();
-    const int rows = N - c - 1;
-    const int cols = N - c;  // columns c+1..N-1 plus the rhs
-    for (int e = tid; e < rows * cols; e += nt) {
-      int r = c + 1 + e / cols;
-      int jj = e % cols;
-      double2 f = fac[r];
-      if (jj == cols - 1) {
-        double2 t = cmul(f, b[c]);
+    // back substitution, column oriented
+    for (int c = N - 1; c >= 0; --c) {
+      if (tid == 0) b[c] = cdiv(b[c], M[c * ld + c]);
+      __syncthreads();
+      const double2 xc = b[c];
+      for (int r = tid; r < c; r += nt) {
+        double2 t = cmul(M[r * ld + c], xc);
         b[r].x -= t.x;
         b[r].y -= t.y;
-      } else {
-        int j = c + 1 + jj;
-        double2 t = cmul(f, M[c * ld + j]);
-        M[r * ld + j].x -= t.x;
-        M[r * ld + j].y -= t.y;
       }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  // back substitution, column oriented
-  for (int c = N - 1; c >= 0; --c) {
-    if (tid == 0) b[c] = cdiv(b[c], M[c * ld + c]);
-    __syncthreads();
-    const double2 xc = b[c];
-    for (int r = tid; r < c; r += nt) {
-      double2 t = cmul(M[r * ld + c], xc);
-      b[r].x -= t.x;
-      b[r].y -= t.y;
-    }
-    __syncthreads();
-  }
-  for (int r = tid; r < N; r += nt) chi[(size_t)w * N + r] = b[r];
+    for (int r = tid; r < N; r += nt) chi[(size_t)w * N + r] = b[r];
   }
   if (tid == 0 && bad) atomicOr(status, 1);
 }
