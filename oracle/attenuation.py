@@ -29,9 +29,13 @@ paper's order:
 
 The filter acts on the uniformly spaced samples with w >= 0 of the caller's grid.
 
-Parity: SG itself is pinned (polynomial exactness, the classic 5-point table); the
-AICc and penalty choices are readings of an unstated recipe, so the selection step
-is "parity unpinned" beyond those pins.
+Pinned by (tests/test_oracle_attenuation.py): the SG filter (polynomial exactness, the
+classic 5-point table, the hat diagonal of the edge rows against the explicit projection
+V (V^T V)^{-1} V^T), the Hann periodogram against its closed form as a sum of geometric
+series, the target bins of planted cosines (with the low-frequency exclusion), and AICc,
+the trace of the smoother and the curvature ratio on a hand-worked 10-sample example.
+The weights and the form of the score are readings (the paper states neither); given
+those readings every ingredient of the selection is pinned.
 """
 from __future__ import annotations
 
@@ -127,6 +131,24 @@ def target_bins(tg, K):
     return sorted(bins)
 
 
+def aicc(rss: float, N: int, k: float) -> float:
+    """Corrected Akaike criterion of a linear smoother: N ln(RSS/N) + 2k + 2k(k+1)/(N-k-1),
+    k = trace of the smoother matrix (its effective number of parameters)."""
+    return N * math.log(max(rss, 1e-300) / N) + 2.0 * k + 2.0 * k * (k + 1.0) / (N - k - 1.0)
+
+
+def retention(P_raw: np.ndarray, P_filt: np.ndarray, bins) -> float:
+    """R_f: power of the filtered dS/dw kept in the target bins / the raw power there."""
+    raw = float(np.sum(P_raw[bins])) if len(bins) else 0.0
+    return float(np.sum(P_filt[bins])) / raw if raw > 0 else 0.0
+
+
+def curvature_ratio(yf: np.ndarray, y: np.ndarray) -> float:
+    """sum of squared second differences of the filtered spectrum / the same of the raw one."""
+    raw = float(np.sum(np.diff(y, 2) ** 2))
+    return float(np.sum(np.diff(yf, 2) ** 2)) / raw if raw > 0 else 0.0
+
+
 def sign_changes(D: np.ndarray) -> int:
     s = np.sign(D)
     s = s[s != 0]
@@ -158,8 +180,6 @@ def attenuate(omega, S, S0, T, ntau, p: AttenParams):
     K = len(P) - 1
     tg = targets(P, p.n_targets, p.low_exclude)
     bins = target_bins(tg, K)
-    raw_power = float(np.sum(P[bins])) if bins else 0.0
-    curv_raw = float(np.sum(np.diff(y, 2) ** 2))
     lf = N if p.lambda_f < 0 else p.lambda_f
     lc = N if p.lambda_c < 0 else p.lambda_c
     w_lo = p.w_min if p.w_min > 0 else 4.0 * dw
@@ -182,12 +202,10 @@ def attenuate(omega, S, S0, T, ntau, p: AttenParams):
             k = float(np.sum(hat))
             if N - k - 1.0 <= 0.0:
                 continue
-            aicc = N * math.log(max(rss, 1e-300) / N) + 2.0 * k + 2.0 * k * (k + 1.0) / (N - k - 1.0)
             Df = derivative(yf, dw, i0, i1)
-            rf = float(np.sum(periodogram(Df)[bins])) / raw_power if raw_power > 0 else 0.0
+            rf = retention(P, periodogram(Df), bins)
             fpen = math.log(max(rf, p.retain_floor) / p.retain_floor)
-            cpen = float(np.sum(np.diff(yf, 2) ** 2)) / curv_raw if curv_raw > 0 else 0.0
-            score = aicc + lf * fpen + lc * cpen
+            score = aicc(rss, N, k) + lf * fpen + lc * curvature_ratio(yf, y)
             cand = (score, sign_changes(Df), m, yf)
             if best is None:
                 best = cand
