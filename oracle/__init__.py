@@ -18,7 +18,7 @@ or fusion beyond what the definition states:
                 F(q,tau) (Eq. 1 with detailed balance), F-tilde (Eq. 2), metrics
   attenuation.py Savitzky-Golay / AICc / constraints filter (Sec. 3, Eqs. 5-7)
   lindhard.py   continuum finite-temperature Lindhard function (pins only)
-  tangent.py    forward-mode tangents of F(q,tau) for the gradient pins
+  adjoint.py    forward-mode tangents of S(q,w) and F(q,tau) for the gradient pins
   pipeline.py   runs the steps above for one workload
 
 Parity status per function is listed in each module header.

@@ -15,7 +15,12 @@ every step, in the order of the forward path, so the two share nothing but the d
                temperature value at the mean density, so K does not depend on T;
   Dyson        M = 1 - chi0 K, chi_{:,0} = M^{-1} chi0_{:,0}:
                d chi_{:,0} = M^{-1} [d chi0 (K chi_{:,0} + e_0) + chi0 dK chi_{:,0}];
-  S (Eq. 8)    S = -Im chi_00/(pi n (1 - e^{-w/T})), w -> 0 form -Im chi_00(h) T/(pi n h);
+  S (Eq. 8)    S = -Im chi_00/(pi n (1 - e^{-w/T})); at w = 0 the limit
+               S(0) = (T/(pi n)) Re s, s = d chi_00/d eta = [M^{-1} E v]_0, E = d chi0/d eta,
+               v = K chi_{:,0} + e_0, whose tangents are second derivatives:
+               d(M^{-1} E v) = M^{-1} [dE v + E dv - dM M^{-1} E v],  dM = -(d chi0 K + chi0 dK),
+               dE/dT = sum_p rho rho* (-i d df_p/dT)/(w + Delta_p + i eta)^2,
+               dE/deta = sum_p rho rho* (-2 df_p)/(w + Delta_p + i eta)^3;
   F (Eq. 1)    the detailed-balance fold; tau is held fixed (absolute), so T also enters
                through e^{-(1/T - tau) w}.
 """
@@ -97,6 +102,8 @@ def tangents_q(wl, iq: int, tau) -> dict:
     dchi00 = np.zeros((len(freqs), NTHETA), dtype=np.complex128)
     e0 = np.zeros(nG, dtype=np.complex128)
     e0[0] = 1.0
+    s0 = 0.0
+    ds0 = np.zeros(NTHETA, dtype=np.complex128)
     for iw, w in enumerate(freqs):
         den = w + delta + 1j * wl.eta
         wt = df / den
@@ -110,6 +117,24 @@ def tangents_q(wl, iq: int, tau) -> dict:
         rhs = np.stack([dc_T @ v, dc_eta @ v] + [c0 @ (dK[j] * x) for j in range(3)])
         dx = response.solve_gauss(np.repeat(M[None], NTHETA, axis=0), rhs)
         dchi00[iw] = dx[:, 0]
+        if iw == hcol:
+            # s = d chi_00/d eta at w = 0 and its tangents (second derivatives of chi_00)
+            y = response.solve_gauss(M[None], (dc_eta @ v)[None])[0]
+            s0 = y[0]
+            dE = [pref * ((rho * (-1j * ddf / den ** 2)[:, None]).T @ rho.conj()),
+                  pref * ((rho * (-2.0 * df / den ** 3)[:, None]).T @ rho.conj())]
+            dc = [dc_T, dc_eta]
+            r = []
+            for j in range(NTHETA):
+                dKj = dK[j - 2] if j >= 2 else np.zeros(nG)
+                dcj = dc[j] if j < 2 else np.zeros_like(c0)
+                dv = dKj * x + K * dx[j]
+                dM = -(dcj * K[None, :] + c0 * dKj[None, :])
+                t = dc_eta @ dv - dM @ y
+                if j < 2:
+                    t = t + dE[j] @ v
+                r.append(t)
+            ds0 = response.solve_gauss(np.repeat(M[None], NTHETA, axis=0), np.stack(r))[:, 0]
 
     # S on the caller's grid and its tangents (Eq. 8)
     nw = len(wl.omega)
@@ -117,14 +142,14 @@ def tangents_q(wl, iq: int, tau) -> dict:
     dS = np.zeros((nw, NTHETA))
     for j, w in enumerate(wl.omega):
         if w == 0.0:
-            S[j], dS[j] = _s0_and_tangent(chi00[hcol], dchi00[hcol], T, n)
+            S[j], dS[j] = _s0_and_tangent(s0, ds0, T, n)
             continue
         g = 1.0 / (-math.expm1(-beta * w))
         S[j] = -chi00[j].imag * g / (math.pi * n)
         dS[j] = -dchi00[j].imag * g / (math.pi * n)
         dg = math.exp(-beta * w) * w / (T * T) * g * g
         dS[j, 0] += -chi00[j].imag * dg / (math.pi * n)
-    S0, dS0 = _s0_and_tangent(chi00[hcol], dchi00[hcol], T, n)
+    S0, dS0 = _s0_and_tangent(s0, ds0, T, n)
 
     # F (Eq. 1, detailed-balance fold) at fixed absolute tau
     wp, Sp = response.positive_branch(S, wl.omega, S0)
@@ -143,13 +168,12 @@ def tangents_q(wl, iq: int, tau) -> dict:
             "freqs": freqs, "hcol": hcol}
 
 
-def _s0_and_tangent(c, dc, T, n):
-    """S(0) = -Im chi_00(h) T/(pi n h) and its tangents."""
-    s = -c.imag * T / (math.pi * n * response.H_ZERO)
-    ds = -dc.imag * T / (math.pi * n * response.H_ZERO)
-    ds = np.array(ds, dtype=np.float64)
-    ds[0] += -c.imag / (math.pi * n * response.H_ZERO)
-    return s, ds
+def _s0_and_tangent(s, ds, T, n):
+    """S(0) = (T/(pi n)) Re s, s = d chi_00/d eta at w = 0, and its tangents."""
+    S0 = T * s.real / (math.pi * n)
+    dS0 = np.array(T * ds.real / (math.pi * n), dtype=np.float64)
+    dS0[0] += s.real / (math.pi * n)
+    return S0, dS0
 
 
 def itcf_at(wl, iq: int, tau) -> np.ndarray:
@@ -165,8 +189,10 @@ def itcf_at(wl, iq: int, tau) -> np.ndarray:
     K = r.kernel_diag(wl, q, gset)
     chi00 = r.dyson_column0(c0, K)[:, 0]
     n = r.density(wl)
-    S = r.dsf(chi00, wl.omega, hcol, wl.T, n)
-    S0 = r.s_zero(chi00, hcol, wl.T, n)
+    om = crystal.volume(wl.lattice)
+    deta = r.chi0_eta_derivative(rho, delta, df, 0.0, wl.eta, wl.nk, om)
+    S0 = r.s_zero(r.chi00_derivative(c0[hcol], deta, K), wl.T, n)
+    S = r.dsf(chi00, wl.omega, S0, wl.T, n)
     wp, Sp = r.positive_branch(S, wl.omega, S0)
     return r.itcf_fold(wp, Sp, tau, wl.T)
 

@@ -6,6 +6,8 @@ Test infrastructure only (see oracle/__init__.py).
       (2/(N_k Omega)) sum_{k,G1} [f(e_{k+G1}) - f(e_{k+q+G1+G})] / (w + e_{k+G1} - e_{k+q+G1+G} + i eta)
       with e_p = |p|^2/2 and G1 running over the plane waves among the lowest nbands at k
       whose partner k+q+G1+G is among the lowest nbands at k+q.
+  discrete_lindhard_dw: its frequency derivative, the same sum of
+      -[f(e_{k+G1}) - f(e_{k+q+G1+G})] / (w + e_{k+G1} - e_{k+q+G1+G} + i eta)^2.
   continuum_lindhard: the finite-temperature Lindhard function at z = w + i eta,
       chi0(q,z) = 1/(2 pi^2 q) int_0^inf dk k f(k^2/2) [ln(z - q^2/2 + kq) - ln(z - q^2/2 - kq)
                                                       - ln(z + q^2/2 + kq) + ln(z + q^2/2 - kq)]
@@ -89,8 +91,9 @@ def lowest_planewaves(lattice, k, ecut, nbands):
     return b[order[:nbands]], e[order[:nbands]], nxt
 
 
-def discrete_lindhard(lattice, kpts, kqpts, ecut, nbands, G, mu, T, freqs, eta):
-    """Zero-potential chi0_GG at the frequencies, by direct plane-wave enumeration."""
+def discrete_lindhard(lattice, kpts, kqpts, ecut, nbands, G, mu, T, freqs, eta, dw=False):
+    """Zero-potential chi0_GG at the frequencies, by direct plane-wave enumeration (dw: its
+    derivative with respect to w, term by term)."""
     om = crystal.volume(lattice)
     nk = len(kpts)
     out = np.zeros(len(freqs), dtype=np.complex128)
@@ -104,5 +107,6 @@ def discrete_lindhard(lattice, kpts, kqpts, ecut, nbands, G, mu, T, freqs, eta):
                 continue
             f1 = expit(-(e1[a] - mu) / T)
             f2 = expit(-(e2[j] - mu) / T)
-            out += (f1 - f2) / (freqs + e1[a] - e2[j] + 1j * eta)
+            den = freqs + e1[a] - e2[j] + 1j * eta
+            out += -(f1 - f2) / den ** 2 if dw else (f1 - f2) / den
     return 2.0 * out / (nk * om)

@@ -36,11 +36,13 @@ def run_q(wl, iq: int, keep_chi0: bool = False, freqs_subset=None) -> dict:
     if freqs_subset is not None:
         return out
     n = response.density(wl)
-    S = response.dsf(chiG0[:, 0], wl.omega, hcol, wl.T, n)
-    S0 = response.s_zero(chiG0[:, 0], hcol, wl.T, n)
+    deta = response.chi0_eta_derivative(rho_flat, delta, df, 0.0, wl.eta, wl.nk, om)
+    S0 = response.s_zero(response.chi00_derivative(chi0[hcol], deta, K), wl.T, n)
+    S = response.dsf(chiG0[:, 0], wl.omega, S0, wl.T, n)
     wp, Sp = response.positive_branch(S, wl.omega, S0)
     tau = response.tau_grid(wl.T, wl.ntau)
     out.update({"S": S, "S0": S0, "wp": wp, "Sp": Sp, "tau": tau,
+                "dchi00_deta0": response.chi00_derivative(chi0[hcol], deta, K),
                 "F": response.itcf_fold(wp, Sp, tau, wl.T),
                 "metrics": response.itcf_metrics(wp, Sp, wl.T, n)})
     return out

@@ -12,8 +12,12 @@ Definitions (Hartree atomic units, spin factor 2, Omega = cell volume, N_k = k p
   chi = (1 - chi0 K)^{-1} chi0; only chi_{G,0} is solved for.
   S(q,w) = -Im chi_00(q,w) / (pi n (1 - e^{-beta w}))          fluctuation-dissipation, Eq. 8
            (hbar = 1; the 1/pi makes int w S dw = q^2/2, the f-sum rule)
-  S(q,0) = -Im chi_00(q,h) / (pi n beta h), h = 1e-4 Ha    (the w -> 0 limit; Im chi_00 is odd,
-           so the step costs O((h/eta)^2); a smaller h amplifies the cancellation in Im chi(h))
+  S(q,0) = lim_{w->0} of Eq. 8 = -(T/(pi n)) d Im chi_00/dw at w = 0 (Im chi_00(0) = 0 on the
+           time-reversal-symmetric pair meshes).  chi0 depends on w and eta only through
+           w + i eta and K on neither, so chi_00 is a function of w + i eta and
+           d chi_00/dw = -i d chi_00/d eta:  S(q,0) = (T/(pi n)) Re d chi_00/d eta (w = 0), with
+           d chi_00/d eta from the Dyson chain rule d x = M^{-1} (d chi0/d eta)(K x + e_0),
+           d chi0/d eta = (2/(N_k Omega)) sum_p rho_p(G) rho_p*(G') (-i df_p)/(w + Delta_p + i eta)^2
   F(q,tau) = int dw S(q,w) e^{-tau w}                        two-sided Laplace transform, Eq. 1
            = int_0^wmax S(w) [e^{-tau w} + e^{-(beta-tau) w}] dw   using detailed balance
              S(-w) = e^{-beta w} S(w) (FOLD mode, trapezoid over the w >= 0 samples)
@@ -23,7 +27,8 @@ Definitions (Hartree atomic units, spin factor 2, Omega = cell volume, N_k = k p
   int_0^beta [e^{-tau w} + e^{-(beta-tau) w}] dtau = 2 (1 - e^{-beta w}) / w.
 
 Pinned by (tests/test_oracle_response.py): the discrete and continuum Lindhard functions at
-zero potential, the exact discrete f-sum rule, detailed balance to rounding on time-reversal
+zero potential, S(q,0) against the analytic w-derivative of the discrete Lindhard sum and
+against the limit of S(q,w) (Richardson extrapolation in w), the exact discrete f-sum rule, detailed balance to rounding on time-reversal
 symmetric meshes, the analytic Laplace transform of a model spectrum, the scalar and K = 0
 limits of Dyson, the Dyson residual, pair-density orthonormality and completeness, and a
 brute-force chi0 built by real-space FFT products on a tiny cell.
@@ -36,7 +41,6 @@ import numpy as np
 
 from . import crystal, occupations, xc
 
-H_ZERO = 1e-4     # Ha; frequency used for the w -> 0 limit of S
 DEGEN_TOL = 1e-6  # Ha; eigenvalues this close to the last kept band form one multiplet
 EXTRA_BANDS = 8   # eigenpairs computed beyond nbands to see a multiplet split by the cut
 
@@ -152,14 +156,13 @@ def pair_weights(gs):
 
 
 def internal_frequencies(omega: np.ndarray):
-    """The frequencies chi is evaluated at: the grid, with an exact 0 replaced by H_ZERO,
-    plus H_ZERO appended when 0 is not on the grid.  Returns (freqs, index of the h column)."""
+    """The frequencies chi is evaluated at: the grid, plus w = 0 appended when 0 is not on it
+    (S(q,0) is needed by the Laplace transform of Eq. 1).  Returns (freqs, index of w = 0)."""
     w = np.array(omega, dtype=np.float64)
     zero = np.where(w == 0.0)[0]
     if len(zero):
-        w[zero[0]] = H_ZERO
         return w, int(zero[0])
-    return np.concatenate([w, [H_ZERO]]), len(w)
+    return np.concatenate([w, [0.0]]), len(w)
 
 
 def chi0(rho_flat, delta, df, freqs, eta, nk, omega_cell) -> np.ndarray:
@@ -170,6 +173,25 @@ def chi0(rho_flat, delta, df, freqs, eta, nk, omega_cell) -> np.ndarray:
         wt = df / (w + delta + 1j * eta)
         out[iw] = pref * ((rho_flat * wt[:, None]).T @ rho_flat.conj())
     return out
+
+
+def chi0_eta_derivative(rho_flat, delta, df, w, eta, nk, omega_cell) -> np.ndarray:
+    """d chi0[G, G']/d eta at frequency w:
+    (2/(N_k Omega)) sum_p rho_p(G) rho_p*(G') (-i df_p) / (w + Delta_p + i eta)^2."""
+    pref = 2.0 / (nk * omega_cell)
+    wt = -1j * df / (w + delta + 1j * eta) ** 2
+    return pref * ((rho_flat * wt[:, None]).T @ rho_flat.conj())
+
+
+def chi00_derivative(chi0w: np.ndarray, dchi0w: np.ndarray, K: np.ndarray) -> complex:
+    """d chi_00 at one frequency for a change d chi0 at fixed K (Dyson chain rule):
+    M = 1 - chi0 K, x = M^{-1} chi0_{:,0}, d x = M^{-1} d chi0 (K x + e_0); returns d x_0."""
+    N = len(K)
+    M = np.eye(N) - chi0w * K[None, :]
+    x = solve_gauss(M[None], chi0w[None, :, 0].copy())[0]
+    v = K * x
+    v[0] += 1.0
+    return complex(solve_gauss(M[None], (dchi0w @ v)[None])[0][0])
 
 
 def kernel_diag(wl, q, gset) -> np.ndarray:
@@ -222,20 +244,21 @@ def dyson_column0(chi0w: np.ndarray, K: np.ndarray) -> np.ndarray:
     return solve_gauss(M, chi0w[:, :, 0].copy())
 
 
-def dsf(chi00_int: np.ndarray, omega: np.ndarray, hcol: int, T: float, n: float) -> np.ndarray:
-    """S on the caller's grid from chi_00 at the internal frequencies (Eq. 8)."""
+def dsf(chi00_int: np.ndarray, omega: np.ndarray, S0: float, T: float, n: float) -> np.ndarray:
+    """S on the caller's grid from chi_00 at the internal frequencies (Eq. 8); S0 at w = 0."""
     beta = 1.0 / T
     S = np.zeros(len(omega))
     for j, w in enumerate(omega):
         if w == 0.0:
-            S[j] = -chi00_int[hcol].imag / (math.pi * n * beta * H_ZERO)
+            S[j] = S0
         else:
             S[j] = -chi00_int[j].imag / (math.pi * n * (-math.expm1(-beta * w)))
     return S
 
 
-def s_zero(chi00_int, hcol, T, n) -> float:
-    return -chi00_int[hcol].imag / (math.pi * n * H_ZERO / T)
+def s_zero(dchi00_deta0: complex, T: float, n: float) -> float:
+    """S(q,0) = (T/(pi n)) Re d chi_00/d eta at w = 0 (the w -> 0 limit of Eq. 8)."""
+    return T * dchi00_deta0.real / (math.pi * n)
 
 
 def positive_branch(S, omega, S0):

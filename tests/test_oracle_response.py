@@ -43,6 +43,42 @@ def test_chi0_zero_potential_equals_discrete_lindhard():
     assert np.abs(off).max() < 1e-12 * scale
 
 
+def test_s_zero_at_zero_potential_is_the_lindhard_derivative():
+    """At V = 0, chi0 is diagonal (the discrete Lindhard sum L_G), so chi_00 = L_0/(1 - L_0 K_0)
+    and d chi_00/dw = L_0'/(1 - L_0 K_0)^2 with L_0' the term-by-term w-derivative of the
+    plane-wave sum: S(q,0) = -(T/(pi n)) Im d chi_00/dw at w = 0 (the limit of Eq. 8)."""
+    wl = _free_tiny()
+    r = pipeline.run_q(wl, 0)
+    kp, kqp = crystal.pair_meshes(wl.lattice, wl.kmesh, wl.q[0], wl.kscheme)
+    z = np.zeros(3, dtype=int)
+    L = lindhard.discrete_lindhard(wl.lattice, kp, kqp, wl.ecut, wl.nbands, z, r["mu"], wl.T,
+                                   np.array([0.0]), wl.eta)[0]
+    dL = lindhard.discrete_lindhard(wl.lattice, kp, kqp, wl.ecut, wl.nbands, z, r["mu"], wl.T,
+                                    np.array([0.0]), wl.eta, dw=True)[0]
+    K0 = r["K"][0]
+    n = response.density(wl)
+    ref = -(wl.T / (math.pi * n)) * (dL / (1.0 - L * K0) ** 2).imag
+    assert abs(r["S0"] - ref) < 1e-12 * abs(ref)
+    assert abs(r["chi00"][r["hcol"]].imag) < 1e-13 * abs(r["chi00"][r["hcol"]])
+
+
+@pytest.mark.parametrize("wmin_ev", [-30.0, 0.0])
+def test_s_zero_is_the_limit_of_s(wmin_ev):
+    """S(q,0) against the w -> 0 limit of Eq. 8 taken numerically: Im chi_00 is odd in w, so
+    Im chi_00(h)/h = a + b h^2 + ..., and the Richardson combination (4 g(h) - g(2h))/3 of
+    g(h) = Im chi_00(h)/h leaves O((h/eta)^4) (4e-10 here at h = 1e-4 Ha; it falls 16x per halving
+    of h down to the rounding floor near 5e-11).  Covers 0 on and off the caller's grid."""
+    wl = _db_workload().replace(omega=np.linspace(W.ev(wmin_ev), W.ev(40.0), 33))
+    r = pipeline.run_q(wl, 0)
+    h = 1e-4
+    probe = pipeline.run_q(wl.replace(omega=np.array([h, 2 * h])), 0)
+    g1, g2 = probe["chi00"][0].imag / h, probe["chi00"][1].imag / (2 * h)
+    n = response.density(wl)
+    ref = -(wl.T / (math.pi * n)) * (4 * g1 - g2) / 3
+    assert abs(r["S0"] - ref) < 2e-9 * abs(ref)
+    assert r["S0"] > 0
+
+
 def test_discrete_lindhard_converges_to_continuum():
     lat = W.fcc_primitive(W.AL_A)
     T, eta = W.ev(5.0), W.ev(0.5)
