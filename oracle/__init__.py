@@ -17,6 +17,9 @@ or fusion beyond what the definition states:
   response.py   pair densities, Adler-Wiser chi0, Dyson, S(q,w) (Eq. 8),
                 F(q,tau) (Eq. 1 with detailed balance), F-tilde (Eq. 2), metrics
   attenuation.py Savitzky-Golay / AICc / constraints filter (Sec. 3, Eqs. 5-7)
+  etascan.py    the eta-convergence test in the imaginary-time domain (Sec. 2)
+  dielectric.py chi, 1/eps, eps and sigma from a DSF (Kramers-Kronig, Eqs. 10-11)
+  kubo.py       the Kubo-Greenwood route to the eta test and the filtered conductivity (App. A.3)
   lindhard.py   continuum finite-temperature Lindhard function (pins only)
   adjoint.py    forward-mode tangents of S(q,w) and F(q,tau) for the gradient pins
   pipeline.py   runs the steps above for one workload
