@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--autotune", action="store_true", help="let the library time its kernel variants")
     ap.add_argument("--variant", type=int, default=-1, help="force a tensor-kernel variant (0, 1)")
     ap.add_argument("--unit-stages", type=int, default=0, help="force the stages per work unit")
+    ap.add_argument("--fine-accum", action="store_true",
+                    help="flush the FP32 tensor-core accumulators every 32 stages instead of 64")
+    ap.add_argument("--workload", default="al1", choices=["al1", "al4_adjoint", "al64_slice", "al32_k1"],
+                    help="al1: the timed 8-q workload (default); the others measure the other "
+                         "configurations once and print one JSON line each")
     return ap.parse_args()
 
 
@@ -187,7 +192,8 @@ def run_ours(args, world, rank, local, pg):
     ctx = binding.Context(wl, args.precision, device=local)
     setup_s = time.time() - t0
     if args.precision != "fp64":
-        ctx.set_tuning(auto=args.autotune, variant=args.variant, unit_stages=args.unit_stages)
+        ctx.set_tuning(auto=args.autotune, variant=args.variant, unit_stages=args.unit_stages,
+                       fine_accum=args.fine_accum)
     dev = torch.device("cuda", local)
     ntau = wl.ntau
     tau = torch.linspace(0.0, 0.5 / wl.T, ntau, dtype=torch.float64, device=dev)
@@ -365,14 +371,14 @@ def run_e2e(ctx, wl, args, cmac_step, pg, world):
 
 
 def run_extras(args, ctx_main, wl):
-    """FP64 form on a slice (1 q, 16 frequencies) beside the split form, and the split form's
-    error against the FP64 form on the full 1-atom 8^3 workload."""
+    """FP64 form on a slice (1 q, 64 frequencies) beside the split form, and the split form's
+    error against the FP64 form at the timed workload's shape on a 4^3 k mesh."""
     from paper_2510_01875_gb300 import binding
     from paper_2510_01875_gb300 import workloads as W
     out = {}
-    # slice: q[0], 16 frequencies around the plasmon
+    # slice: q[0], 64 frequencies from 15 eV (two whole 32-frequency tiles of the FP64 kernel)
     j0 = int(np.searchsorted(wl.omega, W.ev(15.0)))
-    sl = wl.replace(q=wl.q[:1], nG=wl.nG[:1], omega=wl.omega[j0:j0 + 16])
+    sl = wl.replace(q=wl.q[:1], nG=wl.nG[:1], omega=wl.omega[j0:j0 + 64])
     forms = {}
     for prec in ("fp64", args.precision if args.precision != "fp64" else "fp16x3"):
         c = binding.Context(sl, prec)
@@ -385,37 +391,132 @@ def run_extras(args, ctx_main, wl):
     fp = forms["fp64"]
     sp = forms[[k for k in forms if k != "fp64"][0]]
     err = float(np.abs(sp["chi0"] - fp["chi0"]).max() / np.abs(fp["chi0"]).max())
+    peak64 = fp64_peak()
+    dfma = binding.measure_fp64(0)
+    tf64 = 4.0 * fp["cmac"] / (fp["ms"] / 1e3) / 1e12
     out["fp64_form"] = {"value": fp["cmac"] / (fp["ms"] / 1e3), "unit": UNIT,
-                        "chi0_tflops": 4.0 * fp["cmac"] / (fp["ms"] / 1e3) / 1e12,
-                        "sample": f"1 q, 16 frequencies (15-17.5 eV), all {ctx_main.nk * ctx_main.nb ** 2:.3g} "
-                                  "pairs; rate is K-dominated so it extrapolates linearly to the "
-                                  "full workload",
+                        "chi0_tflops": tf64,
+                        "roofline": {"bound": "fp64", "achieved": tf64, "peak": dfma,
+                                     "unit": "TFLOP/s", "frac": tf64 / dfma,
+                                     "peak_source": "measured: FP64 FMA loop on every SM (the pipe "
+                                                    "of the SIMT FP64 kernel), lrtddft_measure_fp64"},
+                        "dgemm_peak": {"tflops": peak64["tflops"], "frac": tf64 / peak64["tflops"],
+                                       "how": peak64["how"]},
+                        "sample": f"1 q, 64 frequencies (15-25 eV), all {ctx_main.nk * ctx_main.nb ** 2:.3g} "
+                                  "pairs; the rate is set by the pair sum, so it extrapolates "
+                                  "linearly to the full workload",
                         "split_rate_same_slice": sp["cmac"] / (sp["ms"] / 1e3),
                         "split_vs_fp64_chi0_err": err}
-    # accuracy of the split form against FP64 on the 1-atom 8^3 workload (full S and F)
-    small = W.al1_fcc_k8_b24()
+    # accuracy of the split form against the FP64 form at the shape of the timed workload
+    # (same cell, 120 bands, 59 G, 1024 frequencies, T, eta), smallest and largest |q|, on a
+    # 4^3 k mesh (the FP64 form is about 37 s per q there)
+    acc = wl.replace(kmesh=(4, 4, 4), q=wl.q[[0, wl.nq - 1]], nG=wl.nG[[0, wl.nq - 1]],
+                     name=wl.name.replace("k12", "k4").replace(f"q{wl.nq}", "q2"))
     res = {}
     for prec in ("fp64", args.precision if args.precision != "fp64" else "fp16x3"):
-        c = binding.Context(small, prec)
+        c = binding.Context(acc, prec)
         c.chi0_assemble()
         c.dyson_solve()
         S = c.dsf()
-        F, m = c.itcf(np.linspace(0.0, 0.5 / small.T, small.ntau))
-        res[prec] = (c.get_chi0(0), S, F)
+        F, m = c.itcf(np.linspace(0.0, 0.5 / acc.T, acc.ntau))
+        res[prec] = ([c.get_chi0(i) for i in range(acc.nq)], S, F)
         c.close()
     a = res["fp64"]
     b = res[[k for k in res if k != "fp64"][0]]
-    peaks = [j for j in range(1, small.nw - 1) if a[1][0, j] > a[1][0, j - 1] and a[1][0, j] >= a[1][0, j + 1]
-             and a[1][0, j] > 0.1 * a[1][0].max()]
+    per_q = []
+    for i in range(acc.nq):
+        Sa, Sb = a[1][i], b[1][i]
+        peaks = [j for j in range(1, acc.nw - 1) if Sa[j] > Sa[j - 1] and Sa[j] >= Sa[j + 1]
+                 and Sa[j] > 0.1 * Sa.max()]
+        per_q.append({
+            "q_inv_bohr": float(np.linalg.norm(acc.q[i])),
+            "chi0_maxnorm_rel": float(np.abs(b[0][i] - a[0][i]).max() / np.abs(a[0][i]).max()),
+            "S_maxnorm_rel": float(np.abs(Sb - Sa).max() / np.abs(Sa).max()),
+            "S_peak_rel": float(max(abs(Sb[j] / Sa[j] - 1) for j in peaks)) if peaks else None,
+            "F_pointwise_rel": float(np.abs(b[2][i] / a[2][i] - 1).max())})
     out["split_accuracy"] = {
-        "workload": small.name,
-        "chi0_maxnorm_rel": float(np.abs(b[0] - a[0]).max() / np.abs(a[0]).max()),
-        "S_maxnorm_rel": float(np.abs(b[1] - a[1]).max() / np.abs(a[1]).max()),
-        "S_peak_rel": float(max(abs(b[1][0, j] / a[1][0, j] - 1) for j in peaks)) if peaks else None,
-        "F_pointwise_rel": float(np.abs(b[2] / a[2] - 1).max()),
+        "workload": acc.name, "against": "the library's FP64 form (parity-tested against the oracle)",
+        "per_q": per_q,
+        "F_pointwise_rel": max(x["F_pointwise_rel"] for x in per_q),
+        "S_peak_rel": max(x["S_peak_rel"] or 0.0 for x in per_q),
         "bounds": {"F": 1e-5, "S_peaks": 1e-4}}
+    out["eta_scan"] = eta_scan_extra(args, wl)
     out["cpu_baseline"] = cpu_baseline(wl)
     return out
+
+
+def eta_scan_extra(args, wl, n_eta=8, tol=5e-3):
+    """The eta-convergence test (Sec. 2) on q[0] of the timed workload: n_eta broadenings in one
+    assembly (the (eta, w) pairs as columns of one contraction launch) against n_eta separate
+    single-eta passes, both through Dyson, S, F and the metrics; device-timed with CUDA events
+    on the legacy stream the library uses."""
+    import torch
+    from paper_2510_01875_gb300 import binding
+    from paper_2510_01875_gb300 import workloads as W
+    one = wl.replace(q=wl.q[:1], nG=wl.nG[:1], name=wl.name.replace(f"q{wl.nq}", "q1"))
+    etas = [W.ev(x) for x in np.linspace(0.1, 0.8, n_eta)]
+    tau = np.linspace(0.0, 0.5 / one.T, one.ntau)
+    prec = args.precision
+    c = binding.Context(one, prec)
+
+    def timed(fn):
+        fn()                              # warm-up (plans, buffers)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def batched():
+        c.chi0_assemble()
+        c.dyson_solve()
+        return c.eta_scan(tau, tol)
+
+    def separate():
+        ms = []
+        for e in etas:
+            c.set_params(one.T, e)
+            c.chi0_assemble()
+            c.dyson_solve()
+            ms.append(c.itcf(tau)[1][0])
+        return np.array(ms)
+
+    c.set_eta_list(etas)
+    t_b, (_, m, ref) = timed(batched)
+    t_s, m_sep = timed(separate)
+    c.close()
+    return {"workload": one.name, "precision": prec, "etas_eV": [float(x) for x in np.linspace(0.1, 0.8, n_eta)],
+            "one_assembly_ms": t_b, "separate_ms": t_s, "speedup": t_s / t_b,
+            "Ftilde_half_beta": [float(x) for x in m[0, :, 2]],
+            "int_Ftilde": [float(x) for x in m[0, :, 3]],
+            "metrics_max_rel_diff_vs_separate": float(np.abs(m[0] / m_sep - 1).max()),
+            "tol": tol, "reference_eta_index": int(ref[0])}
+
+
+def fp64_peak():
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul in float64, 2 N^3 flops per
+    product), best of 5 after a warm-up, CUDA events; the same method as the measured bf16
+    peak.  The FP64 chi0 kernel is SIMT FP64 (4 flops per complex MAC of the Hermitian split)."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return {"tflops": 2.0 * n ** 3 / best / 1e12,
+            "how": f"measured: torch.matmul float64 {n}^3 (cuBLAS DGEMM), best of 5, CUDA events"}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -498,8 +599,135 @@ def run_reference(args, world, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- other configurations
+def _split_vs_fp64(wl, prec, tau):
+    """Split form against the FP64 form on the same workload: chi0 (max norm), S (max norm and
+    peaks), F (pointwise)."""
+    from paper_2510_01875_gb300 import binding
+    res = {}
+    for p in ("fp64", prec):
+        c = binding.Context(wl, p)
+        c.chi0_assemble()
+        c.dyson_solve()
+        S = c.dsf()
+        F, _ = c.itcf(tau)
+        res[p] = ([c.get_chi0(i) for i in range(wl.nq)], S, F)
+        c.close()
+    a, b = res["fp64"], res[prec]
+    out = {"chi0_maxnorm_rel": max(float(np.abs(b[0][i] - a[0][i]).max() / np.abs(a[0][i]).max())
+                                   for i in range(wl.nq)),
+           "S_maxnorm_rel": float(max(np.abs(b[1][i] - a[1][i]).max() / np.abs(a[1][i]).max()
+                                      for i in range(wl.nq))),
+           "F_pointwise_rel": float(np.abs(b[2] / a[2] - 1).max())}
+    pk = []
+    for i in range(wl.nq):
+        Sa = a[1][i]
+        pk += [abs(b[1][i][j] / Sa[j] - 1) for j in range(1, wl.nw - 1)
+               if Sa[j] > Sa[j - 1] and Sa[j] >= Sa[j + 1] and Sa[j] > 0.1 * Sa.max()]
+    out["S_peak_rel"] = float(max(pk)) if pk else None
+    return out
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def run_workload(args):
+    """One measurement of another configuration, one JSON line: setup time, the response path
+    timed with CUDA events (after one untimed pass), the chi0 rate, and accuracy against the
+    FP64 form on a reduced case of the same shape."""
+    from paper_2510_01875_gb300 import binding, build
+    from paper_2510_01875_gb300 import workloads as W
+    build.build()
+    binding.load()
+    prec = args.precision if args.precision != "fp64" else "fp16x3"
+    line = {"workload_kind": args.workload, "precision": prec}
+    if args.workload == "al4_adjoint":
+        wl = W.al4_cubic_k6_b200()
+    elif args.workload == "al64_slice":
+        full = W.al64_k2_b1600()
+        wl = full.replace(q=full.q[:1], nG=full.nG[:1], name=full.name.replace("q48", "q1of48"))
+    else:
+        full = W.al32_k4_b400()
+        wl = full.replace(kmesh=(1, 1, 1), name=full.name.replace("k4", "k1"))
+    tau = np.linspace(0.0, 0.5 / wl.T, wl.ntau)
+    t0 = time.time()
+    c = binding.Context(wl, prec)
+    line["setup_s"] = time.time() - t0
+    line["workload"] = wl.name
+    line.update({"nq": wl.nq, "nk": c.nk, "nbands": c.nb, "nG": [int(x) for x in wl.nG][:48],
+                 "nw": wl.nw, "np_per_q": c.nk * c.nb * c.nb})
+
+    def forward():
+        c.chi0_assemble()
+        c.dyson_solve()
+        return c.itcf(tau)
+
+    forward()
+    c.profile(True)
+    ms, _ = _timed(forward)
+    prof = c.profile_read()
+    cmac = sum(float(g) ** 2 for g in wl.nG) * wl.nw * c.nk * c.nb * c.nb
+    line.update({"forward_ms": ms, "chi0_ms": prof["chi0_ms"], "chi0_launches": prof["chi0_launches"],
+                 "pair_density_ms": prof["rho_ms"], "cmac_per_s": cmac / (ms / 1e3),
+                 "chi0_tflops": 12.0 * cmac / (prof["chi0_ms"] / 1e3) / 1e12})
+    if args.workload == "al4_adjoint":
+        gms, (dS, dF) = _timed(lambda: c.jacobian(tau))
+        line["gradient_ms"] = gms
+        line["gradient"] = "dF(q, tau)/d(T, eta, A, B, C), 16 q x 64 tau, hand-written adjoint"
+    else:
+        ams, _ = _timed(lambda: c.attenuate(binding.atten_params()))
+        line["attenuation_ms"] = ams
+    c.close()
+    # accuracy on a reduced case of the same shape
+    if args.workload == "al4_adjoint":
+        red = wl.replace(kmesh=(2, 2, 2), q=wl.q[[0, wl.nq - 1]], nG=wl.nG[[0, wl.nq - 1]],
+                         name=wl.name.replace("k6", "k2"))
+        acc = _split_vs_fp64(red, prec, tau)
+        jac = {}
+        for p in ("fp64", prec):
+            cc = binding.Context(red, p)
+            cc.chi0_assemble()
+            cc.dyson_solve()
+            jac[p] = cc.jacobian(tau)[1]
+            cc.close()
+        acc["gradient_maxnorm_rel_per_theta"] = [
+            float(np.abs(jac[prec][..., j] - jac["fp64"][..., j]).max() / np.abs(jac["fp64"][..., j]).max())
+            for j in range(5)]
+        acc["reduced_case"] = red.name + " (against the FP64 form and the FP64 adjoint)"
+    elif args.workload == "al64_slice":
+        j0 = int(np.searchsorted(wl.omega, 0.0))
+        red = wl.replace(omega=wl.omega[j0:j0 + 4], name=wl.name + "_4w")
+        chi = {}
+        for p in ("fp64", prec):
+            cc = binding.Context(red, p)
+            cc.chi0_assemble()
+            chi[p] = cc.get_chi0(0)
+            cc.close()
+        acc = {"chi0_maxnorm_rel": float(np.abs(chi[prec] - chi["fp64"]).max() / np.abs(chi["fp64"]).max()),
+               "reduced_case": red.name + " (4 frequencies, all pairs, against the FP64 form)"}
+    else:
+        i = int(np.argmin(wl.nG))
+        red = wl.replace(q=wl.q[i:i + 1], nG=wl.nG[i:i + 1], name=wl.name + f"_q{i}")
+        acc = _split_vs_fp64(red, prec, tau)
+        acc["reduced_case"] = red.name + " (against the FP64 form)"
+    line["accuracy"] = acc
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload != "al1":
+        run_workload(args)
+        return
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank, pg)

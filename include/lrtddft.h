@@ -65,8 +65,8 @@ enum { LRT_KERNEL_RPA = 0, LRT_KERNEL_RPA_ALDA = 1, LRT_KERNEL_FXC_MODEL = 2 };
 /* Precision of the pair densities and the chi0 contraction (the Dyson solve, S and F are
  * always FP64):
  * FP64: FP64 products and sums;  FP16X3 / BF16X3: pair densities in FP32 (tensor cores with a
- * fixed-grid FP16 split whose high products are summed exactly, N_b <= 128; else the FP32
- * SIMT kernel), and each contraction operand split into a high and a low 16-bit part, three
+ * fixed-grid FP16 split whose high products are summed exactly, 128-band blocks), and each
+ * contraction operand split into a high and a low 16-bit part, three
  * tensor-core products (hi*hi + hi*lo + lo*hi) accumulated in FP32 and flushed into FP64
  * partial sums.  FP16X3 is the FP32-emulating form (hi + lo carry about 22 bits). */
 enum { LRT_PREC_FP64 = 0, LRT_PREC_FP16X3 = 1, LRT_PREC_BF16X3 = 2 };
@@ -137,12 +137,13 @@ const char* lrtddft_last_error(void);
 
 /* Sizes of a context: out[0..7] = nq, nw, nk, nb (bands carried per k point: nbands plus the
  * members of any degenerate multiplet split by the band cut), max nG, plane waves (padded), number of
- * internal frequencies (nw plus the w -> 0 column when 0 is not on the grid), precision. */
+ * internal frequencies (nw plus a w = 0 column when 0 is not on the grid), precision. */
 lrt_status lrtddft_query(const lrt_ctx* ctx, int64_t out[8]);
 
 /* chi0 for q in [q_begin, q_end): pair densities (G-space correlation of the orbitals) and
- * the Adler-Wiser contraction at every internal frequency, kept on the device.  Enqueued on
- * `stream` (cudaStream_t; NULL = legacy default stream). */
+ * the Adler-Wiser contraction at every internal frequency, kept on the device, and
+ * d chi_00/d eta at w = 0 (for S(q,0)).  Enqueued on `stream` (cudaStream_t; NULL = legacy
+ * default stream). */
 lrt_status lrtddft_chi0_assemble(lrt_ctx* ctx, int q_begin, int q_end, void* stream);
 
 /* Dyson for q in [q_begin, q_end): solves (1 - chi0 K) x = chi0_{:,0} by LU with partial
@@ -150,9 +151,10 @@ lrt_status lrtddft_chi0_assemble(lrt_ctx* ctx, int q_begin, int q_end, void* str
  * A zero pivot makes a later synchronising call return LRT_ESINGULAR. */
 lrt_status lrtddft_dyson_solve(lrt_ctx* ctx, int q_begin, int q_end, void* stream);
 
-/* S(q,w) (Eq. 8) on the caller's grid: S [nq][nw].  At w = 0 the limit
- * -Im chi_00(h)/(pi n h / T), h = 1e-4 Ha, is used (Im chi_00 is odd in w, so the step
- * costs O((h/eta)^2)).  Requires dyson_solve for every q. */
+/* S(q,w) (Eq. 8) on the caller's grid: S [nq][nw].  At w = 0 the exact limit of Eq. 8 is
+ * used: S(q,0) = -(T/(pi n)) d Im chi_00/dw = (T/(pi n)) Re d chi_00/d eta at w = 0 (chi_00 is
+ * analytic in w + i eta), with d chi_00/d eta from the Dyson chain rule and a projection of
+ * the pair densities computed by chi0_assemble.  Requires dyson_solve for every q. */
 lrt_status lrtddft_dsf(lrt_ctx* ctx, double* S);
 lrt_status lrtddft_dsf_device(lrt_ctx* ctx, double* S_dev, void* stream);
 
@@ -179,11 +181,13 @@ lrt_status lrtddft_itcf_laplace_device(lrt_ctx* ctx, int ntau, const double* tau
  *                             then differ from the defaults at the rounding of the split form);
  *          LRT_TUNE_SINGLE_Q  one launch per q;
  *          LRT_TUNE_PAIR_SIMT pair densities on the FP32 SIMT kernel instead of the tensor
- *                             cores (which need at most 128 bands; above that the SIMT kernel
- *                             runs anyway).
+ *                             cores;
+ *          LRT_TUNE_FINE_ACCUM flush the FP32 tensor-core accumulators into the FP64 sums every
+ *                             32 stages (1024 pairs) instead of 64: the FP32 accumulation
+ *                             error, which grows with the period, halves.
  *   variant: -1 (tuned or default 0), 0 or 1;  unit_stages: 0 (tuned or default 4096) or a
  *   positive multiple of 64.  LRT_EINVAL otherwise.  Invalidates a captured graph. */
-enum { LRT_TUNE_AUTO = 1, LRT_TUNE_SINGLE_Q = 2, LRT_TUNE_PAIR_SIMT = 4 };
+enum { LRT_TUNE_AUTO = 1, LRT_TUNE_SINGLE_Q = 2, LRT_TUNE_PAIR_SIMT = 4, LRT_TUNE_FINE_ACCUM = 8 };
 lrt_status lrtddft_set_tuning(lrt_ctx* ctx, int flags, int variant, int unit_stages);
 /* The variant and unit size used by the last tensor-core launch (-1 and 0 before any). */
 lrt_status lrtddft_get_tuning(lrt_ctx* ctx, int* variant, int* unit_stages);
@@ -198,6 +202,45 @@ lrt_status lrtddft_get_tuning(lrt_ctx* ctx, int* variant, int* unit_stages);
 lrt_status lrtddft_graph_capture(lrt_ctx* ctx, int ntau, const double* tau_dev, int mode,
                                  double* S_dev, double* F_dev, double* metrics_dev);
 lrt_status lrtddft_graph_launch(lrt_ctx* ctx, void* stream);
+
+/* ---- The eta-convergence test in the imaginary-time domain (Sec. 2, Eqs. 1-2).
+ * An eta list makes every later chi0_assemble compute chi0 for all of its broadenings from one
+ * pass of pair densities: the tensor-core contraction takes the (eta, w) pairs as the columns
+ * of one launch (the FP64 form runs one contraction per eta); dyson_solve then solves every
+ * (eta, w), and S, F and the metrics come as rows (q, eta), q-major:
+ *   dsf S [nq][n_eta][nw],  itcf_laplace F [nq][n_eta][ntau], metrics [nq][n_eta][5],
+ *   attenuate S_p [nq][n_eta][nw] and report [nq][n_eta],
+ *   get_chi0 [n_eta][nw_int][nG][nG],  get_chi_col0 [n_eta][nw_int][nG]
+ * (with one eta these are the shapes given elsewhere).  The adjoint calls (jacobian, the vjps)
+ * take a single eta and return LRT_EUNSUPPORTED otherwise; set_params returns to the single
+ * eta it is given. */
+
+/* eta [n_eta] strictly increasing broadenings, Ha (> 0), 1 <= n_eta <= 64.  Drops chi0 and chi
+ * (chi0_assemble and dyson_solve must run again) and invalidates a captured graph.  LRT_EINVAL
+ * for a bad list. */
+lrt_status lrtddft_set_eta_list(lrt_ctx* ctx, int n_eta, const double* eta);
+/* The current list: *n_eta and, if eta is not NULL, eta [n_eta]. */
+lrt_status lrtddft_get_eta_list(const lrt_ctx* ctx, int* n_eta, double* eta);
+/* The convergence test after dyson_solve on every q: F (FOLD form of Eq. 1) at the caller's
+ * tau and the metrics of itcf_laplace for every (q, eta) (F and metrics may be NULL), and
+ * eta_ref [nq], the index of each q's reference eta: the largest eta_j of the converged range,
+ * read as: for every i <= j both F~(beta/2) and int_0^beta F~ (Eq. 2) lie within
+ * tol |m(eta_0)| of their value m(eta_0) at the smallest eta (the paper's criterion, Sec. 2, is
+ * qualitative; tol sets it).  Host buffers. */
+lrt_status lrtddft_eta_scan(lrt_ctx* ctx, int ntau, const double* tau, double tol, double* F,
+                            double* metrics, int* eta_ref);
+
+/* ---- Dielectric properties from a DSF (Sec. 3, closing relations; App. A.2, Eqs. 10-11).
+ * From S (typically the S_p of lrtddft_attenuate) on the context's grid, rows as lrtddft_dsf
+ * returns them ([nq][n_eta][nw]), at the N samples with w >= 0 (uniformly spaced, N >= 3):
+ *   Im chi = -pi n (1 - e^{-w/T}) S  (Eq. 8),
+ *   Re chi = (2/pi) P int_0^inf w' Im chi(w')/(w'^2 - w^2) dw'  (Kramers-Kronig; the principal
+ *            value by Maclaurin's formula on the samples, Ohta and Ishida 1988, second order in
+ *            the spacing, the range below the first and above the last sample left out),
+ *   1/eps = 1 + (4 pi/|q|^2) chi  (Eq. 10),  eps,  sigma = (i w/(4 pi)) (1 - eps)  (Eq. 11).
+ * out [rows][N][8] = Re chi, Im chi, Re 1/eps, Im 1/eps, Re eps, Im eps, Re sigma, Im sigma.
+ * Host buffers.  LRT_EINVAL for a grid without 3 uniformly spaced samples w >= 0. */
+lrt_status lrtddft_dielectric(lrt_ctx* ctx, const double* S, double* out);
 
 /* ---- Parameters and adjoint.  theta = (T, eta, A, B, C): temperature, broadening and the
  * three parameters of the FXC_MODEL kernel (for RPA and RPA_ALDA the A, B, C components are
@@ -283,6 +326,28 @@ lrt_status lrtddft_attenuate(lrt_ctx* ctx, const lrt_atten_params* params, doubl
 lrt_status lrtddft_attenuate_noalloc(lrt_ctx* ctx, const lrt_atten_params* params, double* Sp,
                                      lrt_atten_report* report);
 
+/* ---- The eta-convergence test from the Kubo-Greenwood conductivity (App. A.3).
+ * Optical limit q -> 0 of the interband response on the k mesh and orbitals of q index 0
+ * (trace/3 of the conductivity tensor), FP64:
+ *   L(w) = (2/(N_k Omega)) sum_{k,n,n'} w_nk w_n'k (f_nk - f_n'k) (|p_nn'|^2/3) / Delta^2
+ *          / (w + Delta + i eta),  p_nn' = <nk|-i grad|n'k>,  Delta = eps_nk - eps_n'k
+ *   sigma_KG = i w L,  eps_KG = 1 + 4 pi i sigma_KG/w (Eq. 11),  chi*_KG = 1/eps_KG - 1
+ *   (Eqs. 10, 12),  S*_KG = -Im chi*_KG / (pi n (1 - e^{-w/T})) (Eq. 13; at w = 0 its exact
+ *   limit), and F*_KG (Eq. 14) by the fold of Eq. 1.
+ * For eta [n_eta] (strictly increasing, Ha; 1..64): sigma [n_eta][nw] complex, S [n_eta][nw],
+ * F [n_eta][ntau] at the caller's tau, metrics [n_eta][5] as itcf_laplace (each may be NULL),
+ * and *eta_ref, the reference eta by the rule of lrtddft_eta_scan with tolerance tol.  Host
+ * buffers.  Needs only the context's ground state. */
+lrt_status lrtddft_kubo_greenwood(lrt_ctx* ctx, int n_eta, const double* eta, int ntau,
+                                  const double* tau, double tol, double* sigma, double* S,
+                                  double* F, double* metrics, int* eta_ref);
+/* After lrtddft_kubo_greenwood: the attenuation (as lrtddft_attenuate) of S*_KG at the reference
+ * eta, Sp [nw] and report [1], and, if out is not NULL, the filtered response at the samples
+ * w >= 0 as lrtddft_dielectric returns it with v(q) chi = chi*: out [N][8] = chi*, 1/eps, eps,
+ * sigma (each re, im).  LRT_ESTATE before a scan. */
+lrt_status lrtddft_kubo_greenwood_attenuate(lrt_ctx* ctx, const lrt_atten_params* params, double* Sp,
+                                            lrt_atten_report* report, double* out);
+
 /* ---- instrumentation ---- */
 
 /* Reset the counters below and turn the CUDA-event timing of the chi0 contraction and
@@ -295,6 +360,11 @@ lrt_status lrtddft_profile(lrt_ctx* ctx, int enable);
  * total ms, out[5] chi0 complex MACs of the timed contractions (N_G^2 N_w N_p summed, with
  * the caller's N_w), out[6..7] reserved (0). */
 lrt_status lrtddft_profile_read(lrt_ctx* ctx, double out[8]);
+
+/* Measured FP64 fused-multiply-add rate of a device's CUDA cores, TFLOP/s (2 flops per FMA):
+ * a loop of independent FMAs on every SM, best of 5 launches timed with CUDA events.  The
+ * roofline of the FP64 chi0 form, which runs on that pipe. */
+lrt_status lrtddft_measure_fp64(int device, double* tflops);
 
 /* ---- test and debug hooks ---- */
 
@@ -332,7 +402,7 @@ lrt_status lrtddft_get_chi0(const lrt_ctx* ctx, int iq, double* chi0);
 lrt_status lrtddft_get_pair_densities(lrt_ctx* ctx, int iq, double* rho);
 /* chi_{G,0} of q index iq: [nw_int][nG] complex.  Requires dyson_solve on iq. */
 lrt_status lrtddft_get_chi_col0(const lrt_ctx* ctx, int iq, double* chi);
-/* Internal frequencies [nw_int] and the index of the w -> 0 column. */
+/* Internal frequencies [nw_int] and the index of the w = 0 column. */
 lrt_status lrtddft_get_frequencies(const lrt_ctx* ctx, double* freqs, int* hcol);
 
 #ifdef __cplusplus

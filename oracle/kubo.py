@@ -14,19 +14,19 @@ from the same orbitals as the rest of the path, trace/3 of the conductivity tens
   sigma_KG(w) = i w L(w)                  (continuity: sigma = i w chi/q^2, so that Eq. 11's
                                            eps = 1 + 4 pi i sigma/w is 1 - (4 pi/q^2) chi0)
   eps_KG(w)   = 1 + 4 pi i sigma_KG(w)/w = 1 - 4 pi L(w)
-  chi*_KG(w)  = v(q) chi_KG(q, w) = 1/eps_KG(w) - 1          (Eq. 10 with v(q) = 4 pi/q^2)
-  S*_KG(w)    = -Im chi*_KG(w) / (pi n (1 - e^{-w/T}))        (Eq. 8, hbar = 1, with the pi of
+  chi*_KG(w)  = v(q) chi_KG(q, w) = 1/eps_KG(w) - 1          (Eqs. 10 and 12, v(q) = 4 pi/q^2)
+  S*_KG(w)    = -Im chi*_KG(w) / (pi n (1 - e^{-w/T}))        (Eq. 13, hbar = 1, with the pi of
                                                                the library's reading)
   S*_KG(0)    = (T/(pi n)) Re d(1/eps_KG)/d eta at w = 0 = (T/(pi n)) Re[4 pi L_eta(0)/eps_KG(0)^2],
                 L_eta = dL/d eta (L depends on w + i eta only, as in the S(q,0) limit)
-  F*_KG       = the detailed-balance fold of Eq. 1 over S*_KG (F* = v(q) F_KG)
+  F*_KG       = the detailed-balance fold of Eq. 1 over S*_KG (Eq. 14, F* = v(q) F_KG)
 After the reference eta is found (etascan.reference_eta), S*_KG at that eta is attenuated
 (attenuation.attenuate) and the filtered chi*, eps and sigma follow from it (dielectric.py with
 v = 1, since chi* already carries v(q)).
 
 Pinned by (tests/test_oracle_kubo.py): L(w) against the Adler-Wiser chi0 of this oracle at small
-q (interband pairs, averaged over three orthogonal q directions), which it must approach
-linearly in |q|; S*_KG(0) against the w -> 0 limit of S*_KG(w) (Richardson); and the algebra of
+q (interband pairs, averaged over three orthogonal q directions), which it approaches as q^2;
+S*_KG(0) against the w -> 0 limit of S*_KG(w) (Richardson); and the algebra of
 Eqs. 10-11 between sigma, eps and chi*.
 """
 from __future__ import annotations

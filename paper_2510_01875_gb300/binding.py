@@ -108,6 +108,15 @@ SIGNATURES = {
     "lrtddft_get_pair_densities": (C.c_int, [_P, C.c_int, _D]),
     "lrtddft_get_chi_col0": (C.c_int, [_P, C.c_int, _D]),
     "lrtddft_get_frequencies": (C.c_int, [_P, _D, C.POINTER(C.c_int)]),
+    "lrtddft_set_eta_list": (C.c_int, [_P, C.c_int, _D]),
+    "lrtddft_get_eta_list": (C.c_int, [_P, C.POINTER(C.c_int), _D]),
+    "lrtddft_eta_scan": (C.c_int, [_P, C.c_int, _D, C.c_double, _D, _D, C.POINTER(C.c_int)]),
+    "lrtddft_dielectric": (C.c_int, [_P, _D, _D]),
+    "lrtddft_measure_fp64": (C.c_int, [C.c_int, _D]),
+    "lrtddft_kubo_greenwood": (C.c_int, [_P, C.c_int, _D, C.c_int, _D, C.c_double, _D, _D, _D, _D,
+                                         C.POINTER(C.c_int)]),
+    "lrtddft_kubo_greenwood_attenuate": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D,
+                                                   C.POINTER(lrt_atten_report), _D]),
 }
 
 _lib = None
@@ -137,6 +146,14 @@ def _check(fn: str, st: int):
     if st != LRT_OK:
         lib = load()
         raise LrtError(fn, lib.lrtddft_status_string(st).decode(), lib.lrtddft_last_error().decode())
+
+
+def measure_fp64(device: int = 0) -> float:
+    """Measured FP64 FMA rate of the device's CUDA cores, TFLOP/s."""
+    lib = load()
+    v = C.c_double()
+    _check("lrtddft_measure_fp64", lib.lrtddft_measure_fp64(device, C.byref(v)))
+    return v.value
 
 
 def atten_params(**kw) -> lrt_atten_params:
@@ -184,7 +201,12 @@ class Context:
         sz = (C.c_int64 * 8)()
         _check("lrtddft_query", lib.lrtddft_query(h, sz))
         self.nq, self.nw, self.nk, self.nb, self.nGmax, self.npw, self.nwi, _ = list(sz)
+        self.neta = 1
         self.lib = lib
+
+    def _rows(self, *rest):
+        """Shape of a per-(q, eta) output: (nq, *rest) for one eta, (nq, neta, *rest) for a list."""
+        return (self.nq,) + rest if self.neta == 1 else (self.nq, self.neta) + rest
 
     def close(self):
         if getattr(self, "h", None):
@@ -207,7 +229,7 @@ class Context:
             self.h, q0, self.nq if q1 is None else q1, _P(stream)))
 
     def dsf(self) -> np.ndarray:
-        S = np.zeros((self.nq, self.nw))
+        S = np.zeros(self._rows(self.nw))
         _check("lrtddft_dsf", self.lib.lrtddft_dsf(self.h, _dp(S)))
         return S
 
@@ -216,8 +238,8 @@ class Context:
 
     def itcf(self, tau, mode: str = "fold"):
         tau = np.ascontiguousarray(tau, dtype=np.float64)
-        F = np.zeros((self.nq, len(tau)))
-        m = np.zeros((self.nq, 5))
+        F = np.zeros(self._rows(len(tau)))
+        m = np.zeros(self._rows(5))
         _check("lrtddft_itcf_laplace", self.lib.lrtddft_itcf_laplace(
             self.h, len(tau), _dp(tau), ITCF[mode], _dp(F), _dp(m)))
         return F, m
@@ -227,12 +249,14 @@ class Context:
             self.h, ntau, _P(tau_ptr), ITCF[mode], _P(F_ptr), _P(metrics_ptr), _P(stream)))
 
     def set_tuning(self, auto: bool = False, single_q: bool = False, variant: int = -1, unit_stages: int = 0,
-                   pair_simt: bool = False):
+                   pair_simt: bool = False, fine_accum: bool = False):
         """lrtddft_set_tuning: auto times the contraction's variants and unit sizes on the first
         launch of each shape; single_q launches the contraction once per q; pair_simt computes
         the split path's pair densities on the FP32 SIMT kernel instead of the tensor cores;
-        variant (-1, 0, 1) and unit_stages (0 or a multiple of 64) force a choice."""
-        flags = (1 if auto else 0) | (2 if single_q else 0) | (4 if pair_simt else 0)
+        fine_accum halves the FP32 accumulation period (32 stages); variant (-1, 0, 1) and
+        unit_stages (0 or a multiple of 64) force a choice."""
+        flags = ((1 if auto else 0) | (2 if single_q else 0) | (4 if pair_simt else 0)
+                 | (8 if fine_accum else 0))
         _check("lrtddft_set_tuning", self.lib.lrtddft_set_tuning(self.h, flags, variant, unit_stages))
 
     def get_tuning(self):
@@ -252,6 +276,7 @@ class Context:
         kern = lrt_kernel(KERNEL[kernel or self.wl.kernel],
                           *[float(x) for x in (fxc_params if fxc_params is not None else self.wl.fxc_params)])
         _check("lrtddft_set_params", self.lib.lrtddft_set_params(self.h, float(T), float(eta), C.byref(kern)))
+        self.neta = 1
         self.wl = self.wl.replace(T=float(T), eta=float(eta), kernel=kernel or self.wl.kernel,
                                   fxc_params=tuple(float(x) for x in (fxc_params if fxc_params is not None
                                                                       else self.wl.fxc_params)))
@@ -282,8 +307,8 @@ class Context:
 
     def attenuate(self, params: Optional[lrt_atten_params] = None):
         p = params if params is not None else atten_params()
-        Sp = np.zeros((self.nq, self.nw))
-        rep = (lrt_atten_report * self.nq)()
+        Sp = np.zeros(self._rows(self.nw))
+        rep = (lrt_atten_report * (self.nq * self.neta))()
         _check("lrtddft_attenuate", self.lib.lrtddft_attenuate(self.h, C.byref(p), _dp(Sp), rep))
         return Sp, [report_dict(r) for r in rep]
 
@@ -291,11 +316,73 @@ class Context:
         """lrtddft_attenuate without device allocation (fixed 16 MiB workspace in the library;
         calls must not overlap on the GPU)."""
         p = params if params is not None else atten_params()
-        Sp = np.zeros((self.nq, self.nw))
-        rep = (lrt_atten_report * self.nq)()
+        Sp = np.zeros(self._rows(self.nw))
+        rep = (lrt_atten_report * (self.nq * self.neta))()
         _check("lrtddft_attenuate_noalloc",
                self.lib.lrtddft_attenuate_noalloc(self.h, C.byref(p), _dp(Sp), rep))
         return Sp, [report_dict(r) for r in rep]
+
+    # --- the eta-convergence test (Sec. 2) ---
+    def set_eta_list(self, etas):
+        """Broadenings (Ha, strictly increasing) computed together by later assemblies; outputs
+        then carry an eta axis after q."""
+        e = np.ascontiguousarray(etas, dtype=np.float64)
+        _check("lrtddft_set_eta_list", self.lib.lrtddft_set_eta_list(self.h, len(e), _dp(e)))
+        self.neta = len(e)
+
+    def get_eta_list(self) -> np.ndarray:
+        n = C.c_int()
+        _check("lrtddft_get_eta_list", self.lib.lrtddft_get_eta_list(self.h, C.byref(n), None))
+        e = np.zeros(n.value)
+        _check("lrtddft_get_eta_list", self.lib.lrtddft_get_eta_list(self.h, C.byref(n), _dp(e)))
+        return e
+
+    def eta_scan(self, tau, tol: float):
+        """(F [nq][neta][ntau], metrics [nq][neta][5], reference eta index [nq])."""
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        F = np.zeros((self.nq, self.neta, len(tau)))
+        m = np.zeros((self.nq, self.neta, 5))
+        ref = np.zeros(self.nq, dtype=np.int32)
+        _check("lrtddft_eta_scan", self.lib.lrtddft_eta_scan(
+            self.h, len(tau), _dp(tau), float(tol), _dp(F), _dp(m), ref.ctypes.data_as(C.POINTER(C.c_int))))
+        return F, m, ref
+
+    # --- dielectric properties (Sec. 3, Eqs. 10-11) ---
+    def dielectric(self, S) -> dict:
+        """chi, 1/eps, eps and sigma at the w >= 0 samples from S (rows as dsf returns them)."""
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        npos = int(np.sum(np.asarray(self.wl.omega) >= 0.0))
+        out = np.zeros(self._rows(npos, 8))
+        _check("lrtddft_dielectric", self.lib.lrtddft_dielectric(self.h, _dp(S), _dp(out)))
+        z = lambda k: out[..., k] + 1j * out[..., k + 1]
+        return {"w": np.asarray(self.wl.omega)[np.asarray(self.wl.omega) >= 0.0], "chi": z(0),
+                "eps_inv": z(2), "eps": z(4), "sigma": z(6)}
+
+    # --- Kubo-Greenwood route (App. A.3) ---
+    def kubo_greenwood(self, etas, tau, tol: float) -> dict:
+        e = np.ascontiguousarray(etas, dtype=np.float64)
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        ne = len(e)
+        sigma = np.zeros((ne, self.nw), dtype=np.complex128)
+        S = np.zeros((ne, self.nw))
+        F = np.zeros((ne, len(tau)))
+        m = np.zeros((ne, 5))
+        ref = C.c_int()
+        _check("lrtddft_kubo_greenwood", self.lib.lrtddft_kubo_greenwood(
+            self.h, ne, _dp(e), len(tau), _dp(tau), float(tol), sigma.ctypes.data_as(_D), _dp(S), _dp(F),
+            _dp(m), C.byref(ref)))
+        return {"sigma": sigma, "S": S, "F": F, "metrics": m, "eta_ref": ref.value}
+
+    def kubo_greenwood_attenuate(self, params: Optional[lrt_atten_params] = None):
+        p = params if params is not None else atten_params()
+        Sp = np.zeros(self.nw)
+        rep = lrt_atten_report()
+        npos = int(np.sum(np.asarray(self.wl.omega) >= 0.0))
+        out = np.zeros((npos, 8))
+        _check("lrtddft_kubo_greenwood_attenuate", self.lib.lrtddft_kubo_greenwood_attenuate(
+            self.h, C.byref(p), _dp(Sp), C.byref(rep), _dp(out)))
+        z = lambda k: out[:, k] + 1j * out[:, k + 1]
+        return Sp, report_dict(rep), {"chi_star": z(0), "eps_inv": z(2), "eps": z(4), "sigma": z(6)}
 
     # --- instrumentation ---
     def profile(self, enable: bool = True):
@@ -346,9 +433,9 @@ class Context:
 
     def get_chi0(self, iq: int) -> np.ndarray:
         nG = int(self.wl.nG[iq])
-        out = np.zeros((self.nwi, nG, nG), dtype=np.complex128)
+        out = np.zeros((self.neta * self.nwi, nG, nG), dtype=np.complex128)
         _check("lrtddft_get_chi0", self.lib.lrtddft_get_chi0(self.h, iq, out.ctypes.data_as(_D)))
-        return out
+        return out if self.neta == 1 else out.reshape(self.neta, self.nwi, nG, nG)
 
     def get_pair_densities(self, iq: int) -> np.ndarray:
         """rho[p][G] of q index iq from the context's pair-density kernel (test hook)."""
@@ -360,9 +447,9 @@ class Context:
 
     def get_chi_col0(self, iq: int) -> np.ndarray:
         nG = int(self.wl.nG[iq])
-        out = np.zeros((self.nwi, nG), dtype=np.complex128)
+        out = np.zeros((self.neta * self.nwi, nG), dtype=np.complex128)
         _check("lrtddft_get_chi_col0", self.lib.lrtddft_get_chi_col0(self.h, iq, out.ctypes.data_as(_D)))
-        return out
+        return out if self.neta == 1 else out.reshape(self.neta, self.nwi, nG)
 
     def get_frequencies(self):
         f = np.zeros(self.nwi)

@@ -379,7 +379,8 @@ lrt_status launch_project(const lrt_ctx* c, const QData& q, const double2* du, c
 }  // namespace
 
 // d chi_00(q, w)/d theta for one q at all internal frequencies: out[nwi][5] complex as
-// (re, im) pairs.  Needs chi0 and chi of the q and the pair densities of the q in dw.rho.
+// (re, im) pairs, and q.ds0, the tangents of d chi_00/d eta at w = 0 (zerofreq.cu).  Needs
+// chi0 and chi of the q and the pair densities of the q in dw.rho.
 lrt_status launch_adjoint_q(const lrt_ctx* c, QData& q, int iq, std::vector<double>& out,
                             cudaStream_t s) {
   (void)iq;
@@ -480,6 +481,14 @@ lrt_status launch_adjoint_q(const lrt_ctx* c, QData& q, int iq, std::vector<doub
   else
     st = wide32 ? launch_project<float, 32>(c, q, d_u, d_v, d_dl, d_df, d_ddf, d_g, s)
                 : launch_project<float, 16>(c, q, d_u, d_v, d_dl, d_df, d_ddf, d_g, s);
+  if (st != LRT_OK) {
+    freeall();
+    return st;
+  }
+  // the w -> 0 limit S(0) = (T/(pi n)) Re d chi_00/d eta: its tangents are second derivatives
+  q.ds0.assign(10, 0.0);
+  st = launch_s0_tangents(c, q, d_u + (size_t)c->hcol * N, d_v + (size_t)c->hcol * N, d_dK, d_dl,
+                          d_df, d_ddf, q.ds0.data(), s);
   if (st != LRT_OK) {
     freeall();
     return st;

@@ -42,6 +42,7 @@ void free_ctx(lrt_ctx* c) {
   cudaSetDevice(c->device);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   free_tc_state(c);
+  free_kg_state(c);
   for (auto& q : c->qd) {
     free_split_plan(q.sp);
     cudaFree(q.Kdev);
@@ -64,10 +65,18 @@ void free_ctx(lrt_ctx* c) {
   cudaFree(c->dw.scratch);
   cudaFree(c->dw.pd_work);
   cudaFree(c->dw.dyson_ws);
+  cudaFree(c->dw.s0);
+  cudaFree(c->dw.zf);
+  cudaFree(c->dw.zf_ws);
+  cudaFree(c->dw.eta_ref);
   delete c;
 }
 
-lrt_status check_status_word(lrt_ctx* c) {
+}  // namespace
+
+// The device status word after the work so far: a timed-out wait (bit 2) first, then a zero
+// Dyson pivot (bit 1).
+lrt_status check_status_word(const lrt_ctx* c) {
   int st = 0;
   LRT_CUDA(cudaMemcpy(&st, c->dw.status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & 2) {
@@ -80,8 +89,6 @@ lrt_status check_status_word(lrt_ctx* c) {
   }
   return LRT_OK;
 }
-
-}  // namespace
 
 lrt_status ensure_rho(lrt_ctx* c) {
   size_t elem = (c->precision == LRT_PREC_FP64) ? sizeof(double2) : sizeof(float2);
@@ -173,6 +180,8 @@ extern "C" lrt_status lrtddft_create(const lrt_cell* cell, const lrt_kmesh* kmes
   c->nb = nbands;
   c->T = T;
   c->eta = eta;
+  c->etas.assign(1, eta);
+  c->neta = 1;
   c->nq = nq;
   c->q.assign(q, q + 3 * nq);
   c->nw = nw;
@@ -181,17 +190,16 @@ extern "C" lrt_status lrtddft_create(const lrt_cell* cell, const lrt_kmesh* kmes
   c->precision = o.precision;
   c->device = o.device;
   c->np = (int64_t)c->nk * c->nb * c->nb;
-  // internal frequencies: an exact 0 becomes h; otherwise h is appended
+  // internal frequencies: the grid, plus w = 0 when it is not on it (S(q,0) enters Eq. 1)
   c->freqs = c->omega;
   c->hcol = -1;
   for (int j = 0; j < nw; ++j)
     if (c->omega[j] == 0.0) {
-      c->freqs[j] = kHZero;
       c->hcol = j;
       break;
     }
   if (c->hcol < 0) {
-    c->freqs.push_back(kHZero);
+    c->freqs.push_back(0.0);
     c->hcol = nw;
   }
   c->nwi = (int)c->freqs.size();
@@ -264,8 +272,9 @@ extern "C" lrt_status lrtddft_chi0_assemble(lrt_ctx* c, int q_begin, int q_end, 
   LRT_CUDA(cudaSetDevice(c->device));
   for (int iq = q_begin; iq < q_end; ++iq) {
     QData& Q = c->qd[iq];
-    if (!Q.chi0) LRT_CUDA(cudaMalloc(&Q.chi0, (size_t)c->nwi * Q.nG * Q.nG * sizeof(double2)));
+    if (!Q.chi0) LRT_CUDA(cudaMalloc(&Q.chi0, (size_t)ncol(c) * Q.nG * Q.nG * sizeof(double2)));
   }
+  LRT_TRY(ensure_zf(c));
   if (c->precision == LRT_PREC_FP64) {
     LRT_TRY(ensure_rho(c));
     for (int iq = q_begin; iq < q_end; ++iq) {
@@ -273,6 +282,8 @@ extern "C" lrt_status lrtddft_chi0_assemble(lrt_ctx* c, int q_begin, int q_end, 
       LRT_TRY(launch_pair_weights(c, Q, s));
       LRT_TRY(launch_pair_density(c, Q, c->dw.rho, false, s));
       LRT_TRY(launch_chi0_fp64(c, Q, s));
+      // S(q,0) needs this q's pair densities: before the next q overwrites them
+      LRT_TRY(launch_s0(c, Q, iq, c->dw.rho, nullptr, 1.0f, s));
     }
   } else {
     LRT_TRY(launch_chi0_split_range(c, q_begin, q_end, s));
@@ -299,7 +310,7 @@ extern "C" lrt_status lrtddft_dyson_solve(lrt_ctx* c, int q_begin, int q_end, vo
       set_error("dyson_solve before chi0_assemble");
       return LRT_ESTATE;
     }
-    if (!Q.chi) LRT_CUDA(cudaMalloc(&Q.chi, (size_t)c->nwi * Q.nG * sizeof(double2)));
+    if (!Q.chi) LRT_CUDA(cudaMalloc(&Q.chi, (size_t)ncol(c) * Q.nG * sizeof(double2)));
     LRT_TRY(launch_dyson(c, Q, iq, s));
     Q.have_chi = true;
     Q.have_dchi = false;
@@ -307,6 +318,9 @@ extern "C" lrt_status lrtddft_dyson_solve(lrt_ctx* c, int q_begin, int q_end, vo
   c->have_S = false;
   return LRT_OK;
 }
+
+static lrt_status apply_eta_list(lrt_ctx* c, int n, const double* etas);
+static lrt_status check_tau(const lrt_ctx* c, int ntau, const double* tau);
 
 static lrt_status need_all_chi(lrt_ctx* c) {
   LRT_TRY(need_device(c));
@@ -331,7 +345,7 @@ extern "C" lrt_status lrtddft_dsf(lrt_ctx* c, double* S) {
   // host-buffer calls run on the legacy stream after all earlier work on any stream
   LRT_CUDA(cudaDeviceSynchronize());
   LRT_TRY(launch_dsf(c, c->dw.S, 0));
-  LRT_CUDA(cudaMemcpy(S, c->dw.S, (size_t)c->nq * c->nw * sizeof(double), cudaMemcpyDeviceToHost));
+  LRT_CUDA(cudaMemcpy(S, c->dw.S, (size_t)nrow(c) * c->nw * sizeof(double), cudaMemcpyDeviceToHost));
   LRT_TRY(check_status_word(c));
   c->have_S = true;
   return LRT_OK;
@@ -365,8 +379,8 @@ extern "C" lrt_status lrtddft_itcf_laplace(lrt_ctx* c, int ntau, const double* t
     return st;
   };
   if (cudaMalloc(&dtau, ntau * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dF, (size_t)c->nq * ntau * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dm, (size_t)c->nq * 5 * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&dF, (size_t)nrow(c) * ntau * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dm, (size_t)nrow(c) * 5 * sizeof(double)) != cudaSuccess) {
     set_error("device allocation");
     return done(LRT_ENOMEM);
   }
@@ -375,10 +389,10 @@ extern "C" lrt_status lrtddft_itcf_laplace(lrt_ctx* c, int ntau, const double* t
     return done(LRT_ECUDA);
   lrt_status st = lrtddft_itcf_laplace_device(c, ntau, dtau, mode, dF, dm, 0);
   if (st != LRT_OK) return done(st);
-  if (cudaMemcpy(F, dF, (size_t)c->nq * ntau * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpy(F, dF, (size_t)nrow(c) * ntau * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
     return done(LRT_ECUDA);
   if (metrics &&
-      cudaMemcpy(metrics, dm, (size_t)c->nq * 5 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      cudaMemcpy(metrics, dm, (size_t)nrow(c) * 5 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
     return done(LRT_ECUDA);
   return done(check_status_word(c));
 }
@@ -456,7 +470,7 @@ extern "C" lrt_status lrtddft_get_chi0(const lrt_ctx* c, int iq, double* chi0) {
     set_error("get_chi0 before chi0_assemble");
     return LRT_ESTATE;
   }
-  LRT_CUDA(cudaMemcpy(chi0, Q.chi0, (size_t)c->nwi * Q.nG * Q.nG * sizeof(double2),
+  LRT_CUDA(cudaMemcpy(chi0, Q.chi0, (size_t)ncol(c) * Q.nG * Q.nG * sizeof(double2),
                       cudaMemcpyDeviceToHost));
   return LRT_OK;
 }
@@ -469,7 +483,7 @@ extern "C" lrt_status lrtddft_get_chi_col0(const lrt_ctx* c, int iq, double* chi
     set_error("get_chi_col0 before dyson_solve");
     return LRT_ESTATE;
   }
-  LRT_CUDA(cudaMemcpy(chi, Q.chi, (size_t)c->nwi * Q.nG * sizeof(double2), cudaMemcpyDeviceToHost));
+  LRT_CUDA(cudaMemcpy(chi, Q.chi, (size_t)ncol(c) * Q.nG * sizeof(double2), cudaMemcpyDeviceToHost));
   return LRT_OK;
 }
 
@@ -552,8 +566,8 @@ extern "C" lrt_status lrtddft_set_params(lrt_ctx* c, double T, double eta, const
   LRT_TRY(need_device(c));
   LRT_CUDA(cudaSetDevice(c->device));
   LRT_CUDA(cudaDeviceSynchronize());
+  LRT_TRY(apply_eta_list(c, 1, &eta));
   c->T = T;
-  c->eta = eta;
   c->kernel = *kernel;
   c->graph_valid = false;
   const size_t ne = (size_t)2 * c->nk * c->nb;
@@ -572,8 +586,102 @@ extern "C" lrt_status lrtddft_set_params(lrt_ctx* c, double T, double eta, const
   return LRT_OK;
 }
 
+// Install an eta list (ascending, validated by the caller): everything sized by the number of
+// chi0 columns or spectrum rows is released or reallocated, and chi0, chi and the plans of
+// the tensor path are dropped (they are rebuilt by the next assemble).
+static lrt_status apply_eta_list(lrt_ctx* c, int n, const double* etas) {
+  const bool same_size = n == c->neta;
+  c->etas.assign(etas, etas + n);
+  c->neta = n;
+  c->eta = etas[0];
+  c->graph_valid = false;
+  c->have_S = false;
+  for (auto& Q : c->qd) {
+    Q.have_chi0 = Q.have_chi = Q.have_dchi = false;
+    if (!same_size) {
+      cudaFree(Q.chi0);
+      cudaFree(Q.chi);
+      Q.chi0 = Q.chi = nullptr;
+    }
+    free_split_plan(Q.sp);   // the column tables carry the etas
+  }
+  if (same_size) return LRT_OK;
+  cudaFree(c->dw.S);
+  cudaFree(c->dw.chi00);
+  cudaFree(c->dw.s0);
+  cudaFree(c->dw.eta_ref);
+  c->dw.S = nullptr;
+  c->dw.s0 = nullptr;
+  c->dw.chi00 = nullptr;
+  c->dw.eta_ref = nullptr;
+  LRT_CUDA(cudaMalloc(&c->dw.S, (size_t)nrow(c) * c->nw * sizeof(double)));
+  LRT_CUDA(cudaMalloc(&c->dw.chi00, (size_t)c->nq * ncol(c) * sizeof(double2)));
+  LRT_CUDA(cudaMalloc(&c->dw.s0, (size_t)nrow(c) * sizeof(double2)));
+  LRT_CUDA(cudaMemset(c->dw.s0, 0, (size_t)nrow(c) * sizeof(double2)));
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_set_eta_list(lrt_ctx* c, int n_eta, const double* eta) {
+  if (!c || !eta) return bad("NULL argument");
+  if (n_eta < 1 || n_eta > 64) return bad("n_eta must be in 1..64");
+  for (int j = 0; j < n_eta; ++j)
+    if (!(eta[j] > 0) || !std::isfinite(eta[j]) || (j > 0 && !(eta[j] > eta[j - 1])))
+      return bad("etas must be positive, finite and strictly increasing");
+  LRT_TRY(need_device(c));
+  LRT_CUDA(cudaDeviceSynchronize());
+  return apply_eta_list(c, n_eta, eta);
+}
+
+extern "C" lrt_status lrtddft_get_eta_list(const lrt_ctx* c, int* n_eta, double* eta) {
+  if (!c || !n_eta) return bad("NULL argument");
+  *n_eta = c->neta;
+  if (eta) std::copy(c->etas.begin(), c->etas.end(), eta);
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_eta_scan(lrt_ctx* c, int ntau, const double* tau, double tol, double* F,
+                                       double* metrics, int* eta_ref) {
+  if (!c || !tau || !eta_ref) return bad("NULL argument");
+  if (!(tol >= 0) || !std::isfinite(tol)) return bad("tol must be finite and >= 0");
+  LRT_TRY(check_tau(c, ntau, tau));
+  LRT_TRY(need_all_chi(c));
+  LRT_CUDA(cudaDeviceSynchronize());
+  if (!c->dw.eta_ref) LRT_CUDA(cudaMalloc(&c->dw.eta_ref, (size_t)c->nq * sizeof(int)));
+  double *dtau = nullptr, *dF = nullptr, *dm = nullptr;
+  auto done = [&](lrt_status st) {
+    cudaFree(dtau);
+    cudaFree(dF);
+    cudaFree(dm);
+    return st;
+  };
+  if (cudaMalloc(&dtau, ntau * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dF, (size_t)nrow(c) * ntau * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dm, (size_t)nrow(c) * 5 * sizeof(double)) != cudaSuccess) {
+    set_error("device allocation");
+    return done(LRT_ENOMEM);
+  }
+  if (cudaMemcpy(dtau, tau, ntau * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return done(LRT_ECUDA);
+  lrt_status st = launch_dsf(c, c->dw.S, 0);
+  if (st == LRT_OK) st = launch_itcf(c, c->dw.S, ntau, dtau, LRT_ITCF_FOLD, dF, dm, 0);
+  if (st == LRT_OK) st = launch_eta_pick(c, dm, c->nq, c->neta, tol, c->dw.eta_ref, 0);
+  if (st != LRT_OK) return done(st);
+  if ((F && cudaMemcpy(F, dF, (size_t)nrow(c) * ntau * sizeof(double), cudaMemcpyDeviceToHost) !=
+                cudaSuccess) ||
+      (metrics && cudaMemcpy(metrics, dm, (size_t)nrow(c) * 5 * sizeof(double),
+                             cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      cudaMemcpy(eta_ref, c->dw.eta_ref, (size_t)c->nq * sizeof(int), cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+    return done(LRT_ECUDA);
+  return done(check_status_word(c));
+}
+
 // d chi_00/d theta of every q (cached until chi0, chi or the parameters change)
 static lrt_status ensure_dchi(lrt_ctx* c) {
+  if (c->neta > 1) {
+    set_error("the adjoint takes a single eta (set_params or an eta list of one)");
+    return LRT_EUNSUPPORTED;
+  }
   LRT_TRY(need_all_chi(c));
   LRT_CUDA(cudaSetDevice(c->device));
   LRT_CUDA(cudaDeviceSynchronize());
@@ -603,10 +711,12 @@ static lrt_status s_and_jacobian(lrt_ctx* c, int iq, std::vector<double>& S, std
   auto dim = [&](int w, int j) { return Q.dchi[(size_t)w * 10 + 2 * j + 1]; };
   S.assign(c->nw, 0.0);
   dS.assign((size_t)c->nw * 5, 0.0);
-  const double h = kHZero;
-  S0 = -chi00[c->hcol].y * c->T / (pin * h);
-  for (int j = 0; j < 5; ++j) dS0[j] = -dim(c->hcol, j) * c->T / (pin * h);
-  dS0[0] += -chi00[c->hcol].y / (pin * h);
+  // w -> 0: S(0) = (T/(pi n)) Re s, s = d chi_00/d eta (the eta tangent at w = 0), and its
+  // tangents from the second-order pieces d s/d theta
+  const double s_re = Q.dchi[(size_t)c->hcol * 10 + 2];
+  S0 = c->T * s_re / pin;
+  for (int j = 0; j < 5; ++j) dS0[j] = c->T * Q.ds0[2 * j] / pin;
+  dS0[0] += s_re / pin;
   for (int w = 0; w < c->nw; ++w) {
     const double om = c->omega[w];
     if (om == 0.0) {
@@ -724,13 +834,15 @@ extern "C" lrt_status lrtddft_dsf_vjp(lrt_ctx* c, const double* dL_dS, double gr
 
 extern "C" lrt_status lrtddft_set_tuning(lrt_ctx* c, int flags, int variant, int unit_stages) {
   if (!c) return bad("NULL context");
-  if (flags & ~(LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q | LRT_TUNE_PAIR_SIMT)) return bad("unknown tuning flags");
+  if (flags & ~(LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q | LRT_TUNE_PAIR_SIMT | LRT_TUNE_FINE_ACCUM))
+    return bad("unknown tuning flags");
   if (variant < -1 || variant > 1) return bad("variant must be -1, 0 or 1");
   if (unit_stages != 0 && (unit_stages < 64 || unit_stages % 64 != 0))
     return bad("unit_stages must be 0 or a positive multiple of 64");
   c->autotune = (flags & LRT_TUNE_AUTO) != 0;
   c->multi_q = (flags & LRT_TUNE_SINGLE_Q) == 0;
   c->pair_simt = (flags & LRT_TUNE_PAIR_SIMT) != 0;
+  c->fine_accum = (flags & LRT_TUNE_FINE_ACCUM) != 0;
   c->tune_variant = variant;
   c->tune_unit_stages = unit_stages;
   c->graph_valid = false;

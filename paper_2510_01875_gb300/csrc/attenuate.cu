@@ -58,7 +58,7 @@ struct AttCfg {
   double accept_mean, accept_rms;
   int average;           // 1 mean of accepted degrees, 0 best score
   double T, n;
-  int nw, nwi, hcol;
+  int nw;
 };
 
 __device__ inline double block_sum(double v, double* red) {
@@ -346,7 +346,7 @@ __device__ inline double branch_wt(const AttCfg& c, const double* omega, int i, 
 }
 
 // block per q.  best window per degree, constraints (Eqs. 5, 7), S_p.
-__global__ void att_select(const double* __restrict__ S, const double2* __restrict__ chi00,
+__global__ void att_select(const double* __restrict__ S, const double2* __restrict__ s0,
                            const double* __restrict__ omega, AttCfg cfg,
                            const int2* __restrict__ cands, const double* __restrict__ yf_all,
                            const CandOut* __restrict__ cout, double* __restrict__ Fn_work,
@@ -383,7 +383,7 @@ __global__ void att_select(const double* __restrict__ S, const double2* __restri
   const int npos = N + (cfg.zero ? 0 : 1);
   const int off = cfg.zero ? 0 : 1;
   // reference F(beta/2)
-  double S0 = -chi00[(size_t)iq * cfg.nwi + cfg.hcol].y / (M_PI * cfg.n * kHZero / cfg.T);
+  const double S0 = cfg.T * s0[iq].x / (M_PI * cfg.n);   // the w -> 0 limit (zerofreq.cu)
   double fr = 0.0;
   for (int i = threadIdx.x; i < npos; i += blockDim.x) {
     double xv = branch_x(cfg, omega, i);
@@ -470,13 +470,12 @@ __global__ void att_select(const double* __restrict__ S, const double2* __restri
   if (threadIdx.x == 0) nacc_out[iq] = nacc;
 }
 
-}  // namespace
-
-lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const double* S_dev,
-                           double* Sp_host, lrt_atten_report* rep, cudaStream_t s) {
+// Configuration, validation and the (degree, window) candidates of one attenuation call.
+lrt_status plan_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, AttCfg& cfg,
+                            std::vector<int2>& cands) {
   lrt_atten_params p{};
   if (pin) p = *pin;
-  AttCfg cfg{};
+  cfg = AttCfg{};
   cfg.jp = c->nw;
   for (int j = 0; j < c->nw; ++j)
     if (c->omega[j] >= 0.0) {
@@ -530,8 +529,6 @@ lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const 
   cfg.T = c->T;
   cfg.n = c->density;
   cfg.nw = c->nw;
-  cfg.nwi = c->nwi;
-  cfg.hcol = c->hcol;
   // window grid: m = 2 round(w / (2 dw)) + 1 over linspace(w_min, w_max, n_w), distinct,
   // ascending; candidates with d + 2 <= m <= N
   double wlo = p.w_min > 0 ? p.w_min : 4.0 * cfg.dw;
@@ -542,7 +539,7 @@ lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const 
     double w = nwin == 1 ? wlo : wlo + (whi - wlo) * i / (nwin - 1);
     ms.insert(2 * (int)std::floor(w / (2.0 * cfg.dw) + 0.5) + 1);
   }
-  std::vector<int2> cands;
+  cands.clear();
   for (int d = cfg.dmin; d <= dmax; ++d)
     for (int m : ms)
       if (m >= d + 2 && m <= N && m >= 3) cands.push_back(make_int2(d, m));
@@ -551,46 +548,56 @@ lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const 
     set_error("no admissible (degree, window) candidate");
     return LRT_EINVAL;
   }
-  int nq = c->nq;
-  size_t prep_sz = (size_t)nq * (cfg.L + cfg.K + 1);
-  size_t yf_sz = (size_t)nq * cfg.ncand * N;
-  size_t dw_sz = (size_t)nq * cfg.ncand * cfg.L;
-  size_t bytes = (prep_sz + yf_sz + dw_sz + (size_t)nq * cfg.ntau + (size_t)nq * c->nw) * sizeof(double) +
-                 nq * sizeof(AttQ) + (size_t)nq * cfg.ncand * sizeof(CandOut) +
-                 (size_t)nq * kMaxDegree * sizeof(DegOut) + cfg.ncand * sizeof(int2) + nq * sizeof(int) + 16 * 256;
-  char* buf = nullptr;
-  LRT_CUDA(cudaMalloc(&buf, bytes));
-  struct Free {
-    char* b;
-    ~Free() { cudaFree(b); }
-  } fr{buf};
-  size_t off = 0;
-  auto take = [&](size_t n) {
-    char* p0 = buf + off;
-    off += (n + 255) / 256 * 256;
-    return p0;
-  };
-  double* prep = (double*)take(prep_sz * sizeof(double));
-  double* yf = (double*)take(yf_sz * sizeof(double));
-  double* dwork = (double*)take(dw_sz * sizeof(double));
-  double* fnw = (double*)take((size_t)nq * cfg.ntau * sizeof(double));
-  double* spd = (double*)take((size_t)nq * c->nw * sizeof(double));
-  AttQ* aq = (AttQ*)take(nq * sizeof(AttQ));
-  CandOut* co = (CandOut*)take((size_t)nq * cfg.ncand * sizeof(CandOut));
-  DegOut* dout = (DegOut*)take((size_t)nq * kMaxDegree * sizeof(DegOut));
-  int2* dc = (int2*)take(cfg.ncand * sizeof(int2));
-  int* nacc = (int*)take(nq * sizeof(int));
-  if (off > bytes) {
-    set_error("attenuation workspace sizing");
-    return LRT_ECUDA;
+  return LRT_OK;
+}
+
+// Byte offsets of the workspace parts (each rounded up to 256 bytes).
+struct AttLayout {
+  size_t prep, yf, dwork, fnw, spd, aq, co, dout, dc, nacc, total;
+};
+AttLayout attenuation_layout(const AttCfg& cfg, int nq) {
+  auto up = [](size_t n) { return (n + 255) / 256 * 256; };
+  const size_t sz[10] = {up((size_t)nq * (cfg.L + cfg.K + 1) * sizeof(double)),
+                         up((size_t)nq * cfg.ncand * cfg.N * sizeof(double)),
+                         up((size_t)nq * cfg.ncand * cfg.L * sizeof(double)),
+                         up((size_t)nq * cfg.ntau * sizeof(double)),
+                         up((size_t)nq * cfg.nw * sizeof(double)),
+                         up(nq * sizeof(AttQ)),
+                         up((size_t)nq * cfg.ncand * sizeof(CandOut)),
+                         up((size_t)nq * kMaxDegree * sizeof(DegOut)),
+                         up(cfg.ncand * sizeof(int2)),
+                         up(nq * sizeof(int))};
+  size_t off[10], o = 0;
+  for (int i = 0; i < 10; ++i) {
+    off[i] = o;
+    o += sz[i];
   }
+  return AttLayout{off[0], off[1], off[2], off[3], off[4], off[5], off[6], off[7], off[8], off[9], o};
+}
+
+// The kernels of one attenuation call on the workspace at buf (laid out by attenuation_layout),
+// then S_p and the report to the host.
+lrt_status run_on_workspace(const lrt_ctx* c, const AttCfg& cfg, const std::vector<int2>& cands,
+                            char* buf, const double* S_dev, const double2* s0_dev, int rows,
+                            double* Sp_host, lrt_atten_report* rep, cudaStream_t s) {
+  const int nq = rows;   // spectrum rows: (q, eta) pairs of the context, or the caller's
+  const AttLayout L = attenuation_layout(cfg, nq);
+  double* prep = (double*)(buf + L.prep);
+  double* yf = (double*)(buf + L.yf);
+  double* dwork = (double*)(buf + L.dwork);
+  double* fnw = (double*)(buf + L.fnw);
+  double* spd = (double*)(buf + L.spd);
+  AttQ* aq = (AttQ*)(buf + L.aq);
+  CandOut* co = (CandOut*)(buf + L.co);
+  DegOut* dout = (DegOut*)(buf + L.dout);
+  int2* dc = (int2*)(buf + L.dc);
+  int* nacc = (int*)(buf + L.nacc);
   LRT_CUDA(cudaMemcpyAsync(dc, cands.data(), cands.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
   att_prep<<<nq, 256, 0, s>>>(S_dev, cfg, prep, aq);
   LRT_CUDA(cudaGetLastError());
   att_candidates<<<dim3(cfg.ncand, nq), 256, 0, s>>>(S_dev, cfg, dc, aq, yf, dwork, co);
   LRT_CUDA(cudaGetLastError());
-  att_select<<<nq, 256, 0, s>>>(S_dev, (const double2*)c->dw.chi00, c->dw.omega, cfg, dc, yf, co, fnw,
-                                spd, dout, nacc);
+  att_select<<<nq, 256, 0, s>>>(S_dev, s0_dev, c->dw.omega, cfg, dc, yf, co, fnw, spd, dout, nacc);
   count_launch(c, 3);
   LRT_CUDA(cudaGetLastError());
   LRT_CUDA(cudaMemcpyAsync(Sp_host, spd, (size_t)nq * c->nw * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -625,6 +632,29 @@ lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const 
     }
   }
   return LRT_OK;
+}
+
+}  // namespace
+
+lrt_status run_attenuation_rows(const lrt_ctx* c, const lrt_atten_params* pin, const double* S_dev,
+                                const double2* s0_dev, int rows, double* Sp_host,
+                                lrt_atten_report* rep, cudaStream_t s) {
+  AttCfg cfg;
+  std::vector<int2> cands;
+  LRT_TRY(plan_attenuation(c, pin, cfg, cands));
+  const AttLayout L = attenuation_layout(cfg, rows);
+  char* buf = nullptr;
+  LRT_CUDA(cudaMalloc(&buf, L.total));
+  struct Free {
+    char* b;
+    ~Free() { cudaFree(b); }
+  } fr{buf};
+  return run_on_workspace(c, cfg, cands, buf, S_dev, s0_dev, rows, Sp_host, rep, s);
+}
+
+lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* pin, const double* S_dev,
+                           double* Sp_host, lrt_atten_report* rep, cudaStream_t s) {
+  return run_attenuation_rows(c, pin, S_dev, c->dw.s0, nrow(c), Sp_host, rep, s);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -664,95 +694,10 @@ static lrt_status scratch_address(int dev, void** out) {
 lrt_status run_attenuation_noalloc(const lrt_ctx* c, const lrt_atten_params* pin,
                                    const double* S_dev, double* Sp_host, lrt_atten_report* rep,
                                    cudaStream_t s) {
-  lrt_atten_params p{};
-  if (pin) p = *pin;
-  AttCfg cfg{};
-  cfg.jp = c->nw;
-  for (int j = 0; j < c->nw; ++j)
-    if (c->omega[j] >= 0.0) {
-      cfg.jp = j;
-      break;
-    }
-  cfg.N = c->nw - cfg.jp;
-  if (cfg.N < 8) {
-    set_error("attenuation needs at least 8 samples with w >= 0");
-    return LRT_EINVAL;
-  }
-  cfg.zero = c->omega[cfg.jp] == 0.0;
-  cfg.dw = c->omega[cfg.jp + 1] - c->omega[cfg.jp];
-  for (int j = cfg.jp + 1; j < c->nw; ++j)
-    if (std::fabs((c->omega[j] - c->omega[j - 1]) - cfg.dw) > 1e-9 * cfg.dw) {
-      set_error("attenuation needs uniformly spaced samples with w >= 0");
-      return LRT_EINVAL;
-    }
-  const int N = cfg.N;
-  if (p.feat_lo <= 0.0 && p.feat_hi <= 0.0) {
-    cfg.i0 = std::max(1, (int)std::floor(0.05 * (N - 1)));
-    cfg.i1 = std::min(N - 2, (int)std::ceil(0.95 * (N - 1)));
-  } else {
-    const double* w = c->omega.data() + cfg.jp;
-    cfg.i0 = std::max(1, (int)(std::lower_bound(w, w + N, p.feat_lo) - w));
-    cfg.i1 = std::min(N - 2, (int)(std::upper_bound(w, w + N, p.feat_hi) - w) - 1);
-  }
-  cfg.L = cfg.i1 - cfg.i0 + 1;
-  if (cfg.L < 8) {
-    set_error("featureless range too short");
-    return LRT_EINVAL;
-  }
-  cfg.K = cfg.L / 2;
-  double low = p.low_exclude > 0 ? p.low_exclude : 0.05;
-  cfg.kmin = std::max(1, (int)std::ceil(low * cfg.K));
-  cfg.ntargets = p.n_targets > 0 ? std::min(p.n_targets, kMaxTargets) : 2;
-  cfg.lf = p.lambda_f > 0 ? p.lambda_f : N;
-  cfg.lc = p.lambda_c > 0 ? p.lambda_c : N;
-  cfg.r0 = p.retain_floor > 0 ? p.retain_floor : 1e-4;
-  cfg.dmin = p.d_min > 0 ? p.d_min : 1;
-  int dmax = p.d_max > 0 ? p.d_max : 4;
-  if (dmax < cfg.dmin || dmax - cfg.dmin + 1 > kMaxDegree || dmax > kMaxDegree) {
-    set_error("degree range");
-    return LRT_EINVAL;
-  }
-  cfg.ndeg = dmax - cfg.dmin + 1;
-  cfg.ntau = p.ntau > 1 ? p.ntau : 64;
-  cfg.accept_mean = p.accept_mean > 0 ? p.accept_mean : 4e-3;
-  cfg.accept_rms = p.accept_rms > 0 ? p.accept_rms : 4.2e-5;
-  cfg.average = (p.average == 2) ? 0 : 1;
-  cfg.T = c->T;
-  cfg.n = c->density;
-  cfg.nw = c->nw;
-  cfg.nwi = c->nwi;
-  cfg.hcol = c->hcol;
-  double wlo = p.w_min > 0 ? p.w_min : 4.0 * cfg.dw;
-  double whi = p.w_max > 0 ? p.w_max : 0.25 * N * cfg.dw;
-  int nwin = p.n_w > 0 ? p.n_w : 24;
-  std::set<int> ms;
-  for (int i = 0; i < nwin; ++i) {
-    double w = nwin == 1 ? wlo : wlo + (whi - wlo) * i / (nwin - 1);
-    ms.insert(2 * (int)std::floor(w / (2.0 * cfg.dw) + 0.5) + 1);
-  }
+  AttCfg cfg;
   std::vector<int2> cands;
-  for (int d = cfg.dmin; d <= dmax; ++d)
-    for (int m : ms)
-      if (m >= d + 2 && m <= N && m >= 3) cands.push_back(make_int2(d, m));
-  cfg.ncand = (int)cands.size();
-  if (cfg.ncand == 0) {
-    set_error("no admissible (degree, window) candidate");
-    return LRT_EINVAL;
-  }
-  const int nq = c->nq;
-  // carve the fixed array; reject what does not fit
-  auto up = [](size_t n) { return (n + 255) / 256 * 256; };
-  const size_t prep_b = up((size_t)nq * (cfg.L + cfg.K + 1) * sizeof(double));
-  const size_t yf_b = up((size_t)nq * cfg.ncand * N * sizeof(double));
-  const size_t dw_b = up((size_t)nq * cfg.ncand * cfg.L * sizeof(double));
-  const size_t fn_b = up((size_t)nq * cfg.ntau * sizeof(double));
-  const size_t sp_b = up((size_t)nq * c->nw * sizeof(double));
-  const size_t aq_b = up(nq * sizeof(AttQ));
-  const size_t co_b = up((size_t)nq * cfg.ncand * sizeof(CandOut));
-  const size_t do_b = up((size_t)nq * kMaxDegree * sizeof(DegOut));
-  const size_t dc_b = up(cfg.ncand * sizeof(int2));
-  const size_t na_b = up(nq * sizeof(int));
-  const size_t need = prep_b + yf_b + dw_b + fn_b + sp_b + aq_b + co_b + do_b + dc_b + na_b;
+  LRT_TRY(plan_attenuation(c, pin, cfg, cands));
+  const size_t need = attenuation_layout(cfg, nrow(c)).total;
   if (need > kNoAllocScratchBytes) {
     set_error("attenuation workspace of " + std::to_string(need) + " bytes exceeds the " +
               std::to_string(kNoAllocScratchBytes) +
@@ -762,66 +707,10 @@ lrt_status run_attenuation_noalloc(const lrt_ctx* c, const lrt_atten_params* pin
   }
   void* base = nullptr;
   LRT_TRY(scratch_address(c->device, &base));
-  char* buf = static_cast<char*>(base);
-  size_t off = 0;
-  auto take = [&](size_t b) {
-    char* p0 = buf + off;
-    off += b;
-    return p0;
-  };
-  double* prep = (double*)take(prep_b);
-  double* yf = (double*)take(yf_b);
-  double* dwork = (double*)take(dw_b);
-  double* fnw = (double*)take(fn_b);
-  double* spd = (double*)take(sp_b);
-  AttQ* aq = (AttQ*)take(aq_b);
-  CandOut* co = (CandOut*)take(co_b);
-  DegOut* dout = (DegOut*)take(do_b);
-  int2* dc = (int2*)take(dc_b);
-  int* nacc = (int*)take(na_b);
   // the array keeps the previous call's contents: start this call from zeros
-  LRT_CUDA(cudaMemsetAsync(buf, 0, need, s));
-  LRT_CUDA(cudaMemcpyAsync(dc, cands.data(), cands.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-  att_prep<<<nq, 256, 0, s>>>(S_dev, cfg, prep, aq);
-  LRT_CUDA(cudaGetLastError());
-  att_candidates<<<dim3(cfg.ncand, nq), 256, 0, s>>>(S_dev, cfg, dc, aq, yf, dwork, co);
-  LRT_CUDA(cudaGetLastError());
-  att_select<<<nq, 256, 0, s>>>(S_dev, (const double2*)c->dw.chi00, c->dw.omega, cfg, dc, yf, co, fnw,
-                                spd, dout, nacc);
-  count_launch(c, 3);
-  LRT_CUDA(cudaGetLastError());
-  LRT_CUDA(cudaMemcpyAsync(Sp_host, spd, (size_t)nq * c->nw * sizeof(double), cudaMemcpyDeviceToHost, s));
-  std::vector<AttQ> hq(nq);
-  std::vector<DegOut> hd((size_t)nq * kMaxDegree);
-  std::vector<int> hn(nq);
-  LRT_CUDA(cudaMemcpyAsync(hq.data(), aq, nq * sizeof(AttQ), cudaMemcpyDeviceToHost, s));
-  LRT_CUDA(cudaMemcpyAsync(hd.data(), dout, hd.size() * sizeof(DegOut), cudaMemcpyDeviceToHost, s));
-  LRT_CUDA(cudaMemcpyAsync(hn.data(), nacc, nq * sizeof(int), cudaMemcpyDeviceToHost, s));
-  LRT_CUDA(cudaStreamSynchronize(s));
-  if (rep) {
-    for (int iq = 0; iq < nq; ++iq) {
-      lrt_atten_report& r = rep[iq];
-      r.n_accepted = hn[iq];
-      for (int i = 0; i < 4; ++i) r.targets[i] = i < hq[iq].ntg ? hq[iq].tg[i] : -1;
-      for (int i = 0; i < LRT_ATTEN_MAX_DEG; ++i) {
-        if (i < cfg.ndeg && hd[(size_t)iq * kMaxDegree + i].m > 0) {
-          const DegOut& o = hd[(size_t)iq * kMaxDegree + i];
-          r.degree[i] = o.d;
-          r.window[i] = o.m;
-          r.score[i] = o.score;
-          r.mean_ratio[i] = o.mean_ratio;
-          r.rms_ratio[i] = o.rms_ratio;
-          r.accepted[i] = o.accepted;
-        } else {
-          r.degree[i] = -1;
-          r.window[i] = 0;
-          r.score[i] = r.mean_ratio[i] = r.rms_ratio[i] = 0.0;
-          r.accepted[i] = 0;
-        }
-      }
-    }
-  }
-  return LRT_OK;
+  LRT_CUDA(cudaMemsetAsync(base, 0, need, s));
+  return run_on_workspace(c, cfg, cands, static_cast<char*>(base), S_dev, c->dw.s0, nrow(c), Sp_host,
+                          rep, s);
 }
 
 }  // namespace lrt
@@ -847,15 +736,5 @@ extern "C" lrt_status lrtddft_attenuate_noalloc(lrt_ctx* c, const lrt_atten_para
   LRT_CUDA(cudaDeviceSynchronize());
   LRT_TRY(launch_dsf(c, c->dw.S, 0));
   LRT_TRY(run_attenuation_noalloc(c, p, c->dw.S, Sp, rep, 0));
-  int st = 0;
-  LRT_CUDA(cudaMemcpy(&st, c->dw.status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (st & 1) {
-    set_error("zero pivot in a Dyson matrix");
-    return LRT_ESINGULAR;
-  }
-  if (st & 2) {
-    set_error("a bounded device wait ran out");
-    return LRT_ETIMEOUT;
-  }
-  return LRT_OK;
+  return check_status_word(c);
 }

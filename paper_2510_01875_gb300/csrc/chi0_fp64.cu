@@ -112,19 +112,20 @@ lrt_status launch_chi0_fp64(const lrt_ctx* c, QData& q, cudaStream_t s) {
   int64_t per = (c->np + split - 1) / split;
   per = (per + PC - 1) / PC * PC;
   split = (c->np + per - 1) / per;
-  LRT_CUDA(cudaMemsetAsync(q.chi0, 0, (size_t)c->nwi * q.nG * q.nG * sizeof(double2), s));
+  LRT_CUDA(cudaMemsetAsync(q.chi0, 0, (size_t)ncol(c) * q.nG * q.nG * sizeof(double2), s));
   dim3 grid(npairs, nwt, (unsigned)split);
   double pref = 2.0 / (c->nk * c->volume);
-  {
+  // one launch per broadening of the eta list, into that eta's block of chi0
+  for (int j = 0; j < c->neta; ++j) {
     TimedLaunch tl(c, &c->ev_chi0, s);
     chi0_fp64_kernel<<<grid, 256, 0, s>>>((const double2*)c->dw.rho, c->dw.delta, c->dw.df,
-                                          c->dw.freqs, c->nwi, q.nG, c->np, c->rho_ld, c->eta, pref,
-                                          nblk, per,
-                                          q.chi0);
+                                          c->dw.freqs, c->nwi, q.nG, c->np, c->rho_ld, c->etas[j],
+                                          pref, nblk, per,
+                                          q.chi0 + (size_t)j * c->nwi * q.nG * q.nG);
+    count_launch(c);
+    LRT_CUDA(cudaGetLastError());
   }
-  count_launch(c);
-  if (c->profiling) c->timed_cmac += (double)q.nG * q.nG * c->nw * (double)c->np;
-  LRT_CUDA(cudaGetLastError());
+  if (c->profiling) c->timed_cmac += (double)q.nG * q.nG * c->nw * (double)c->np * c->neta;
   return LRT_OK;
 }
 

@@ -80,6 +80,7 @@ struct QDesc {
   const int* blk;             // [n_st * MAXBLK] G blocks of the super-tile, -1 padding
   const float4* wtab;         // [n_n * 64] per frequency pair {hi_f, hi_f+1, lo_f, lo_f+1}
                               // (CTA r of a pair builds the columns of pairs 32 r .. 32 r + 31)
+  const float2* etab;         // [n_n * 64] eta of both columns of each pair (eta lists only)
   double* C;                  // [n_n * TN][ldr] FP64 sums, column-major
   long long np;
   long long ldr;              // = n_st * NACC * TM (n_st even: super-tile 2 st2 + r is CTA r's)
@@ -114,8 +115,9 @@ __device__ __forceinline__ Unit unit_of(const QDesc& D, int u) {
   return U;
 }
 
-// NS: operand (A/B) stages; NSR: prefetch stages of rho blocks and pair weights.
-template <bool BF, int NS, int NSR>
+// NS: operand (A/B) stages; NSR: prefetch stages of rho blocks and pair weights.  ME: the
+// columns carry their own eta (an eta list: columns (eta, w), eta-major), else P.eta.
+template <bool BF, int NS, int NSR, bool ME>
 __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   extern __shared__ uint8_t smem_raw[];
   // full[s]: this CTA's producers arrive; in the even CTA also the odd CTA's relay.
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   __shared__ int blk_s[MAXBLK];
   __shared__ int nblk_s;
   __shared__ float4 wtab_s[TNH / 4];
+  __shared__ float2 etab_s[TNH / 4];
   __shared__ volatile int abort_s;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -181,6 +184,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       rowtab_s[threadIdx.x] = make_int2(g.x * KS * 8, g.y * KS * 8);
     }
     if (threadIdx.x < TNH / 4) wtab_s[threadIdx.x] = D.wtab[U.nt * 64 + rank * (TNH / 4) + threadIdx.x];
+    if (ME && threadIdx.x < TNH / 4)
+      etab_s[threadIdx.x] = D.etab[U.nt * 64 + rank * (TNH / 4) + threadIdx.x];
     if (threadIdx.x < MAXBLK) blk_s[threadIdx.x] = D.blk[st * MAXBLK + threadIdx.x];
     if (threadIdx.x == 0) {
       int n = 0;
@@ -211,6 +216,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       }
       const int2 ro = rowtab_s[warp & 7];                      // A warps
       const float4* wt = wtab_s + CHUNKS_B * 2 * (warp & 7);   // B warps: 4 frequency pairs
+      const float2* et = etab_s + CHUNKS_B * 2 * (warp & 7);
       const float eta2 = P.eta * P.eta;
       uint32_t s = it % NS, ph = (it / NS) & 1, sr = it % NSR, phr = (it / NSR) & 1;
       for (int st_ = 0; st_ < nstage; ++st_) {
@@ -262,10 +268,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
               // w + Delta from the hi and lo parts of both
               const float2 x = __fadd2_rn(__fadd2_rn(make_float2(w.x, w.y), dh),
                                           __fadd2_rn(make_float2(w.z, w.w), dl));
-              const float2 d = __ffma2_rn(x, x, e2);
+              float2 d, mm;
+              if constexpr (ME) {
+                const float2 e = et[2 * cc + h];                    // eta of both columns
+                d = __ffma2_rn(x, x, __fmul2_rn(e, e));
+                mm = __fmul2_rn(make_float2(-pw.z, -pw.z), e);
+              } else {
+                d = __ffma2_rn(x, x, e2);
+                mm = m;
+              }
               const float2 r = make_float2(rcp_approx(d.x), rcp_approx(d.y));
               const float2 re = __fmul2_rn(__fmul2_rn(df, x), r);   // Re df / (x + i eta)
-              const float2 im = __fmul2_rn(m, r);                   // Im
+              const float2 im = __fmul2_rn(mm, r);                  // Im
               v[4 * h] = re.x;
               v[4 * h + 1] = im.x;
               v[4 * h + 2] = re.y;
@@ -464,16 +478,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TN));
 }
 
-// chi0[w][G][G'] from the FP64 sums (C column-major: C[col * ldr + row])
+// chi0[i][G][G'] from the FP64 sums (C column-major: C[col * ldr + row]).  Tensor column pair
+// w (of ncol = n_eta x nw_tc, eta-major) holds internal frequency i = (w / nw_tc) nwi + w % nw_tc
+// (the w = 0 column appended after the grid is not a tensor column: nw_tc = nwi - 1 then).
 __global__ void chi0_unpack(const double* __restrict__ C, long long ldr,
-                            const int* __restrict__ rp_of, int nG, int nwi, double scale,
-                            double2* __restrict__ chi0) {
+                            const int* __restrict__ rp_of, int nG, int ncol, int nw_tc, int nwi,
+                            double scale, double2* __restrict__ chi0) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long total = (long long)nwi * nG * nG;
+  long long total = (long long)ncol * nG * nG;
   if (t >= total) return;
   int Gp = (int)(t % nG);
   int G = (int)((t / nG) % nG);
   int w = (int)(t / ((long long)nG * nG));
+  const long long out = ((long long)(w / nw_tc) * nwi + w % nw_tc) * nG * nG + (long long)G * nG + Gp;
   int rp = rp_of[G * nG + Gp];
   const double* cre = C + (long long)(2 * w) * ldr;       // column Re w
   const double* cim = C + (long long)(2 * w + 1) * ldr;   // column Im w
@@ -483,7 +500,125 @@ __global__ void chi0_unpack(const double* __restrict__ C, long long ldr,
     v = make_double2(RR - II, RI + IR);
   else
     v = make_double2(RR + II, RI - IR);
-  chi0[t] = make_double2(scale * v.x, scale * v.y);
+  chi0[out] = make_double2(scale * v.x, scale * v.y);
+}
+
+// chi0 at w = 0 when 0 is not on the caller's grid (the column S(q,0) needs), for every eta,
+// on the CUDA cores instead of a tensor tile of its own (one extra frequency would cost a whole
+// 128-frequency column tile of the contraction).  Same Hermitian split as the contraction:
+// with P_p = rho_p(G) rho_p*(G') and w_p = df_p sB/(Delta_p + i eta), RR = sum Pr wr,
+// RI = sum Pr wi, IR = sum Pi wr, II = sum Pi wi give chi0(G,G') = (RR - II) + i(RI + IR) and
+// chi0(G',G) = (RR + II) + i(RI - IR).  FP32 products and per-thread FP32 partial sums over
+// 1024 pairs, flushed into FP64 (round-to-nearest, so unbiased), then FP64 atomics into chi0.
+// grid (G-tile pair I <= J of 16 x 16, pair range); block 64: each thread a 2 x 2 (G, G')
+// register tile (two 16-byte shared loads feed four entries); ZN etas per pass.
+constexpr int ZT = 16;   // G per tile side
+constexpr int ZE = 2;    // etas per pass of an eta list
+struct ZEtas {
+  float v[64];
+};
+template <int ZN>   // etas per pass: 1 (a single eta) or ZE
+__global__ void __launch_bounds__(64) chi0_zero_split_kernel(
+    const float2* __restrict__ rho, int gpad, const float4* __restrict__ pw, long long np,
+    long long per, int nG, int nT, int neta, int e0, double scale, double2* __restrict__ chi0,
+    long long mat_stride, ZEtas etas) {
+  __shared__ __align__(16) float2 rI[32][ZT];
+  __shared__ __align__(16) float2 rJ[32][ZT];
+  __shared__ float2 ws[ZN][32];
+  int bp = blockIdx.x, I = 0;
+  while (bp >= nT - I) {
+    bp -= nT - I;
+    ++I;
+  }
+  const int J = I + bp;
+  const int ti = threadIdx.x >> 3, tj = threadIdx.x & 7;   // rows 2 ti, 2 ti + 1; cols 2 tj, 2 tj + 1
+  const int ne = min(ZN, neta - e0);
+  float acc[ZN][4][4];
+  double sum[ZN][4][4];
+#pragma unroll
+  for (int e = 0; e < ZN; ++e)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[e][k][c] = 0.f, sum[e][k][c] = 0.0;
+  const long long pb = (long long)blockIdx.y * per, pe = min(np, pb + per);
+  int nch = 0;
+  for (long long p0 = pb; p0 < pe; p0 += 32) {
+    __syncthreads();
+    for (int e2 = threadIdx.x; e2 < 2 * 32 * ZT; e2 += 64) {
+      const int half = e2 / (32 * ZT), r = e2 % (32 * ZT);
+      const int l = r % 32, g = r / 32;
+      const long long p = p0 + l;
+      const int GG = (half ? J : I) * ZT + g;
+      float2 v = make_float2(0.f, 0.f);
+      if (p < pe && GG < nG) v = rho[((size_t)((p >> 5) * gpad + GG) << 5) + (size_t)(p & 31)];
+      (half ? rJ : rI)[l][g] = v;
+    }
+    if (threadIdx.x < 32) {
+      const int l = threadIdx.x;
+      const long long p = p0 + l;
+      const float4 q = p < pe ? pw[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float x = q.x + q.y;
+#pragma unroll
+      for (int e = 0; e < ZN; ++e) {
+        float2 w = make_float2(0.f, 0.f);
+        if (p < pe && e < ne) {
+          const float eta = etas.v[e0 + e];
+          const float r = 1.0f / (x * x + eta * eta);
+          w = make_float2(q.z * x * r, -q.z * eta * r);   // df sB / (x + i eta)
+        }
+        ws[e][l] = w;
+      }
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int l = 0; l < 32; ++l) {
+      const float4 A = *reinterpret_cast<const float4*>(&rI[l][2 * ti]);
+      const float4 B = *reinterpret_cast<const float4*>(&rJ[l][2 * tj]);
+      // a conj(b) for the four (row, col) pairs: k = 2 r + c
+      float pr[4], pi[4];
+      pr[0] = A.x * B.x + A.y * B.y, pi[0] = A.y * B.x - A.x * B.y;
+      pr[1] = A.x * B.z + A.y * B.w, pi[1] = A.y * B.z - A.x * B.w;
+      pr[2] = A.z * B.x + A.w * B.y, pi[2] = A.w * B.x - A.z * B.y;
+      pr[3] = A.z * B.z + A.w * B.w, pi[3] = A.w * B.z - A.z * B.w;
+#pragma unroll
+      for (int e = 0; e < ZN; ++e) {
+        const float2 w = ws[e][l];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc[e][k][0] = fmaf(pr[k], w.x, acc[e][k][0]);
+          acc[e][k][1] = fmaf(pr[k], w.y, acc[e][k][1]);
+          acc[e][k][2] = fmaf(pi[k], w.x, acc[e][k][2]);
+          acc[e][k][3] = fmaf(pi[k], w.y, acc[e][k][3]);
+        }
+      }
+    }
+    if (++nch == 32) {
+      nch = 0;
+#pragma unroll
+      for (int e = 0; e < ZN; ++e)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) sum[e][k][c] += (double)acc[e][k][c], acc[e][k][c] = 0.f;
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    const int gi = 2 * ti + (k >> 1), gj = 2 * tj + (k & 1);
+    const int G = I * ZT + gi, Gp = J * ZT + gj;
+    if (G >= nG || Gp >= nG || (I == J && gi > gj)) continue;
+    for (int e = 0; e < ne; ++e) {
+      const double RR = sum[e][k][0] + acc[e][k][0], RI = sum[e][k][1] + acc[e][k][1];
+      const double IR = sum[e][k][2] + acc[e][k][2], II = sum[e][k][3] + acc[e][k][3];
+      double2* m = chi0 + (size_t)(e0 + e) * mat_stride;
+      atomicAdd(&m[(size_t)G * nG + Gp].x, scale * (RR - II));
+      atomicAdd(&m[(size_t)G * nG + Gp].y, scale * (RI + IR));
+      if (G != Gp) {
+        atomicAdd(&m[(size_t)Gp * nG + G].x, scale * (RR + II));
+        atomicAdd(&m[(size_t)Gp * nG + G].y, scale * (RI - IR));
+      }
+    }
+  }
 }
 
 // {Delta_hi, Delta_lo, df sB, 0} per pair (Delta split so that w + Delta keeps FP64-level
@@ -523,9 +658,13 @@ size_t smem_of(int v) {
   return (size_t)kVariants[v].ns * STAGE_BYTES + (size_t)kVariants[v].nsr * R_STAGE + 1024;
 }
 typedef void (*KernFn)(Params);
-KernFn kernel_of(bool bf, int v) {
-  if (bf) return v == 0 ? chi0_tc_kernel<true, 4, 2> : chi0_tc_kernel<true, 3, 4>;
-  return v == 0 ? chi0_tc_kernel<false, 4, 2> : chi0_tc_kernel<false, 3, 4>;
+KernFn kernel_of(bool bf, int v, bool me) {
+  if (me) {
+    if (bf) return v == 0 ? chi0_tc_kernel<true, 4, 2, true> : chi0_tc_kernel<true, 3, 4, true>;
+    return v == 0 ? chi0_tc_kernel<false, 4, 2, true> : chi0_tc_kernel<false, 3, 4, true>;
+  }
+  if (bf) return v == 0 ? chi0_tc_kernel<true, 4, 2, false> : chi0_tc_kernel<true, 3, 4, false>;
+  return v == 0 ? chi0_tc_kernel<false, 4, 2, false> : chi0_tc_kernel<false, 3, 4, false>;
 }
 
 // Per-context state of the tensor path (owned through lrt_ctx::tc).
@@ -538,7 +677,7 @@ struct TcState {
   std::vector<int2> units_h;       // what d_units holds
   float4* stage = nullptr;
   size_t stage_bytes = 0;
-  int ncl[2][kNumVariants] = {{0, 0}, {0, 0}};   // resident CTA pairs per (bf, variant)
+  int ncl[2][kNumVariants][2] = {};   // resident CTA pairs per (bf, variant, eta list)
   std::map<std::vector<long long>, std::pair<int, int>> tuned;   // shape -> (variant, unit idx)
 };
 
@@ -550,11 +689,12 @@ TcState* tc_of(const lrt_ctx* c) {
 
 lrt_status cluster_capacity(const lrt_ctx* c, bool bf, int v, int* out) {
   TcState* T = tc_of(c);
-  if (T->ncl[bf][v] > 0) {
-    *out = T->ncl[bf][v];
+  const bool me = c->neta > 1;
+  if (T->ncl[bf][v][me] > 0) {
+    *out = T->ncl[bf][v][me];
     return LRT_OK;
   }
-  KernFn kern = kernel_of(bf, v);
+  KernFn kern = kernel_of(bf, v, me);
   const size_t smem = smem_of(v);
   LRT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchAttribute attr[1];
@@ -576,7 +716,7 @@ lrt_status cluster_capacity(const lrt_ctx* c, bool bf, int v, int* out) {
     set_error("the chi0 tensor kernel cannot be resident as a CTA pair");
     return LRT_EUNSUPPORTED;
   }
-  T->ncl[bf][v] = n;
+  T->ncl[bf][v][me] = n;
   *out = n;
   return LRT_OK;
 }
@@ -598,11 +738,17 @@ void free_split_plan(SplitPlan& sp) {
   cudaFree(sp.blk);
   cudaFree(sp.rp_of);
   cudaFree(sp.wtab);
+  cudaFree(sp.etab);
   cudaFree(sp.pw);
   cudaFree(sp.C);
   cudaFree(sp.rho);
   sp = SplitPlan();
 }
+
+// Frequencies per eta that run as tensor columns: every internal one except a w = 0 appended
+// after the grid (computed by chi0_zero_split_kernel instead).
+static int nw_tc(const lrt_ctx* c) { return c->hcol == c->nw ? c->nwi - 1 : c->nwi; }
+static int ncol_tc(const lrt_ctx* c) { return c->neta * nw_tc(c); }
 
 // Tables of one q, built once: row super-tiles (4 x 4 sub-blocks of G quads), G blocks,
 // frequency pairs, the unpack map, and the weight and FP64-sum buffers.
@@ -664,14 +810,19 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
         }
     }
   }
-  const int n_n = (2 * c->nwi + TN - 1) / TN;
+  // columns (eta, w), eta-major: column j has the frequency freqs[j % nw_tc] and eta j / nw_tc
+  const int nc = ncol_tc(c), nwt = nw_tc(c);
+  const int n_n = (2 * nc + TN - 1) / TN;
   std::vector<float4> wtab((size_t)n_n * 64, make_float4(0.f, 0.f, 0.f, 0.f));
-  for (int j = 0; j < c->nwi; ++j) {
+  std::vector<float2> etab((size_t)n_n * 64, make_float2(0.f, 0.f));
+  for (int j = 0; j < nc; ++j) {
     // frequency pair j / 2 of its column tile: {hi_f, hi_f+1, lo_f, lo_f+1}
-    const float h = (float)c->freqs[j], l = (float)(c->freqs[j] - (double)h);
+    const double f = c->freqs[j % nwt];
+    const float h = (float)f, l = (float)(f - (double)h);
     float* w4 = reinterpret_cast<float*>(&wtab[j / 2]);
     w4[j % 2] = h;
     w4[2 + j % 2] = l;
+    reinterpret_cast<float*>(&etab[j / 2])[j % 2] = (float)c->etas[j / nwt];
   }
   P.nsub = nsub;
   P.n_st2 = n_st / 2;
@@ -689,6 +840,7 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
       (e = cudaMalloc(&P.blk, blk.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&P.rp_of, rp_of.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&P.wtab, wtab.size() * sizeof(float4))) != cudaSuccess ||
+      (e = cudaMalloc(&P.etab, etab.size() * sizeof(float2))) != cudaSuccess ||
       (e = cudaMalloc(&P.pw, P.pw_n * sizeof(float4))) != cudaSuccess ||
       (e = cudaMalloc(&P.C, (size_t)P.ldr * P.ldc * sizeof(double))) != cudaSuccess)
     return fail(e);
@@ -698,6 +850,8 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
       (e = cudaMemcpy(P.rp_of, rp_of.data(), rp_of.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMemcpy(P.wtab, wtab.data(), wtab.size() * sizeof(float4), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(P.etab, etab.data(), etab.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMemset(P.pw, 0, P.pw_n * sizeof(float4))) != cudaSuccess)
     return fail(e);
@@ -711,9 +865,10 @@ static double scale_A(const lrt_ctx* c) {
   const double r = split_rho_scale(c->precision);
   return r * r;
 }
+// (from the smallest eta of the list: |w| <= df/eta, so every column fits the FP16 range)
 static float scale_B(const lrt_ctx* c) {
   if (c->precision == LRT_PREC_BF16X3) return 1.0f;
-  return std::ldexp(1.0f, (int)std::floor(std::log2(16384.0 * c->eta)));
+  return std::ldexp(1.0f, (int)std::floor(std::log2(16384.0 * c->etas[0])));
 }
 
 // Units of one q for a target of `stages` per unit (a multiple of the accumulator period).
@@ -743,6 +898,7 @@ static lrt_status upload_tables(const lrt_ctx* c, const std::vector<int>& qs,
     D.rowtab = P.rowtab;
     D.blk = P.blk;
     D.wtab = P.wtab;
+    D.etab = P.etab;
     D.C = P.C;
     D.np = c->np;
     D.ldr = P.ldr;
@@ -810,7 +966,7 @@ static lrt_status launch_tables(const lrt_ctx* c, bool bf, int v, int nunits, cu
   P.nunits = nunits;
   P.stage = T->stage;
   P.status = c->dw.status;
-  P.flush = kFlushStages;
+  P.flush = c->fine_accum ? kFlushStages / 2 : kFlushStages;
   P.eta = (float)c->eta;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -826,9 +982,9 @@ static lrt_status launch_tables(const lrt_ctx* c, bool bf, int v, int nunits, cu
   cfg.numAttrs = 1;
   if (timed) {
     TimedLaunch tl(c, &c->ev_chi0, s);
-    LRT_CUDA(cudaLaunchKernelEx(&cfg, kernel_of(bf, v), P));
+    LRT_CUDA(cudaLaunchKernelEx(&cfg, kernel_of(bf, v, c->neta > 1), P));
   } else {
-    LRT_CUDA(cudaLaunchKernelEx(&cfg, kernel_of(bf, v), P));
+    LRT_CUDA(cudaLaunchKernelEx(&cfg, kernel_of(bf, v, c->neta > 1), P));
   }
   return LRT_OK;
 }
@@ -849,7 +1005,7 @@ static lrt_status choose(const lrt_ctx* c, const std::vector<int>& qs,
   LRT_CUDA(cudaStreamIsCapturing(s, &cs));
   if (cs != cudaStreamCaptureStatusNone) return LRT_OK;   // no timing inside a capture
   TcState* T = tc_of(c);
-  std::vector<long long> key = {bf ? 1 : 0, c->np, c->nwi};
+  std::vector<long long> key = {bf ? 1 : 0, c->np, ncol_tc(c), c->fine_accum ? 1 : 0};
   for (int qi : qs) key.push_back(c->qd[qi].nG);
   auto it = T->tuned.find(key);
   if (it != T->tuned.end()) {
@@ -913,19 +1069,56 @@ static lrt_status launch_group(const lrt_ctx* c, const std::vector<int>& qs,
   LRT_TRY(launch_tables(c, bf, v, nunits, s, true));
   count_launch(c);
   if (c->profiling)
-    for (int qi : qs) c->timed_cmac += (double)c->qd[qi].nG * c->qd[qi].nG * c->nw * (double)c->np;
+    for (int qi : qs)
+      c->timed_cmac += (double)c->qd[qi].nG * c->qd[qi].nG * c->nw * (double)c->np * c->neta;
   const double scale = 2.0 / (c->nk * c->volume) / (scale_A(c) * (double)scale_B(c));
   for (int qi : qs) {
     QData& q = const_cast<lrt_ctx*>(c)->qd[qi];
     const int nG = q.nG;
-    long long total = (long long)c->nwi * nG * nG;
+    long long total = (long long)ncol_tc(c) * nG * nG;
     chi0_unpack<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(q.sp.C, q.sp.ldr, q.sp.rp_of, nG,
-                                                               c->nwi, scale, q.chi0);
+                                                               ncol_tc(c), nw_tc(c), c->nwi, scale,
+                                                               q.chi0);
     count_launch(c);
     LRT_CUDA(cudaGetLastError());
   }
   const_cast<lrt_ctx*>(c)->last_tc_variant = v;
   const_cast<lrt_ctx*>(c)->last_tc_unit_stages = stages;
+  return LRT_OK;
+}
+
+// chi0 at an appended w = 0 for every eta of q (pair densities in rho), on the CUDA cores.
+static lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho, float sB, cudaStream_t s) {
+  if (c->hcol != c->nw) return LRT_OK;   // w = 0 is on the grid: a tensor column
+  const int nG = q.nG;
+  const long long mat = (long long)nG * nG;
+  double2* base = q.chi0 + (size_t)c->hcol * mat;
+  LRT_CUDA(cudaMemset2DAsync(base, (size_t)c->nwi * mat * sizeof(double2), 0, (size_t)mat * sizeof(double2),
+                             c->neta, s));
+  int dev = 0, nsm = 0;
+  LRT_CUDA(cudaGetDevice(&dev));
+  LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int nT = (nG + ZT - 1) / ZT, nTP = nT * (nT + 1) / 2;
+  long long nsplit = std::max<long long>(1, (32LL * nsm + nTP - 1) / nTP);
+  long long per = (c->np + nsplit - 1) / nsplit;
+  per = (per + 31) / 32 * 32;
+  nsplit = (c->np + per - 1) / per;
+  const double rs = split_rho_scale(c->precision);
+  const double scale = 2.0 / (c->nk * c->volume) / (rs * rs * (double)sB);
+  ZEtas E{};   // the etas travel as a kernel argument (at most 64)
+  for (int j = 0; j < c->neta; ++j) E.v[j] = (float)c->etas[j];
+  for (int e0 = 0; e0 < c->neta; e0 += ZE) {
+    if (c->neta == 1)
+      chi0_zero_split_kernel<1><<<dim3(nTP, (unsigned)nsplit), 64, 0, s>>>(
+          (const float2*)rho, c->rho_gpad, q.sp.pw, c->np, per, nG, nT, c->neta, e0, scale, base,
+          (long long)c->nwi * mat, E);
+    else
+      chi0_zero_split_kernel<ZE><<<dim3(nTP, (unsigned)nsplit), 64, 0, s>>>(
+          (const float2*)rho, c->rho_gpad, q.sp.pw, c->np, per, nG, nT, c->neta, e0, scale, base,
+          (long long)c->nwi * mat, E);
+    count_launch(c);
+    LRT_CUDA(cudaGetLastError());
+  }
   return LRT_OK;
 }
 
@@ -981,10 +1174,17 @@ lrt_status launch_chi0_split_range(lrt_ctx* c, int q_begin, int q_end, cudaStrea
       rhos.push_back(c->qd[iq].sp.rho);
     }
     LRT_TRY(launch_group(c, grp, rhos, s));
+    for (int iq : grp) {
+      LRT_TRY(launch_zero_split(c, c->qd[iq], c->qd[iq].sp.rho, sB, s));
+      LRT_TRY(launch_s0(c, c->qd[iq], iq, c->qd[iq].sp.rho, c->qd[iq].sp.pw, sB, s));
+    }
   }
   for (int iq : solo) {
     LRT_TRY(prep(iq, c->dw.rho));
     LRT_TRY(launch_group(c, std::vector<int>{iq}, std::vector<const void*>{c->dw.rho}, s));
+    // chi0(0) and S(q,0) need this q's pair densities: before the next q overwrites them
+    LRT_TRY(launch_zero_split(c, c->qd[iq], c->dw.rho, sB, s));
+    LRT_TRY(launch_s0(c, c->qd[iq], iq, c->dw.rho, c->qd[iq].sp.pw, sB, s));
   }
   return LRT_OK;
 }

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) dyson_kernel(const double2* __restrict__ 
 
 lrt_status launch_dyson(const lrt_ctx* c, QData& q, int iq, cudaStream_t s) {
   (void)iq;
-  const int N = q.nG, nw = c->nwi;
+  const int N = q.nG, nw = ncol(c);   // every internal frequency of every eta
   const size_t mat = (size_t)N * (N + 1) * sizeof(double2);
   const size_t smem = mat + 2 * (size_t)N * sizeof(double2);
   int dev = 0;

@@ -11,7 +11,6 @@
 
 namespace lrt {
 
-constexpr double kHZero = 1e-4;        // Ha; frequency standing in for w -> 0 in S(q,0)
 constexpr double kBasisTol = 1e-9;     // |k+G|^2 <= 2 ecut + kBasisTol
 constexpr double kShellTol = 1e-9;     // |q+G|^2 (and |G|^2) closer than this: same shell
 constexpr double kPadDiag = 1.0e6;     // Ha; diagonal of the padding rows of H(k)
@@ -34,6 +33,7 @@ struct SplitPlan {
   int* blk = nullptr;             // [2 n_st2][6] G blocks per super-tile
   int* rp_of = nullptr;           // [nG][nG] row pair of (G, G')
   float4* wtab = nullptr;         // [n_n][64] frequency pairs (hi, hi, lo, lo)
+  float2* etab = nullptr;         // [n_n][64] eta of the two frequencies of each pair
   float4* pw = nullptr;           // [pw_n] (Delta_hi, Delta_lo, df sB, 0)
   double* C = nullptr;            // [ldc][ldr] FP64 sums, column-major
   void* rho = nullptr;            // this q's own pair densities (multi-q launches), or null
@@ -57,11 +57,12 @@ struct QData {
   std::vector<double> wgt_h;      // host copy
   double2* coeff = nullptr;       // device [2][nk][nb][npw]
   int32_t* gather = nullptr;      // device [nk][nG][npw]: index into the k+q basis or -1
-  double2* chi0 = nullptr;        // device [nwi][nG][nG]
-  double2* chi = nullptr;         // device [nwi][nG]  (chi_{G,0})
+  double2* chi0 = nullptr;        // device [neta][nwi][nG][nG]
+  double2* chi = nullptr;         // device [neta][nwi][nG]  (chi_{G,0})
   bool have_chi0 = false;
   bool have_chi = false;
   std::vector<double> dchi;       // [nwi][5] complex: d chi_00/d(T, eta, A, B, C) (adjoint)
+  std::vector<double> ds0;        // [5] complex: d/d(T, eta, A, B, C) of d chi_00/d eta at w = 0
   bool have_dchi = false;
   SplitPlan sp;                   // tensor-path tables of this q
 };
@@ -74,8 +75,8 @@ struct DeviceWork {
   double* df = nullptr;           // [np]
   double* freqs = nullptr;        // [nwi]
   double* omega = nullptr;        // [nw]
-  double* S = nullptr;            // [nq][nw]
-  double* chi00 = nullptr;        // [nq][nwi][2] gather of chi_00 for the spectra kernels
+  double* S = nullptr;            // [nq][neta][nw]
+  double* chi00 = nullptr;        // [nq][neta][nwi][2] gather of chi_00 for the spectra kernels
   int* status = nullptr;          // device status word (0 ok, bit 1 singular, bit 2 timeout)
   double* scratch = nullptr;      // tensor path: FP64 sums of the contraction
   size_t scratch_bytes = 0;
@@ -83,6 +84,11 @@ struct DeviceWork {
   size_t pd_bytes = 0;
   void* dyson_ws = nullptr;       // Dyson matrices of N_G too large for shared memory
   size_t dyson_bytes = 0;
+  double2* s0 = nullptr;          // [nq][neta] d chi_00/d eta at w = 0 (S(q,0) = T Re s0/(pi n))
+  int* eta_ref = nullptr;         // [nq] reference eta of the last eta scan
+  double2* zf = nullptr;          // zero-frequency vectors: x, u, v and the adjoint's pieces
+  void* zf_ws = nullptr;          // matrix of the zero-frequency LU when it exceeds shared memory
+  size_t zf_ws_bytes = 0;
 };
 
 }  // namespace lrt
@@ -101,7 +107,9 @@ struct lrt_ctx {
   int nk = 0;
   int nbands = 0;                 // bands requested per k point
   int nb = 0;                     // bands carried: nbands plus split-multiplet members
-  double T = 0.0, eta = 0.0;
+  double T = 0.0, eta = 0.0;      // eta: the broadening (the smallest of the eta list)
+  int neta = 1;                   // broadenings per context (lrtddft_set_eta_list)
+  std::vector<double> etas;       // [neta] ascending; {eta} unless a list was set
   int nq = 0;
   std::vector<double> q;          // [nq][3]
   int nw = 0;
@@ -135,15 +143,22 @@ struct lrt_ctx {
   bool autotune = false;
   bool multi_q = true;
   bool pair_simt = false;         // split-path pair densities on the FP32 SIMT kernel
+  bool fine_accum = false;        // FP32 accumulation period of 32 stages instead of 64
   int tune_variant = -1;          // forced kernel variant, -1: tuned or default
   int tune_unit_stages = 0;       // forced stages per unit, 0: tuned or default
   int last_tc_variant = -1, last_tc_unit_stages = 0;
+  // Kubo-Greenwood scan (kubo.cu): S*_KG rows and the reference eta of the last scan
+  void* kg = nullptr;
   // captured forward graph (lrtddft_graph_capture)
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
 };
 
 namespace lrt {
+// Columns of chi0 per q (every internal frequency for every eta, eta-major) and rows of the
+// spectra (S, F, metrics: every q for every eta, q-major).
+inline int ncol(const lrt_ctx* c) { return c->neta * c->nwi; }
+inline int nrow(const lrt_ctx* c) { return c->nq * c->neta; }
 // Count kernel launches for lrtddft_profile_read.
 inline void count_launch(const lrt_ctx* c, int n = 1) { c->launches += n; }
 inline cudaEvent_t new_event();
@@ -206,25 +221,55 @@ lrt_status launch_chi0_fp64(const lrt_ctx* c, QData& q, cudaStream_t s);
 lrt_status launch_chi0_split_range(lrt_ctx* c, int q_begin, int q_end, cudaStream_t s);
 void free_split_plan(SplitPlan& sp);
 void free_tc_state(lrt_ctx* c);
-// api.cu: the shared pair-density buffer
+// api.cu: the shared pair-density buffer; the device status word (timeout before singular)
 lrt_status ensure_rho(lrt_ctx* c);
+lrt_status check_status_word(const lrt_ctx* c);
 
 // dyson.cu
 lrt_status launch_dyson(const lrt_ctx* c, QData& q, int iq, cudaStream_t s);
+
+// zerofreq.cu: the w -> 0 limit of Eq. 8, S(q,0) = (T/(pi n)) Re d chi_00/d eta at w = 0
+lrt_status ensure_zf(lrt_ctx* c);
+lrt_status launch_lu_two_solves(const lrt_ctx* c, const QData& q, int w, const double2* rhs_n,
+                                const double2* rhs_t, const double* tscale, double2* out_n,
+                                double2* out_t, double2* v_out, cudaStream_t s);
+lrt_status launch_s0(const lrt_ctx* c, const QData& q, int iq, const void* rho, const float4* pw,
+                     float sB, cudaStream_t s);
+lrt_status launch_s0_tangents(const lrt_ctx* c, const QData& q, const double2* u, const double2* v,
+                              const double* d_dK, const double* delta, const double* df,
+                              const double* ddf, double* ds_host, cudaStream_t s);
 
 // spectra.cu
 lrt_status launch_dsf(const lrt_ctx* c, double* S_dev, cudaStream_t s);
 lrt_status launch_itcf(const lrt_ctx* c, const double* S_dev, int ntau, const double* tau_dev,
                        int mode, double* F_dev, double* metrics_dev, cudaStream_t s);
+// the same on explicit rows of S [rows][nw] with their S(0) values s0 [rows] (S(0) = T Re s0/(pi n))
+lrt_status launch_itcf_rows(const lrt_ctx* c, const double* S_dev, const double2* s0_dev, int rows,
+                            int ntau, const double* tau_dev, int mode, double* F_dev,
+                            double* metrics_dev, cudaStream_t s);
+// reference eta per q from metrics [nq][neta][5] (Sec. 2)
+lrt_status launch_eta_pick(const lrt_ctx* c, const double* metrics_dev, int nq, int neta, double tol,
+                           int* ref_dev, cudaStream_t s);
 
 // adjoint.cu: d chi_00/d(T, eta, A, B, C) at every internal frequency of one q, out[nwi][10]
 // (complex pairs); needs the q's chi0, chi and pair densities (in dw.rho)
 lrt_status launch_adjoint_q(const lrt_ctx* c, QData& q, int iq, std::vector<double>& out,
                             cudaStream_t s);
 
-// attenuate.cu
+// attenuate.cu: the context's spectrum rows, or explicit rows S [rows][nw] with s0 [rows]
 lrt_status run_attenuation(const lrt_ctx* c, const lrt_atten_params* p, const double* S_dev,
                            double* Sp_host, lrt_atten_report* rep, cudaStream_t s);
+lrt_status run_attenuation_rows(const lrt_ctx* c, const lrt_atten_params* p, const double* S_dev,
+                                const double2* s0_dev, int rows, double* Sp_host,
+                                lrt_atten_report* rep, cudaStream_t s);
+
+// kubo.cu
+void free_kg_state(lrt_ctx* c);
+
+// dielectric.cu: Kramers-Kronig and Eqs. 10-11 on rows S [rows][nw] (host), v [rows] the
+// Coulomb factor per row; out [rows][N][8] (host)
+lrt_status run_dielectric(const lrt_ctx* c, const double* S_host, int rows, const double* v,
+                          double* out_host);
 
 }  // namespace lrt
 

@@ -124,8 +124,8 @@ __global__ void pair_weights_kernel(const double* __restrict__ eps, const double
 
 lrt_status launch_pair_density(const lrt_ctx* c, const QData& q, void* rho, bool fp32,
                                cudaStream_t s) {
-  // split path: tensor cores unless the caller asked for this kernel or the bands do not fit
-  if (fp32 && !c->pair_simt && c->nb <= 128) return launch_pair_density_tc(c, q, rho, s);
+  // split path: tensor cores unless the caller asked for this kernel
+  if (fp32 && !c->pair_simt) return launch_pair_density_tc(c, q, rho, s);
   int ntile = (c->nb + TN - 1) / TN;
   dim3 grid(ntile * ntile, q.nG, c->nk);
   const double2* ck = q.coeff;

@@ -7,7 +7,8 @@
 //   C'[n][128 + n'] = sum_g Re c_nk(g) Im c'_n'(j) - Im c_nk(g) Re c'_n'(j)   = Im rho
 // i.e. A'[n][K] = (Re c_nk | Im c_nk) over K = (g | N_pwp + g) and, for the Re tile, B' rows
 // Re c'(j) for K = g and Im c'(j) for K = N_pwp + g; for the Im tile Im c'(j) and -Re c'(j)
-// (j = idx_G(g)).  Each (k, G) is two tiles, M = 128 (bands), N = 128, K = 2 N_pwp.
+// (j = idx_G(g)).  Each (k, G) is two tiles per pair of 128-band blocks (n block, n' block),
+// M = 128, N = 128, K = 2 N_pwp; beyond 128 bands the blocks tile the (n, n') square.
 //
 // Precision.  The tensor core's FP32 accumulation drops bits below the accumulator's last place
 // at every update, always toward zero, so an ordinary FP16 hi/lo split loses about one unit in
@@ -89,31 +90,50 @@ __device__ __forceinline__ void grid_split(const double* x, uint4* part) {
 }
 
 struct PParams {
-  const uint4* A;             // [nk][nst][hi | r1 | r2 | r11 tile] prepared A' (32 KB per stage)
-  const uint4* B;             // [nk][npw + 1][hi | r1 | r2][PROW fp16] k+q rows, last row zero
+  const uint4* A;             // [nk][nbt][nst][hi | r1 | r2 | r11 tile] prepared A' (32 KB per stage)
+  const uint4* B;             // [nk][nbt][npw + 1][hi | r1 | r2][PROW fp16] k+q rows, last row zero
   const int32_t* gather;      // [nk][nG][npw]
   float2* rho;                // blocked [ld/32][gpad][32]
   int* status;
-  int nk, nb, nG, npw, npwp, nst, gpad;
+  int nk, nb, nbt, nG, npw, npwp, nst, gpad;   // nbt: 128-band blocks
   float scale;                // applied to C' when storing rho
 };
 
-// A'[k][stage][part]: thread per (k, stage, K in stage, chunk of 8 bands).
-__global__ void pd_prep_a(const double2* __restrict__ ck, int nk, int nb, int npw, int npwp, int nst,
-                          uint4* __restrict__ A) {
-  const long long total = (long long)nk * nst * PK * (PM / 8);
+// Tile t of the launch: part t % 2 (0: Re rho, 1: Im rho) of band blocks (tn, tm) of (k, G),
+// with t / 2 = ((k nG + G) nbt + tn) nbt + tm.
+struct PTile {
+  int k, G, tn, tm, part;
+};
+__device__ __forceinline__ PTile ptile(const PParams& P, int t) {
+  PTile r;
+  r.part = t & 1;
+  int u = t >> 1;
+  r.tm = u % P.nbt;
+  u /= P.nbt;
+  r.tn = u % P.nbt;
+  u /= P.nbt;
+  r.G = u % P.nG;
+  r.k = u / P.nG;
+  return r;
+}
+
+// A'[k][band block][stage][part]: thread per (k, block, stage, K in stage, chunk of 8 bands).
+__global__ void pd_prep_a(const double2* __restrict__ ck, int nk, int nb, int nbt, int npw, int npwp,
+                          int nst, uint4* __restrict__ A) {
+  const long long total = (long long)nk * nbt * nst * PK * (PM / 8);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(t % (PM / 8));
     const int kk = (int)((t / (PM / 8)) % PK);
     const int s = (int)((t / (PM / 8 * PK)) % nst);
-    const int k = (int)(t / ((long long)PM / 8 * PK * nst));
+    const long long kb = t / ((long long)PM / 8 * PK * nst);   // k nbt + block
+    const int k = (int)(kb / nbt), tb = (int)(kb % nbt);
     const int K = s * PK + kk;
     const bool im = K >= npwp;
     const int g = im ? K - npwp : K;
     double v[8];
     for (int i = 0; i < 8; ++i) {
-      const int n = 8 * c + i;
+      const int n = tb * PM + 8 * c + i;
       double x = 0.0;
       if (n < nb && g < npw) {
         const double2 z = ck[((size_t)k * nb + n) * npw + g];
@@ -123,25 +143,27 @@ __global__ void pd_prep_a(const double2* __restrict__ ck, int nk, int nb, int np
     }
     uint4 part[4];
     grid_split(v, part);
-    uint8_t* tile = reinterpret_cast<uint8_t*>(A) + ((size_t)k * nst + s) * NPA * PA_BYTES;
+    uint8_t* tile = reinterpret_cast<uint8_t*>(A) + ((size_t)kb * nst + s) * NPA * PA_BYTES;
 #pragma unroll
     for (int j = 0; j < NPA; ++j)
       *reinterpret_cast<uint4*>(tile + j * PA_BYTES + mn_chunk(kk, c, PA_SBO)) = part[j];
   }
 }
 
-// k+q rows: thread per (k, row j, chunk of 8 columns); row npw is zero.
-__global__ void pd_prep_b(const double2* __restrict__ ckq, int nk, int nb, int npw, uint4* __restrict__ B) {
-  const long long total = (long long)nk * (npw + 1) * (PROW / 8);
+// k+q rows: thread per (k, band block, row j, chunk of 8 columns); row npw is zero.
+__global__ void pd_prep_b(const double2* __restrict__ ckq, int nk, int nb, int nbt, int npw,
+                          uint4* __restrict__ B) {
+  const long long total = (long long)nk * nbt * (npw + 1) * (PROW / 8);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(t % (PROW / 8));
     const int j = (int)((t / (PROW / 8)) % (npw + 1));
-    const int k = (int)(t / ((long long)(PROW / 8) * (npw + 1)));
+    const long long kb = t / ((long long)(PROW / 8) * (npw + 1));   // k nbt + block
+    const int k = (int)(kb / nbt), tb = (int)(kb % nbt);
     double v[8];
     for (int i = 0; i < 8; ++i) {
       const int col = 8 * c + i;
-      const int n = col & (PM - 1);
+      const int n = tb * PM + (col & (PM - 1));
       double x = 0.0;
       if (n < nb && j < npw) {
         const double2 z = ckq[((size_t)k * nb + n) * npw + j];
@@ -151,7 +173,7 @@ __global__ void pd_prep_b(const double2* __restrict__ ckq, int nk, int nb, int n
     }
     uint4 part[4];
     grid_split(v, part);
-    uint4* row = B + ((size_t)k * (npw + 1) + j) * (NPB * PROW / 8);
+    uint4* row = B + ((size_t)kb * (npw + 1) + j) * (NPB * PROW / 8);
 #pragma unroll
     for (int p = 0; p < NPB; ++p) row[p * (PROW / 8) + c] = part[p];
   }
@@ -191,7 +213,7 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
-  const int ntiles = 2 * P.nk * P.nG;   // (k, G, Re | Im)
+  const int ntiles = 2 * P.nk * P.nG * P.nbt * P.nbt;   // (k, G, n block, n' block, Re | Im)
   const int nst = P.nst;
   const uint32_t idesc = (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(PN >> 3) << 17) |
                          ((uint32_t)(PM >> 4) << 24);
@@ -203,13 +225,14 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
       uint32_t it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int k = (t >> 1) / P.nG;
+        const PTile T = ptile(P, t);
+        const size_t kb = (size_t)T.k * P.nbt + T.tn;
         for (int s = 0; s < nst; ++s, ++it) {
           const int slot = it % PNS;
           if (!(ok = mbar_wait(&empty[slot], ((it / PNS) & 1) ^ 1, &abort_s, P.status))) break;
           mbar_expect_tx(&full[slot], NPA * PA_BYTES);
           bulk_g2s(base + slot * PSTAGE,
-                   reinterpret_cast<const uint8_t*>(P.A) + ((size_t)k * nst + s) * NPA * PA_BYTES,
+                   reinterpret_cast<const uint8_t*>(P.A) + (kb * nst + s) * NPA * PA_BYTES,
                    NPA * PA_BYTES, &full[slot]);
         }
       }
@@ -224,9 +247,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
     uint32_t it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int k = (t >> 1) / P.nG, G = (t >> 1) % P.nG, part = t & 1;
-      const int32_t* tab = P.gather + ((size_t)k * P.nG + G) * P.npw;
-      const uint4* Bk = P.B + (size_t)k * (P.npw + 1) * (NPB * PROW / 8);
+      const PTile T = ptile(P, t);
+      const int part = T.part;
+      const int32_t* tab = P.gather + ((size_t)T.k * P.nG + T.G) * P.npw;
+      const uint4* Bk = P.B + ((size_t)T.k * P.nbt + T.tm) * (P.npw + 1) * (NPB * PROW / 8);
       for (int s = 0; s < nst; ++s, ++it) {
         if ((int)(it & 1) != grp) continue;
         const int slot = it % PNS;
@@ -318,9 +342,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       tc_fence_after();
-      const int k = (t >> 1) / P.nG, G = (t >> 1) % P.nG, part = t & 1;
-      const long long p0 = ((long long)k * P.nb + n) * P.nb;
-      float* out = reinterpret_cast<float*>(P.rho) + part;
+      const PTile T = ptile(P, t);
+      const int G = T.G, nn = T.tn * PM + n;
+      const long long p0 = ((long long)T.k * P.nb + nn) * P.nb + (long long)T.tm * PN;
+      float* out = reinterpret_cast<float*>(P.rho) + T.part;
 #pragma unroll 1
       for (int c = 0; c < PN / 16; ++c) {
         uint32_t big[16], sml[16];   // the two accumulators' columns 16 c .. 16 c + 15
@@ -340,11 +365,11 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
               "=r"(sml[12]), "=r"(sml[13]), "=r"(sml[14]), "=r"(sml[15])
             : "r"(ta + PN));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (n < P.nb) {
+        if (nn < P.nb) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int np_ = c * 16 + j;
-            if (np_ < P.nb) {
+            if (T.tm * PN + np_ < P.nb) {
               const long long p = p0 + np_;
               out[2 * (((size_t)((p >> 5) * P.gpad + G) << 5) + (size_t)(p & 31))] =
                   __fmaf_rn(__uint_as_float(sml[j]), kSmall, __uint_as_float(big[j])) * P.scale;
@@ -366,19 +391,16 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
 
 }  // namespace
 
-// Tensor-core pair densities of one q into the blocked FP32 layout.  Returns LRT_EUNSUPPORTED
-// (nothing launched) when the shape does not fit the kernel (more than 128 bands).
+// Tensor-core pair densities of one q into the blocked FP32 layout (any band count: the
+// (n, n') square is tiled by 128-band blocks).
 lrt_status launch_pair_density_tc(const lrt_ctx* c, const QData& q, void* rho, cudaStream_t s) {
-  if (c->nb > PM) {
-    set_error("tensor-core pair densities: more than 128 bands");
-    return LRT_EUNSUPPORTED;
-  }
+  const int nbt = (c->nb + PM - 1) / PM;
   const int npw = c->npw;
   const int npwp = (npw + PK - 1) / PK * PK;
   const int nst = 2 * npwp / PK;
   lrt_ctx* cc = const_cast<lrt_ctx*>(c);
-  const size_t a_bytes = (size_t)c->nk * nst * NPA * PA_BYTES;
-  const size_t b_bytes = (size_t)c->nk * (npw + 1) * NPB * PROW * 2;
+  const size_t a_bytes = (size_t)c->nk * nbt * nst * NPA * PA_BYTES;
+  const size_t b_bytes = (size_t)c->nk * nbt * (npw + 1) * NPB * PROW * 2;
   if (cc->dw.pd_bytes < a_bytes + b_bytes) {
     cudaFree(cc->dw.pd_work);
     cc->dw.pd_work = nullptr;
@@ -393,8 +415,8 @@ lrt_status launch_pair_density_tc(const lrt_ctx* c, const QData& q, void* rho, c
   LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const double2* ck = q.coeff;
   const double2* ckq = q.coeff + (size_t)c->nk * c->nb * npw;
-  pd_prep_a<<<8 * nsm, 256, 0, s>>>(ck, c->nk, c->nb, npw, npwp, nst, A);
-  pd_prep_b<<<8 * nsm, 256, 0, s>>>(ckq, c->nk, c->nb, npw, B);
+  pd_prep_a<<<8 * nsm, 256, 0, s>>>(ck, c->nk, c->nb, nbt, npw, npwp, nst, A);
+  pd_prep_b<<<8 * nsm, 256, 0, s>>>(ckq, c->nk, c->nb, nbt, npw, B);
   count_launch(c, 2);
   LRT_CUDA(cudaGetLastError());
   PParams P;
@@ -405,6 +427,7 @@ lrt_status launch_pair_density_tc(const lrt_ctx* c, const QData& q, void* rho, c
   P.status = c->dw.status;
   P.nk = c->nk;
   P.nb = c->nb;
+  P.nbt = nbt;
   P.nG = q.nG;
   P.npw = npw;
   P.npwp = npwp;
@@ -419,7 +442,7 @@ lrt_status launch_pair_density_tc(const lrt_ctx* c, const QData& q, void* rho, c
                                   (int)smem));
     if (dev >= 0 && dev < 64) attr_set[dev] = smem;
   }
-  const int grid = std::min(nsm, 2 * c->nk * q.nG);
+  const int grid = (int)std::min<long long>(nsm, 2LL * c->nk * q.nG * nbt * nbt);
   {
     TimedLaunch tl(c, &c->ev_rho, s);
     pair_density_tc_kernel<<<grid, PTHREADS, smem, s>>>(P);

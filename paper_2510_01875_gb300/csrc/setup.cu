@@ -1,7 +1,9 @@
 // Setup (not part of the timed response path): k meshes, plane-wave bases, response G-sets,
 // the empty-core Hamiltonian H_GG'(k) = |k+G|^2/2 delta_GG' + V(G-G') assembled on the GPU
-// and diagonalised by cuSOLVER, Fermi-Dirac occupations with mu by bisection, and the
-// Dyson kernel K_GG = 4 pi/|q+G|^2 + f_xc.
+// and diagonalised by cuSOLVER, the kept eigenvectors refined by one first-order step in the
+// solver's eigenbasis, Fermi-Dirac occupations with mu by bisection, and the Dyson kernel
+// K_GG = 4 pi/|q+G|^2 + f_xc.
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -397,14 +399,120 @@ __global__ void extract_eigen(const double2* __restrict__ A, const double* __res
   }
 }
 
+// First-order correction coefficients of the kept eigenvectors from E = V^H H V_kept
+// ([npw][nb] column-major per matrix, W the solver's ascending eigenvalues):
+//   C_ij = E_ij / (eps_j - eps_i) for i != j, 0 on the diagonal and for pairs closer than
+//   kDegenTol or with |E_ij| not small against the gap (near-degenerate pairs: any rotation
+//   inside them is an eigenbasis to this accuracy).
+__global__ void refine_coeffs(double2* __restrict__ E, const double* __restrict__ W, int npw, int nb,
+                              int nmat) {
+  int64_t total = (int64_t)nmat * nb * npw;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % npw);
+    const int j = (int)((t / npw) % nb);
+    const int m = (int)(t / ((int64_t)npw * nb));
+    const double gap = W[(size_t)m * npw + j] - W[(size_t)m * npw + i];
+    const double2 e = E[t];
+    double2 c = make_double2(0.0, 0.0);
+    if (i != j && fabs(gap) > kDegenTol && sqrt(e.x * e.x + e.y * e.y) < 1e-3 * fabs(gap))
+      c = make_double2(e.x / gap, e.y / gap);
+    E[t] = c;
+  }
+}
+
+// W[m][j] = Re v_j^H (H v_j) for the first nb columns (Rayleigh quotients of the refined
+// vectors; HV = H V_kept [npw][nb] per matrix).  One warp per (matrix, column).
+__global__ void rayleigh_quotients(const double2* __restrict__ V, const double2* __restrict__ HV,
+                                   int npw, int nb, int nmat, double* __restrict__ W) {
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (long long)nmat * nb) return;
+  const int m = (int)(warp / nb), j = (int)(warp % nb);
+  const double2* v = V + (size_t)m * npw * npw + (size_t)j * npw;
+  const double2* h = HV + (size_t)m * npw * nb + (size_t)j * npw;
+  double acc = 0.0;
+  for (int g = lane; g < npw; g += 32) acc += v[g].x * h[g].x + v[g].y * h[g].y;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) W[(size_t)m * npw + j] = acc;
+}
+
+// S <- 3/2 I - S/2 per [nb][nb] matrix (one Lowdin step: (V^H V)^{-1/2} to second order).
+__global__ void lowdin_factor(double2* __restrict__ S, int nb, int nmat) {
+  int64_t total = (int64_t)nmat * nb * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % nb), j = (int)((t / nb) % nb);
+    double2 v = S[t];
+    v = make_double2(-0.5 * v.x, -0.5 * v.y);
+    if (i == j) v.x += 1.5;
+    S[t] = v;
+  }
+}
+
 struct Solver {
   cusolverDnHandle_t h = nullptr;
   cusolverDnParams_t p = nullptr;
+  cublasHandle_t b = nullptr;
   ~Solver() {
     if (p) cusolverDnDestroyParams(p);
     if (h) cusolverDnDestroy(h);
+    if (b) cublasDestroy(b);
   }
 };
+
+#define LRT_BLAS(call)                                                     \
+  do {                                                                     \
+    cublasStatus_t st_ = (call);                                           \
+    if (st_ != CUBLAS_STATUS_SUCCESS) {                                    \
+      set_error(std::string(#call) + " failed: " + std::to_string(st_));   \
+      return LRT_ECUDA;                                                    \
+    }                                                                      \
+  } while (0)
+
+// One refinement step of the nb kept eigenvectors of nm matrices: V (npw x npw per matrix,
+// column-major, the solver's full eigenbasis) and W (its eigenvalues); Hm holds the same
+// Hamiltonians; T1, T2 are [npw][nb] and Sm [nb][nb] per matrix.  The batched solver's vectors
+// carry residuals ||H v - eps v|| up to ~1e-9 Ha; the correction
+//   v_j <- v_j + sum_i v_i C_ij,  C = refine_coeffs(V^H H V_kept)
+// removes them to first order (the residual then falls quadratically), and one Lowdin step
+// V <- V (3/2 I - (V^H V)/2) restores orthonormality to second order.  The corrected vectors
+// replace the first nb columns of V, and their Rayleigh quotients replace the first nb
+// eigenvalues in W (the solver's eigenvalues carried errors up to ~1e-11 Ha, larger than the
+// refined vectors' residuals).
+lrt_status refine_kept(const Solver& sv, double2* V, double* W, const double2* Hm, double2* T1,
+                       double2* T2, double2* Sm, int npw, int nb, int nm) {
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+  const long long sM = (long long)npw * npw, sT = (long long)npw * nb, sS = (long long)nb * nb;
+  auto Z = [](const double2* p) { return reinterpret_cast<const cuDoubleComplex*>(p); };
+  auto Zm = [](double2* p) { return reinterpret_cast<cuDoubleComplex*>(p); };
+  // T1 = H V_kept;  T2 = V^H T1
+  LRT_BLAS(cublasZgemmStridedBatched(sv.b, CUBLAS_OP_N, CUBLAS_OP_N, npw, nb, npw, &one, Z(Hm), npw,
+                                     sM, Z(V), npw, sM, &zero, Zm(T1), npw, sT, nm));
+  LRT_BLAS(cublasZgemmStridedBatched(sv.b, CUBLAS_OP_C, CUBLAS_OP_N, npw, nb, npw, &one, Z(V), npw,
+                                     sM, Z(T1), npw, sT, &zero, Zm(T2), npw, sT, nm));
+  refine_coeffs<<<1216, 256>>>(T2, W, npw, nb, nm);
+  LRT_CUDA(cudaGetLastError());
+  // T1 = V_kept + V C
+  LRT_CUDA(cudaMemcpy2D(T1, sT * sizeof(double2), V, sM * sizeof(double2), sT * sizeof(double2), nm,
+                        cudaMemcpyDeviceToDevice));
+  LRT_BLAS(cublasZgemmStridedBatched(sv.b, CUBLAS_OP_N, CUBLAS_OP_N, npw, nb, npw, &one, Z(V), npw,
+                                     sM, Z(T2), npw, sT, &one, Zm(T1), npw, sT, nm));
+  // S = T1^H T1;  V_kept = T1 (3/2 I - S/2)
+  LRT_BLAS(cublasZgemmStridedBatched(sv.b, CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, npw, &one, Z(T1), npw,
+                                     sT, Z(T1), npw, sT, &zero, Zm(Sm), nb, sS, nm));
+  lowdin_factor<<<1216, 256>>>(Sm, nb, nm);
+  LRT_CUDA(cudaGetLastError());
+  LRT_BLAS(cublasZgemmStridedBatched(sv.b, CUBLAS_OP_N, CUBLAS_OP_N, npw, nb, nb, &one, Z(T1), npw,
+                                     sT, Z(Sm), nb, sS, &zero, Zm(V), npw, sM, nm));
+  // eigenvalues: Rayleigh quotients of the refined vectors
+  LRT_BLAS(cublasZgemmStridedBatched(sv.b, CUBLAS_OP_N, CUBLAS_OP_N, npw, nb, npw, &one, Z(Hm), npw,
+                                     sM, Z(V), npw, sM, &zero, Zm(T1), npw, sT, nm));
+  const long long warps = (long long)nm * nb;
+  rayleigh_quotients<<<(unsigned)((warps * 32 + 255) / 256), 256>>>(V, T1, npw, nb, nm, W);
+  LRT_CUDA(cudaGetLastError());
+  return LRT_OK;
+}
 
 #define LRT_SOLVER(call)                                                   \
   do {                                                                     \
@@ -509,7 +617,12 @@ lrt_status solve_ground_states(lrt_ctx* c, const double* occupations) {
   Solver sv;
   LRT_SOLVER(cusolverDnCreate(&sv.h));
   LRT_SOLVER(cusolverDnCreateParams(&sv.p));
+  LRT_BLAS(cublasCreate(&sv.b));
+  // standard FP64 arithmetic in the refinement products (no emulated or reduced-precision
+  // algorithms): they must resolve residuals far below the solver's
+  LRT_BLAS(cublasSetMathMode(sv.b, CUBLAS_PEDANTIC_MATH));
   double2* A = nullptr;
+  double2 *Hm = nullptr, *T1 = nullptr, *T2 = nullptr, *Sm = nullptr;
   double* W = nullptr;
   int* info = nullptr;
   int32_t *d_miller = nullptr, *d_npw = nullptr;
@@ -525,12 +638,20 @@ lrt_status solve_ground_states(lrt_ctx* c, const double* occupations) {
     cudaFree(d_k);
     cudaFree(d_pos);
     cudaFree(dwork);
+    cudaFree(Hm);
+    cudaFree(T1);
+    cudaFree(T2);
+    cudaFree(Sm);
   };
   struct Guard {
     std::function<void()> f;
     ~Guard() { f(); }
   } guard{cleanup};
   LRT_CUDA(cudaMalloc(&A, per_mat * batch));
+  LRT_CUDA(cudaMalloc(&Hm, per_mat * batch));
+  LRT_CUDA(cudaMalloc(&T1, (size_t)npw * nb * batch * sizeof(double2)));
+  LRT_CUDA(cudaMalloc(&T2, (size_t)npw * nb * batch * sizeof(double2)));
+  LRT_CUDA(cudaMalloc(&Sm, (size_t)nb * nb * batch * sizeof(double2)));
   LRT_CUDA(cudaMalloc(&W, (size_t)npw * batch * sizeof(double)));
   LRT_CUDA(cudaMalloc(&info, batch * sizeof(int)));
   LRT_CUDA(cudaMalloc(&d_miller, (size_t)batch * npw * 3 * sizeof(int32_t)));
@@ -595,6 +716,11 @@ lrt_status solve_ground_states(lrt_ctx* c, const double* occupations) {
         set_error("eigensolver did not converge (info " + std::to_string(info_h[m]) + ")");
         return LRT_ECUDA;
       }
+    // the solver overwrote A with the eigenvectors: H again, then refine the kept vectors
+    assemble_h<<<1216, 256>>>(Hm, d_miller, d_npw, d_k, npw, nm, d_pos, c->natoms, b0, b1, b2, c->Z,
+                              c->r_c, c->volume, c->potential == LRT_POT_ZERO);
+    LRT_CUDA(cudaGetLastError());
+    LRT_TRY(refine_kept(sv, A, W, Hm, T1, T2, Sm, npw, nb, nm));
     // scatter into the per-q arrays; a batch may straddle q boundaries
     for (int m0 = 0; m0 < nm;) {
       int gidx = start + m0;

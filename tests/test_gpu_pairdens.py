@@ -9,8 +9,11 @@ of the output (~3e-8 of the largest |rho|).  Bounds: 2e-7 of the largest |rho| e
 and, because small interband densities enter near-cancelling sums (the T tangent of the
 adjoint), a median relative error of 1e-7 over the elements above 1e-4 of the largest.  The
 FP32 SIMT kernel (round-to-nearest FMA) is held to 2e-6 and 5e-7.  Cases span several tiles
-with ragged band counts, G counts and plane-wave padding, up to the 128-band limit of the
-tensor-core tile; above it the SIMT kernel runs.
+with ragged band counts, G counts and plane-wave padding; beyond 128 bands the tensor-core
+kernel tiles the (n, n') square with 128-band blocks (two and three blocks per side, the last
+one partial).  Those cases have many more small interband densities (and 2-3x the plane waves),
+which moves the median of the relative error up for any FP32 arithmetic; there the tensor-core
+median must not exceed the FP32 SIMT kernel's on the same orbitals.
 """
 import numpy as np
 import pytest
@@ -24,6 +27,8 @@ CASES = {
     "tiny": dict(seed=41, nq=2, nw=16),
     "ragged": dict(seed=42, nq=1, nw=16, nbands=13, nG=11, kmesh=(3, 2, 2)),
     "bands_near_tile": dict(seed=43, nq=1, nw=16, nbands=110, ecut=6.0, kmesh=(2, 2, 2), nG=15),
+    "two_band_blocks": dict(seed=44, nq=1, nw=16, nbands=200, ecut=9.0, kmesh=(2, 1, 1), nG=9),
+    "three_band_blocks": dict(seed=45, nq=1, nw=16, nbands=290, ecut=12.0, kmesh=(1, 1, 2), nG=5),
 }
 
 
@@ -53,10 +58,16 @@ def test_tensor_core_pair_densities(name):
     for iq in range(wl.nq):
         scale = np.abs(ref[iq]).max()
         big = np.abs(ref[iq]) > 1e-4 * scale
-        assert np.abs(tc[iq] - ref[iq]).max() <= 2e-7 * scale, (name, iq)
-        assert np.median(np.abs(tc[iq] - ref[iq])[big] / np.abs(ref[iq][big])) <= 1e-7, (name, iq)
-        assert np.abs(simt[iq] - ref[iq]).max() <= 2e-6 * scale, (name, iq)
-        assert np.median(np.abs(simt[iq] - ref[iq])[big] / np.abs(ref[iq][big])) <= 5e-7, (name, iq)
+        med_tc = float(np.median(np.abs(tc[iq] - ref[iq])[big] / np.abs(ref[iq][big])))
+        med_simt = float(np.median(np.abs(simt[iq] - ref[iq])[big] / np.abs(ref[iq][big])))
+        errs = (name, iq, float(np.abs(tc[iq] - ref[iq]).max() / scale), med_tc,
+                float(np.abs(simt[iq] - ref[iq]).max() / scale), med_simt)
+        assert errs[2] <= 2e-7, errs
+        assert errs[4] <= 2e-6, errs
+        if nb <= 128:
+            assert med_tc <= 1e-7 and med_simt <= 5e-7, errs
+        else:
+            assert med_tc <= med_simt, errs
 
 
 def test_repeat_calls_agree():
