@@ -237,10 +237,10 @@ def run_ours(args, world, rank, local, pg):
     # roofline of the dominant kernel (the chi0 contraction)
     peaks, src = measured_peaks()
     if args.precision == "fp64":
-        bound, unit = "alu", "TFLOP/s"
+        bound, unit = "fp64", "TFLOP/s"
         flops_per_cmac = 4.0
-        peak = peaks.get("fp64_tflops", 1.25)
-        peak_note = "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+        peak = binding.measure_fp64(local)
+        peak_note = "measured: FP64 FMA loop on every SM (lrtddft_measure_fp64)"
     else:
         bound, unit = "tensor", "TFLOP/s"
         flops_per_cmac = 12.0      # 2 real MACs per complex MAC (Hermitian split) x 3 products
@@ -276,7 +276,7 @@ def run_ours(args, world, rank, local, pg):
     extras = {}
     if not args.no_extras and rank == 0:
         try:
-            extras = run_extras(args, ctx, wl)
+            extras = run_extras(args, ctx, wl, S.cpu().numpy(), F.cpu().numpy())
         except Exception as exc:
             extras = {"extras_error": repr(exc)}
     ctx.close()
@@ -345,40 +345,56 @@ def run_e2e(ctx, wl, args, cmac_step, pg, world):
     h2d = sum(c.numel() * 8 + e.numel() * 8 + o.numel() * 8 for c, e, o in zip(coeff, eps, occ))
     d2h = (wl.nq * wl.nw * 8) * 2 + wl.nq * wl.ntau * 8 + wl.nq * 5 * 8
 
-    def step():
+    def upload():
         for iq in range(wl.nq):
-            ctx.set_orbitals(iq, eps[iq].numpy(), coeff[iq].numpy().view(np.complex128), occ[iq].numpy())
-        ctx.chi0_assemble()
-        ctx.dyson_solve()
-        S = ctx.dsf()
-        F, m = ctx.itcf(tau)
-        Sp, _ = ctx.attenuate(params)
+            ctx.set_orbitals_async(iq, eps[iq].numpy(), coeff[iq].numpy().view(np.complex128).reshape(2, nk, nb, npw),
+                                   occ[iq].numpy())
+
+    def steps(n):
+        # pipelined: the first step's inputs are copied before it, every later step's while the
+        # step before it runs its contraction (the copies of all n steps are in the region)
+        upload()
+        for i in range(n):
+            ctx.chi0_assemble()          # waits for this step's copies
+            if i + 1 < n:
+                upload()
+            ctx.dyson_solve()
+            S = ctx.dsf()
+            F, m = ctx.itcf(tau)
+            Sp, _ = ctx.attenuate(params)
         return S, F, m, Sp
 
-    step()
+    steps(1)
     torch.cuda.synchronize()
     barrier(pg)
     t0 = time.perf_counter()
-    n = max(1, min(args.steps, 2))
-    for _ in range(n):
-        step()
+    n = max(1, min(args.steps, 3))
+    steps(n)
     torch.cuda.synchronize()
     barrier(pg)
     dt = (time.perf_counter() - t0) / n
     dt = max_over_ranks(pg, dt)
     return {"value": sum_over_ranks(pg, cmac_step) / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": n}
+            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": n,
+            "pipeline": "orbitals of step i+1 copied from pinned host memory during step i's "
+                        "contraction (lrtddft_set_orbitals_async); step 1's before it, in the region"}
 
 
-def run_extras(args, ctx_main, wl):
-    """FP64 form on a slice (1 q, 64 frequencies) beside the split form, and the split form's
-    error against the FP64 form at the timed workload's shape on a 4^3 k mesh."""
+def run_extras(args, ctx_main, wl, S_direct, F_direct):
+    """The spectral chi0 engine on the timed workload against the direct engine's S and F of the
+    timed steps; the FP64 form on a slice (1 q, 63 frequencies) beside the split form; the split
+    form's error against the FP64 form at the timed workload's shape on a 4^3 k mesh; the eta
+    scan; the CPU oracle."""
     from paper_2510_01875_gb300 import binding
     from paper_2510_01875_gb300 import workloads as W
     out = {}
-    # slice: q[0], 64 frequencies from 15 eV (two whole 32-frequency tiles of the FP64 kernel)
+    if args.precision != "fp64":
+        out["spectral_engine"] = spectral_extra(ctx_main, wl, S_direct, F_direct)
+    # slice: q[0], 63 frequencies from 15 eV; with the w = 0 column that S(q,0) needs they fill
+    # one whole 64-frequency tile of the FP64 kernel, as the 1025 columns of the full grid
+    # nearly fill 17
     j0 = int(np.searchsorted(wl.omega, W.ev(15.0)))
-    sl = wl.replace(q=wl.q[:1], nG=wl.nG[:1], omega=wl.omega[j0:j0 + 64])
+    sl = wl.replace(q=wl.q[:1], nG=wl.nG[:1], omega=wl.omega[j0:j0 + 63])
     forms = {}
     for prec in ("fp64", args.precision if args.precision != "fp64" else "fp16x3"):
         c = binding.Context(sl, prec)
@@ -402,14 +418,14 @@ def run_extras(args, ctx_main, wl):
                                                     "of the SIMT FP64 kernel), lrtddft_measure_fp64"},
                         "dgemm_peak": {"tflops": peak64["tflops"], "frac": tf64 / peak64["tflops"],
                                        "how": peak64["how"]},
-                        "sample": f"1 q, 64 frequencies (15-25 eV), all {ctx_main.nk * ctx_main.nb ** 2:.3g} "
+                        "sample": f"1 q, 63 frequencies (15-25 eV) and w = 0, all {ctx_main.nk * ctx_main.nb ** 2:.3g} "
                                   "pairs; the rate is set by the pair sum, so it extrapolates "
                                   "linearly to the full workload",
                         "split_rate_same_slice": sp["cmac"] / (sp["ms"] / 1e3),
                         "split_vs_fp64_chi0_err": err}
     # accuracy of the split form against the FP64 form at the shape of the timed workload
     # (same cell, 120 bands, 59 G, 1024 frequencies, T, eta), smallest and largest |q|, on a
-    # 4^3 k mesh (the FP64 form is about 37 s per q there)
+    # 4^3 k mesh (the FP64 form takes tens of seconds per q there)
     acc = wl.replace(kmesh=(4, 4, 4), q=wl.q[[0, wl.nq - 1]], nG=wl.nG[[0, wl.nq - 1]],
                      name=wl.name.replace("k12", "k4").replace(f"q{wl.nq}", "q2"))
     res = {}
@@ -443,6 +459,41 @@ def run_extras(args, ctx_main, wl):
     out["eta_scan"] = eta_scan_extra(args, wl)
     out["cpu_baseline"] = cpu_baseline(wl)
     return out
+
+
+def spectral_extra(ctx, wl, S_direct, F_direct, order=3, hdiv=16):
+    """All q of the timed workload through the spectral chi0 engine (bin width eta/hdiv,
+    Lagrange order 3; same context, orbitals and split precision), Dyson, S and F, device-timed
+    after one untimed pass, against the direct engine's S and F of the timed steps."""
+    tau = np.linspace(0.0, 0.5 / wl.T, wl.ntau)
+    chi_direct = ctx.get_chi0(0)
+    h = wl.eta / hdiv
+    ctx.set_spectral(h, order)
+
+    def fwd():
+        ctx.chi0_assemble()
+        ctx.dyson_solve()
+        return ctx.dsf(), ctx.itcf(tau)[0]
+
+    fwd()
+    ms, (S, F) = _timed(fwd)
+    chi = ctx.get_chi0(0)
+    grids = [ctx.get_spectral_grid(i) for i in range(wl.nq)]
+    ctx.set_spectral(0.0)
+    pk = []
+    for i in range(wl.nq):
+        Sa = S_direct[i]
+        pk += [abs(S[i][j] / Sa[j] - 1) for j in range(1, wl.nw - 1)
+               if Sa[j] > Sa[j - 1] and Sa[j] >= Sa[j + 1] and Sa[j] > 0.1 * Sa.max()]
+    return {"h_eV": h * 27.211386245988, "order": order, "bins_per_q": [int(g[1]) for g in grids],
+            "ms_per_step": ms, "q_spectra_per_s": wl.nq / (ms / 1e3),
+            "timed": "chi0_assemble (spectral) + dyson_solve + dsf + itcf for all q",
+            "vs_direct_engine": {
+                "chi0_maxnorm_rel_q0": float(np.abs(chi - chi_direct).max() / np.abs(chi_direct).max()),
+                "S_maxnorm_rel": float(max(np.abs(S[i] - S_direct[i]).max() / np.abs(S_direct[i]).max()
+                                           for i in range(wl.nq))),
+                "S_peak_rel": float(max(pk)) if pk else None,
+                "F_pointwise_rel": float(np.abs(F / F_direct - 1).max())}}
 
 
 def eta_scan_extra(args, wl, n_eta=8, tol=5e-3):

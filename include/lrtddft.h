@@ -173,24 +173,51 @@ lrt_status lrtddft_itcf_laplace_device(lrt_ctx* ctx, int ntau, const double* tau
 /* ---- Scheduling of the tensor-core contraction (FP16X3 / BF16X3; no effect on FP64).
  * chi0_assemble runs all requested q in one persistent launch when their pair densities fit
  * next to each other in device memory (q of different N_G mix freely: the launch walks a list
- * of (q, row super-tile pair, column tile, pair range) units); otherwise q by q.  Each unit
- * covers a fixed number of 32-pair stages ("unit size"), and two kernel variants differ in
- * their shared-memory ring depths (0: 4 operand / 2 prefetch stages, 1: 3 / 4).
- *   flags: LRT_TUNE_AUTO      time each (variant, unit size) candidate on the first units of
- *                             the first launch of each shape and keep the fastest (results
- *                             then differ from the defaults at the rounding of the split form);
+ * of (q, row unit, column tile, pair range) units); otherwise q by q.  A row unit is 512 rows
+ * of the Hermitian-split chi0 (256 per CTA of the pair, two accumulators each) or, as a half,
+ * 256 rows (128 per CTA); an odd last unit is always a half.  Each unit covers a fixed number
+ * of 32-pair stages ("unit size"), and two kernel variants differ in their shared-memory ring
+ * depths (0: 4 operand / 2 prefetch stages, 1: 3 / 4).
+ *   flags: LRT_TUNE_AUTO      time each (row unit shape, variant, unit size) candidate on the
+ *                             first units of the first launch of each shape and keep the
+ *                             fastest (results then differ from the defaults at the rounding
+ *                             of the split form);
  *          LRT_TUNE_SINGLE_Q  one launch per q;
  *          LRT_TUNE_PAIR_SIMT pair densities on the FP32 SIMT kernel instead of the tensor
  *                             cores;
  *          LRT_TUNE_FINE_ACCUM flush the FP32 tensor-core accumulators into the FP64 sums every
  *                             32 stages (1024 pairs) instead of 64: the FP32 accumulation
- *                             error, which grows with the period, halves.
+ *                             error, which grows with the period, halves;
+ *          LRT_TUNE_HALF_TILES every row unit a half (256 rows; more, smaller units).
  *   variant: -1 (tuned or default 0), 0 or 1;  unit_stages: 0 (tuned or default 4096) or a
  *   positive multiple of 64.  LRT_EINVAL otherwise.  Invalidates a captured graph. */
-enum { LRT_TUNE_AUTO = 1, LRT_TUNE_SINGLE_Q = 2, LRT_TUNE_PAIR_SIMT = 4, LRT_TUNE_FINE_ACCUM = 8 };
+enum { LRT_TUNE_AUTO = 1, LRT_TUNE_SINGLE_Q = 2, LRT_TUNE_PAIR_SIMT = 4, LRT_TUNE_FINE_ACCUM = 8,
+       LRT_TUNE_HALF_TILES = 16 };
 lrt_status lrtddft_set_tuning(lrt_ctx* ctx, int flags, int variant, int unit_stages);
 /* The variant and unit size used by the last tensor-core launch (-1 and 0 before any). */
 lrt_status lrtddft_get_tuning(lrt_ctx* ctx, int* variant, int* unit_stages);
+/* Rows of chi0 per full row unit of the last tensor-core launch: 512, or 256 when every unit
+ * was a half (0 before any). */
+lrt_status lrtddft_get_tile_rows(lrt_ctx* ctx, int* rows);
+
+/* ---- chi0 through a spectral function (an engine variant; the paper's method is the direct
+ * Adler-Wiser sum above).  With x_p = eps_n'k+q - eps_nk, every pole 1/(w - x_p + i eta) of
+ * the sum is replaced by its Lagrange interpolant of order `order` (1 or 3) in x_p on the grid
+ * x_b = x_0 + b h: A_b(G,G') = sum_p rho_p(G) rho_p*(G') df_p L_b(x_p) is formed once from the
+ * pairs sorted by bin, and chi0(w) = (2/(N_k Omega)) sum_b A_b / (w - x_b + i eta) for every
+ * frequency and every eta of a list is one GEMM over the bins.  The relative error is
+ * O((h/eta)^(order+1)) (order 3, h = eta/16: about 1e-6 of max |chi0|); the cost of the pair
+ * sum no longer grows with the number of frequencies.  Grid: over the pairs with df != 0,
+ * x_0 = h (floor(min x_p / h) - 1), n_b = floor((max x_p - x_0)/h) + 3.  The FP64 context sums
+ * in FP64 (cuBLAS DGEMM transform); the split contexts sum FP32 products with compensated FP32
+ * sums (SGEMM transform).  S(q,0) keeps its exact limit.  h = 0 selects the direct engine
+ * (the default).  Not with the adjoint or graph capture (LRT_EUNSUPPORTED there).  LRT_EINVAL
+ * for h < 0 or an order other than 1, 3; chi0_assemble returns LRT_EINVAL when the grid would
+ * exceed 2^26 bins. */
+lrt_status lrtddft_set_spectral(lrt_ctx* ctx, double h, int order);
+/* Grid of the last spectral assembly of q index iq: x_0 (Ha) and the number of bins (0 and 0
+ * before one, or when no pair carries weight). */
+lrt_status lrtddft_get_spectral_grid(const lrt_ctx* ctx, int iq, double* x0, long long* nbins);
 
 /* CUDA graph of the forward path for every q: chi0_assemble, dyson_solve, dsf_device and
  * itcf_laplace_device into the given device buffers (S_dev [nq][nw], F_dev [nq][ntau],
@@ -375,6 +402,18 @@ lrt_status lrtddft_measure_fp64(int device, double* tflops);
  * Host pointers. */
 lrt_status lrtddft_set_orbitals(lrt_ctx* ctx, int iq, const double* eps, const double* coeff,
                                 const double* occ);
+/* The same replacement, pipelined: the coefficients are copied on a stream of the context's own
+ * while earlier work runs, into a second set of orbital buffers (2 N_k N_b N_pw complex per q,
+ * allocated on first use), and take effect at the next call that uses the orbitals of iq
+ * (lrtddft_chi0_assemble over iq, whose stream then waits for the copy, or any call reading
+ * the ground state of iq); results of the current orbitals (chi0, chi, S, F, derivatives) stay
+ * valid until then.  eps and occ are read before the call returns.  coeff must stay unchanged
+ * until that adopting call's stream has passed it (e.g. until a later call returning results
+ * to the host has returned), and should be page-locked host memory for the copy to overlap
+ * kernels (pageable memory is copied correctly, without overlap).  A later lrtddft_set_orbitals
+ * of iq drops a pending upload.  Errors as lrtddft_set_orbitals.  Host pointers. */
+lrt_status lrtddft_set_orbitals_async(lrt_ctx* ctx, int iq, const double* eps, const double* coeff,
+                                      const double* occ);
 /* Orbital coefficients of q index iq: coeff [2][nk][nb][npw] complex (the layout
  * lrtddft_set_orbitals takes). */
 lrt_status lrtddft_get_orbitals(const lrt_ctx* ctx, int iq, double* coeff);

@@ -20,6 +20,7 @@ or fusion beyond what the definition states:
   etascan.py    the eta-convergence test in the imaginary-time domain (Sec. 2)
   dielectric.py chi, 1/eps, eps and sigma from a DSF (Kramers-Kronig, Eqs. 10-11)
   kubo.py       the Kubo-Greenwood route to the eta test and the filtered conductivity (App. A.3)
+  spectral.py   chi0 through a binned spectral function and its transform (engine variant)
   lindhard.py   continuum finite-temperature Lindhard function (pins only)
   adjoint.py    forward-mode tangents of S(q,w) and F(q,tau) for the gradient pins
   pipeline.py   runs the steps above for one workload

@@ -89,6 +89,9 @@ SIGNATURES = {
     "lrtddft_set_params": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(lrt_kernel)]),
     "lrtddft_set_tuning": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "lrtddft_get_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lrtddft_get_tile_rows": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "lrtddft_set_spectral": (C.c_int, [_P, C.c_double, C.c_int]),
+    "lrtddft_get_spectral_grid": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "lrtddft_graph_capture": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
     "lrtddft_graph_launch": (C.c_int, [_P, _P]),
     "lrtddft_jacobian": (C.c_int, [_P, C.c_int, _D, _D, _D]),
@@ -100,6 +103,7 @@ SIGNATURES = {
     "lrtddft_profile": (C.c_int, [_P, C.c_int]),
     "lrtddft_profile_read": (C.c_int, [_P, _D]),
     "lrtddft_set_orbitals": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "lrtddft_set_orbitals_async": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "lrtddft_get_orbitals": (C.c_int, [_P, C.c_int, _D]),
     "lrtddft_get_basis": (C.c_int, [_P, C.c_int, _I32, _I32]),
     "lrtddft_get_ground_state": (C.c_int, [_P, C.c_int, _D, _D, _D, _D]),
@@ -249,20 +253,37 @@ class Context:
             self.h, ntau, _P(tau_ptr), ITCF[mode], _P(F_ptr), _P(metrics_ptr), _P(stream)))
 
     def set_tuning(self, auto: bool = False, single_q: bool = False, variant: int = -1, unit_stages: int = 0,
-                   pair_simt: bool = False, fine_accum: bool = False):
-        """lrtddft_set_tuning: auto times the contraction's variants and unit sizes on the first
-        launch of each shape; single_q launches the contraction once per q; pair_simt computes
-        the split path's pair densities on the FP32 SIMT kernel instead of the tensor cores;
-        fine_accum halves the FP32 accumulation period (32 stages); variant (-1, 0, 1) and
-        unit_stages (0 or a multiple of 64) force a choice."""
+                   pair_simt: bool = False, fine_accum: bool = False, half_tiles: bool = False):
+        """lrtddft_set_tuning: auto times the contraction's row-unit shapes, variants and unit
+        sizes on the first launch of each shape; single_q launches the contraction once per q;
+        pair_simt computes the split path's pair densities on the FP32 SIMT kernel instead of
+        the tensor cores; fine_accum halves the FP32 accumulation period (32 stages);
+        half_tiles makes every row unit 256 rows; variant (-1, 0, 1) and unit_stages (0 or a
+        multiple of 64) force a choice."""
         flags = ((1 if auto else 0) | (2 if single_q else 0) | (4 if pair_simt else 0)
-                 | (8 if fine_accum else 0))
+                 | (8 if fine_accum else 0) | (16 if half_tiles else 0))
         _check("lrtddft_set_tuning", self.lib.lrtddft_set_tuning(self.h, flags, variant, unit_stages))
 
     def get_tuning(self):
         v, u = C.c_int(), C.c_int()
         _check("lrtddft_get_tuning", self.lib.lrtddft_get_tuning(self.h, C.byref(v), C.byref(u)))
         return v.value, u.value
+
+    def set_spectral(self, h: float, order: int = 3):
+        """lrtddft_set_spectral: chi0 through a spectral function on a grid of spacing h (Ha)
+        with Lagrange interpolation of the given order (1 or 3); h = 0 restores the direct sum."""
+        _check("lrtddft_set_spectral", self.lib.lrtddft_set_spectral(self.h, float(h), int(order)))
+
+    def get_spectral_grid(self, iq: int):
+        x0, nb = C.c_double(), C.c_longlong()
+        _check("lrtddft_get_spectral_grid", self.lib.lrtddft_get_spectral_grid(
+            self.h, iq, C.byref(x0), C.byref(nb)))
+        return x0.value, nb.value
+
+    def get_tile_rows(self) -> int:
+        r = C.c_int()
+        _check("lrtddft_get_tile_rows", self.lib.lrtddft_get_tile_rows(self.h, C.byref(r)))
+        return r.value
 
     def graph_capture(self, ntau: int, tau_ptr: int, S_ptr: int, F_ptr: int, metrics_ptr: int, mode="fold"):
         _check("lrtddft_graph_capture", self.lib.lrtddft_graph_capture(
@@ -401,6 +422,18 @@ class Context:
         oc = None if occ is None else np.ascontiguousarray(occ, dtype=np.float64)
         _check("lrtddft_set_orbitals", self.lib.lrtddft_set_orbitals(
             self.h, iq, _dp(eps), cf.ctypes.data_as(_D), None if oc is None else _dp(oc)))
+
+    def set_orbitals_async(self, iq: int, eps: np.ndarray, coeff: np.ndarray,
+                           occ: Optional[np.ndarray] = None):
+        """Pipelined set_orbitals: coeff (ideally page-locked, e.g. a pinned torch tensor's
+        numpy view) is copied while earlier work runs and must stay unchanged until the next
+        chi0_assemble of iq has been followed by a call that returns results."""
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        if coeff.dtype != np.complex128 or not coeff.flags.c_contiguous:
+            raise ValueError("coeff must be a C-contiguous complex128 array (it is read after the call)")
+        oc = None if occ is None else np.ascontiguousarray(occ, dtype=np.float64)
+        _check("lrtddft_set_orbitals_async", self.lib.lrtddft_set_orbitals_async(
+            self.h, iq, _dp(eps), coeff.ctypes.data_as(_D), None if oc is None else _dp(oc)))
 
     def get_orbitals(self, iq: int, out: Optional[np.ndarray] = None) -> np.ndarray:
         if out is None:

@@ -43,7 +43,19 @@ void free_ctx(lrt_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   free_tc_state(c);
   free_kg_state(c);
+  free_spectral_state(c);
+  if (c->upload) {
+    cudaStreamSynchronize(c->upload);
+    cudaStreamDestroy(c->upload);
+  }
   for (auto& q : c->qd) {
+    cudaFree(q.up.coeff);
+    cudaFree(q.up.eps);
+    cudaFree(q.up.occ);
+    cudaFree(q.up.wgt);
+    cudaFreeHost(q.up.stage);
+    if (q.up.ready) cudaEventDestroy(q.up.ready);
+    if (q.up.free) cudaEventDestroy(q.up.free);
     free_split_plan(q.sp);
     cudaFree(q.Kdev);
     cudaFree(q.eps);
@@ -272,10 +284,27 @@ extern "C" lrt_status lrtddft_chi0_assemble(lrt_ctx* c, int q_begin, int q_end, 
   LRT_CUDA(cudaSetDevice(c->device));
   for (int iq = q_begin; iq < q_end; ++iq) {
     QData& Q = c->qd[iq];
+    LRT_TRY(adopt_orbitals(c, iq, s));
     if (!Q.chi0) LRT_CUDA(cudaMalloc(&Q.chi0, (size_t)ncol(c) * Q.nG * Q.nG * sizeof(double2)));
   }
   LRT_TRY(ensure_zf(c));
-  if (c->precision == LRT_PREC_FP64) {
+  if (c->spectral_order) {
+    // spectral engine, q by q on the shared pair-density buffer; S(q,0) from the same
+    // pair densities while they are resident
+    LRT_TRY(ensure_rho(c));
+    const bool fp64 = c->precision == LRT_PREC_FP64;
+    for (int iq = q_begin; iq < q_end; ++iq) {
+      QData& Q = c->qd[iq];
+      float sB = 1.0f;
+      if (fp64)
+        LRT_TRY(launch_pair_weights(c, Q, s));
+      else
+        LRT_TRY(split_pair_weights(c, Q, &sB, s));
+      LRT_TRY(launch_pair_density(c, Q, c->dw.rho, !fp64, s));
+      LRT_TRY(launch_chi0_spectral(c, Q, c->dw.rho, s));
+      LRT_TRY(launch_s0(c, Q, iq, c->dw.rho, fp64 ? nullptr : Q.sp.pw, sB, s));
+    }
+  } else if (c->precision == LRT_PREC_FP64) {
     LRT_TRY(ensure_rho(c));
     for (int iq = q_begin; iq < q_end; ++iq) {
       QData& Q = c->qd[iq];
@@ -414,6 +443,11 @@ extern "C" lrt_status lrtddft_set_orbitals(lrt_ctx* c, int iq, const double* eps
   LRT_TRY(need_device(c));
   LRT_CUDA(cudaSetDevice(c->device));
   QData& Q = c->qd[iq];
+  if (Q.up.pending) {
+    // the later call wins: an asynchronous upload still waiting for adoption is dropped
+    LRT_CUDA(cudaEventSynchronize(Q.up.ready));
+    Q.up.pending = false;
+  }
   size_t ne = (size_t)2 * c->nk * c->nb;
   LRT_CUDA(cudaMemcpy(Q.eps, eps, ne * sizeof(double), cudaMemcpyHostToDevice));
   LRT_CUDA(cudaMemcpy(Q.coeff, coeff, ne * c->npw * sizeof(double2), cudaMemcpyHostToDevice));
@@ -427,6 +461,75 @@ extern "C" lrt_status lrtddft_set_orbitals(lrt_ctx* c, int iq, const double* eps
   Q.have_chi0 = Q.have_chi = Q.have_dchi = false;
   c->have_S = false;
   c->graph_valid = false;
+  return LRT_OK;
+}
+
+// Swap in the orbitals of a completed or in-flight lrtddft_set_orbitals_async upload of q: the
+// stream s waits for the copies, the two buffer sets trade places, and the set just retired is
+// marked free once the work already on s (which may still read it) is done.
+namespace lrt {
+lrt_status adopt_orbitals(lrt_ctx* c, int iq, cudaStream_t s) {
+  QData& Q = c->qd[iq];
+  if (!Q.up.pending) return LRT_OK;
+  LRT_CUDA(cudaStreamWaitEvent(s, Q.up.ready, 0));
+  std::swap(Q.coeff, Q.up.coeff);
+  std::swap(Q.eps, Q.up.eps);
+  std::swap(Q.occ, Q.up.occ);
+  std::swap(Q.wgt, Q.up.wgt);
+  std::swap(Q.wgt_h, Q.up.wgt_h);
+  std::swap(Q.mu, Q.up.mu);
+  LRT_CUDA(cudaEventRecord(Q.up.free, s));
+  Q.up.pending = false;
+  Q.have_chi0 = Q.have_chi = Q.have_dchi = false;
+  c->have_S = false;
+  c->graph_valid = false;
+  return LRT_OK;
+}
+}  // namespace lrt
+
+extern "C" lrt_status lrtddft_set_orbitals_async(lrt_ctx* c, int iq, const double* eps,
+                                                 const double* coeff, const double* occ) {
+  if (!c || !eps || !coeff) return bad("NULL argument");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  LRT_TRY(need_device(c));
+  LRT_CUDA(cudaSetDevice(c->device));
+  QData& Q = c->qd[iq];
+  auto& U = Q.up;
+  const size_t ne = (size_t)2 * c->nk * c->nb;
+  const size_t nc = ne * c->npw;
+  if (!c->upload) LRT_CUDA(cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking));
+  if (!U.coeff) {
+    LRT_CUDA(cudaMalloc(&U.coeff, nc * sizeof(double2)));
+    LRT_CUDA(cudaMalloc(&U.eps, ne * sizeof(double)));
+    LRT_CUDA(cudaMalloc(&U.occ, ne * sizeof(double)));
+    LRT_CUDA(cudaMalloc(&U.wgt, ne * sizeof(double)));
+    LRT_CUDA(cudaMallocHost(&U.stage, 3 * ne * sizeof(double)));
+    LRT_CUDA(cudaEventCreateWithFlags(&U.ready, cudaEventDisableTiming));
+    LRT_CUDA(cudaEventCreateWithFlags(&U.free, cudaEventDisableTiming));
+    U.wgt_h.assign(ne, 0.0);
+  }
+  // an earlier upload into these buffers may still be reading the staging area
+  LRT_CUDA(cudaEventSynchronize(U.ready));
+  double* st_eps = U.stage;
+  double* st_occ = U.stage + ne;
+  double* st_wgt = U.stage + 2 * ne;
+  std::copy(eps, eps + ne, st_eps);
+  LRT_TRY(band_weights_all(c, eps, U.wgt_h.data()));
+  std::copy(U.wgt_h.begin(), U.wgt_h.end(), st_wgt);
+  if (occ) {
+    U.mu = NAN;
+    std::copy(occ, occ + ne, st_occ);
+  } else {
+    LRT_TRY(fermi_occupations(c, eps, U.wgt_h.data(), st_occ, &U.mu));
+  }
+  // the buffers about to be written were read by work enqueued before the last swap
+  LRT_CUDA(cudaStreamWaitEvent(c->upload, U.free, 0));
+  LRT_CUDA(cudaMemcpyAsync(U.coeff, coeff, nc * sizeof(double2), cudaMemcpyHostToDevice, c->upload));
+  LRT_CUDA(cudaMemcpyAsync(U.eps, st_eps, ne * sizeof(double), cudaMemcpyHostToDevice, c->upload));
+  LRT_CUDA(cudaMemcpyAsync(U.occ, st_occ, ne * sizeof(double), cudaMemcpyHostToDevice, c->upload));
+  LRT_CUDA(cudaMemcpyAsync(U.wgt, st_wgt, ne * sizeof(double), cudaMemcpyHostToDevice, c->upload));
+  LRT_CUDA(cudaEventRecord(U.ready, c->upload));
+  U.pending = true;
   return LRT_OK;
 }
 
@@ -444,6 +547,7 @@ extern "C" lrt_status lrtddft_get_ground_state(const lrt_ctx* c, int iq, double*
   if (!c) return bad("NULL context");
   if (iq < 0 || iq >= c->nq) return bad("q index");
   LRT_TRY(need_device(c));
+  LRT_TRY(adopt_orbitals(const_cast<lrt_ctx*>(c), iq, 0));
   const QData& Q = c->qd[iq];
   size_t ne = (size_t)2 * c->nk * c->nb;
   if (eps) LRT_CUDA(cudaMemcpy(eps, Q.eps, ne * sizeof(double), cudaMemcpyDeviceToHost));
@@ -547,6 +651,7 @@ extern "C" lrt_status lrtddft_get_orbitals(const lrt_ctx* c, int iq, double* coe
   if (!c || !coeff) return bad("NULL argument");
   if (iq < 0 || iq >= c->nq) return bad("q index");
   LRT_TRY(need_device(c));
+  LRT_TRY(adopt_orbitals(const_cast<lrt_ctx*>(c), iq, 0));
   const QData& Q = c->qd[iq];
   LRT_CUDA(cudaMemcpy(coeff, Q.coeff, (size_t)2 * c->nk * c->nb * c->npw * sizeof(double2),
                       cudaMemcpyDeviceToHost));
@@ -574,6 +679,7 @@ extern "C" lrt_status lrtddft_set_params(lrt_ctx* c, double T, double eta, const
   std::vector<double> eps(ne);
   for (int iq = 0; iq < c->nq; ++iq) {
     QData& Q = c->qd[iq];
+    LRT_TRY(adopt_orbitals(c, iq, 0));
     kernel_diag(c, Q);
     LRT_CUDA(cudaMemcpy(Q.Kdev, Q.K.data(), Q.nG * sizeof(double), cudaMemcpyHostToDevice));
     if (!std::isnan(Q.mu)) {   // Fermi-Dirac occupations (not supplied by the caller)
@@ -680,6 +786,10 @@ extern "C" lrt_status lrtddft_eta_scan(lrt_ctx* c, int ntau, const double* tau, 
 static lrt_status ensure_dchi(lrt_ctx* c) {
   if (c->neta > 1) {
     set_error("the adjoint takes a single eta (set_params or an eta list of one)");
+    return LRT_EUNSUPPORTED;
+  }
+  if (c->spectral_order) {
+    set_error("the adjoint differentiates the direct pair sum; use the direct chi0 engine");
     return LRT_EUNSUPPORTED;
   }
   LRT_TRY(need_all_chi(c));
@@ -834,7 +944,8 @@ extern "C" lrt_status lrtddft_dsf_vjp(lrt_ctx* c, const double* dL_dS, double gr
 
 extern "C" lrt_status lrtddft_set_tuning(lrt_ctx* c, int flags, int variant, int unit_stages) {
   if (!c) return bad("NULL context");
-  if (flags & ~(LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q | LRT_TUNE_PAIR_SIMT | LRT_TUNE_FINE_ACCUM))
+  if (flags & ~(LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q | LRT_TUNE_PAIR_SIMT | LRT_TUNE_FINE_ACCUM |
+                LRT_TUNE_HALF_TILES))
     return bad("unknown tuning flags");
   if (variant < -1 || variant > 1) return bad("variant must be -1, 0 or 1");
   if (unit_stages != 0 && (unit_stages < 64 || unit_stages % 64 != 0))
@@ -843,6 +954,7 @@ extern "C" lrt_status lrtddft_set_tuning(lrt_ctx* c, int flags, int variant, int
   c->multi_q = (flags & LRT_TUNE_SINGLE_Q) == 0;
   c->pair_simt = (flags & LRT_TUNE_PAIR_SIMT) != 0;
   c->fine_accum = (flags & LRT_TUNE_FINE_ACCUM) != 0;
+  c->half_tiles = (flags & LRT_TUNE_HALF_TILES) != 0;
   c->tune_variant = variant;
   c->tune_unit_stages = unit_stages;
   c->graph_valid = false;
@@ -853,6 +965,37 @@ extern "C" lrt_status lrtddft_get_tuning(lrt_ctx* c, int* variant, int* unit_sta
   if (!c || !variant || !unit_stages) return bad("NULL argument");
   *variant = c->last_tc_variant;
   *unit_stages = c->last_tc_unit_stages;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_set_spectral(lrt_ctx* c, double h, int order) {
+  if (!c) return bad("NULL context");
+  if (h == 0.0) {
+    c->spectral_order = 0;
+    c->spectral_h = 0.0;
+  } else {
+    if (!(h > 0.0) || !std::isfinite(h)) return bad("h must be 0 or a positive bin width");
+    if (order != 1 && order != 3) return bad("order must be 1 or 3");
+    c->spectral_order = order;
+    c->spectral_h = h;
+  }
+  c->graph_valid = false;
+  for (auto& Q : c->qd) Q.have_chi0 = Q.have_chi = Q.have_dchi = false;
+  c->have_S = false;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_spectral_grid(const lrt_ctx* c, int iq, double* x0, long long* nbins) {
+  if (!c || !x0 || !nbins) return bad("NULL argument");
+  if (iq < 0 || iq >= c->nq) return bad("q index");
+  *x0 = c->qd[iq].sp_x0;
+  *nbins = c->qd[iq].sp_nbins;
+  return LRT_OK;
+}
+
+extern "C" lrt_status lrtddft_get_tile_rows(lrt_ctx* c, int* rows) {
+  if (!c || !rows) return bad("NULL argument");
+  *rows = c->last_tc_rows;
   return LRT_OK;
 }
 
@@ -871,6 +1014,10 @@ extern "C" lrt_status lrtddft_graph_capture(lrt_ctx* c, int ntau, const double* 
   if (ntau < 1) return bad("ntau must be >= 1");
   if (mode != LRT_ITCF_FOLD && mode != LRT_ITCF_DIRECT) return bad("unknown ITCF mode");
   LRT_TRY(need_device(c));
+  if (c->spectral_order) {
+    set_error("the spectral chi0 engine sizes its grid on the host: no graph capture");
+    return LRT_EUNSUPPORTED;
+  }
   LRT_CUDA(cudaDeviceSynchronize());
   cudaStream_t st = nullptr;
   LRT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -937,6 +1084,7 @@ extern "C" lrt_status lrtddft_get_pair_densities(lrt_ctx* c, int iq, double* rho
   if (!c || !rho) return bad("NULL argument");
   if (iq < 0 || iq >= c->nq) return bad("q index");
   LRT_TRY(need_device(c));
+  LRT_TRY(adopt_orbitals(c, iq, 0));
   LRT_CUDA(cudaDeviceSynchronize());
   LRT_TRY(ensure_rho(c));
   const QData& Q = c->qd[iq];

@@ -83,10 +83,15 @@ struct QDesc {
   const float2* etab;         // [n_n * 64] eta of both columns of each pair (eta lists only)
   double* C;                  // [n_n * TN][ldr] FP64 sums, column-major
   long long np;
-  long long ldr;              // = n_st * NACC * TM (n_st even: super-tile 2 st2 + r is CTA r's)
+  long long ldr;              // = n_st * NACC * TM
   long long k_per_split;      // multiple of KS
   int gpad;
-  int n_st2, n_n, n_split;    // super-tile pairs, column tiles, pair ranges
+  int n_ru, n_n, n_split;     // row units, column tiles, pair ranges
+  // Row unit r: super-tiles 2 r (CTA 0) and 2 r + 1 (CTA 1), 512 rows; or, when it is a half,
+  // super-tile r' shared by the pair, CTA c holding its sub-blocks 4 c .. 4 c + 3 in one
+  // accumulator (256 rows): every unit under half_all (r' = r), else only the last one when
+  // the super-tile count is odd (r' = 2 r).
+  int half_all, half_last;
 };
 
 struct Params {
@@ -102,14 +107,17 @@ struct Params {
 using namespace tcx;
 
 struct Unit {
-  int st2, nt;
+  int st, nt;  // super-tile of CTA 0 (CTA 1 takes st + 1 unless half), column tile
+  bool half;   // the pair shares super-tile st: CTA r holds its sub-blocks 4 r .. 4 r + 3
   long long kb, ke;
 };
-__device__ __forceinline__ Unit unit_of(const QDesc& D, int u) {
+__host__ __device__ __forceinline__ Unit unit_of(const QDesc& D, int u) {
   Unit U;
   int tile = u / D.n_split, ks = u % D.n_split;
-  U.st2 = tile / D.n_n;
+  const int ru = tile / D.n_n;
   U.nt = tile % D.n_n;
+  U.half = D.half_all || (D.half_last && ru == D.n_ru - 1);
+  U.st = D.half_all ? ru : 2 * ru;
   U.kb = (long long)ks * D.k_per_split;
   U.ke = min(D.np, U.kb + D.k_per_split);
   return U;
@@ -176,11 +184,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     const int2 uu = P.units[u];
     const QDesc& D = P.qd[uu.x];
     const Unit U = unit_of(D, uu.y);
-    const int st = 2 * U.st2 + (int)rank;   // this CTA's row super-tile
+    // this CTA's row super-tile (a half unit: both CTAs on the same one, 4 sub-blocks each,
+    // accumulator 0 only)
+    const int st = U.half ? U.st : U.st + (int)rank;
+    const int sub0 = U.half ? 4 * (int)rank : 0;
+    const int nacc = U.half ? 1 : NACC;
     // per-unit tables (row pairs and G blocks of the super-tile, frequencies of the column tile)
     __syncthreads();
     if (threadIdx.x < NSUB) {
-      const int2 g = D.rowtab[st * NSUB + threadIdx.x];
+      const int w = sub0 + (int)threadIdx.x;   // (w >= NSUB: an unused A warp of a half unit)
+      const int2 g = w < NSUB ? D.rowtab[st * NSUB + w] : make_int2(0, 0);
       rowtab_s[threadIdx.x] = make_int2(g.x * KS * 8, g.y * KS * 8);
     }
     if (threadIdx.x < TNH / 4) wtab_s[threadIdx.x] = D.wtab[U.nt * 64 + rank * (TNH / 4) + threadIdx.x];
@@ -225,7 +238,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
         if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1, &abort_s, P.status))) break;
         const uint32_t ring = rbase + sr * R_STAGE + stage_token();
         const uint32_t sst = base + s * STAGE_BYTES;
-        if (warp < 8) {
+        if (warp < 8 && warp >= 4 * nacc) {
+          // a half unit: accumulator 1 is not used, its rows are not built
+        } else if (warp < 8) {
           // rho(4a + i) and rho(4b + j) of this lane's pair; x conj(y) as
           // y.re (x.re, x.im) + y.im (x.im, -x.re) in packed FP32x2
           const uint32_t ra = ring + lane * 8 + ro.x, rb = ring + lane * 8 + ro.y;
@@ -349,7 +364,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
                   if (!ok) break;
                   tc_fence_after();
                 }
-                if (lane == 0) {
+                if (lane == 0 && a < nacc) {
                   const uint32_t aH = sst + a * 2 * A_BYTES, aL = aH + A_BYTES;
                   const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
                   const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       // collect values that are never read).
       const int q = warp & 3;            // tensor-memory lane quadrant of this warp
       float4* stg = P.stage + ((size_t)blockIdx.x * 4 + q) * (NCHUNK * 4 * 32) + lane;
-      const long long grow0 = (long long)st * (NACC * TM) + q * 32 + lane;
+      const long long grow0 = (long long)st * (NACC * TM) + sub0 * 32 + q * 32 + lane;
       const size_t ldr = (size_t)D.ldr;
       double* cbase = D.C + (size_t)(U.nt * TN) * ldr;
       const uint32_t acc_empty0 = cluster_addr(&acc_empty[0], 0);
@@ -409,6 +424,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
 #pragma unroll 1
         for (int ch = 0; ch < NCHUNK; ++ch) {
           const int a = ch / (TN / 16), c = ch % (TN / 16);
+          if (a >= nacc) {
+            // accumulator 1 of a half unit holds nothing: hand it back unread
+            if (c == TN / 16 - 1) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive_cluster(acc_empty0 + a * 8);
+            }
+            continue;
+          }
           uint32_t r[16];
           const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + c * 16;
           asm volatile(
@@ -434,6 +458,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
 #pragma unroll 1
         for (int ch = 0; ch < NCHUNK; ++ch) {
           const int a = ch / (TN / 16), c = ch % (TN / 16);
+          if (a >= nacc) break;
           const float4* sp = stg + (size_t)ch * 128;
           float4 v[4];
 #pragma unroll
@@ -678,7 +703,10 @@ struct TcState {
   float4* stage = nullptr;
   size_t stage_bytes = 0;
   int ncl[2][kNumVariants][2] = {};   // resident CTA pairs per (bf, variant, eta list)
-  std::map<std::vector<long long>, std::pair<int, int>> tuned;   // shape -> (variant, unit idx)
+  struct Choice {
+    int v, ui, half;   // kernel variant, unit-size index, half row units
+  };
+  std::map<std::vector<long long>, Choice> tuned;   // shape -> choice
 };
 
 TcState* tc_of(const lrt_ctx* c) {
@@ -774,9 +802,10 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
         for (int qb = 2 * J; qb < std::min(nQ, 2 * J + 2); ++qb)
           if (qa <= qb) sub.push_back(make_int2(qa, qb));
   const int nsub = (int)sub.size();
-  // an even number of super-tiles: CTA r of a pair takes super-tile 2 st2 + r (a padding
-  // super-tile reads G block 0 and fills rows that are never read)
-  const int n_st = ((nsub + NSUB - 1) / NSUB + 1) / 2 * 2;
+  // a row unit is a pair of super-tiles, one per CTA, or a single super-tile shared by the
+  // pair (one accumulator per CTA): an odd last super-tile is such a half, so no super-tile
+  // is padding
+  const int n_st = (nsub + NSUB - 1) / NSUB;
   std::vector<int2> rowtab((size_t)n_st * NSUB, make_int2(0, 0));
   std::vector<int> blk((size_t)n_st * MAXBLK, -1);
   std::vector<int> rp_of((size_t)nG * nG, 0);
@@ -825,7 +854,7 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
     reinterpret_cast<float*>(&etab[j / 2])[j % 2] = (float)c->etas[j / nwt];
   }
   P.nsub = nsub;
-  P.n_st2 = n_st / 2;
+  P.n_st = n_st;
   P.n_n = n_n;
   P.ldc = n_n * TN;
   P.ldr = (long long)n_st * NACC * TM;
@@ -841,7 +870,7 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
       (e = cudaMalloc(&P.rp_of, rp_of.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&P.wtab, wtab.size() * sizeof(float4))) != cudaSuccess ||
       (e = cudaMalloc(&P.etab, etab.size() * sizeof(float2))) != cudaSuccess ||
-      (e = cudaMalloc(&P.pw, P.pw_n * sizeof(float4))) != cudaSuccess ||
+      (!P.pw && (e = cudaMalloc(&P.pw, P.pw_n * sizeof(float4))) != cudaSuccess) ||
       (e = cudaMalloc(&P.C, (size_t)P.ldr * P.ldc * sizeof(double))) != cudaSuccess)
     return fail(e);
   if ((e = cudaMemcpy(P.rowtab, rowtab.data(), rowtab.size() * sizeof(int2), cudaMemcpyHostToDevice)) !=
@@ -884,8 +913,8 @@ static void split_q(const lrt_ctx* c, const SplitPlan& P, int stages, int* n_spl
 
 // Descriptor and unit tables of a launch (q-major), uploaded when they changed.
 static lrt_status upload_tables(const lrt_ctx* c, const std::vector<int>& qs,
-                                const std::vector<const void*>& rhos, int stages, int limit_units,
-                                int* nunits, cudaStream_t s) {
+                                const std::vector<const void*>& rhos, int stages, bool half_all,
+                                int limit_units, int* nunits, cudaStream_t s) {
   TcState* T = tc_of(c);
   std::vector<QDesc> qd(qs.size());
   std::vector<int2> units;
@@ -903,18 +932,20 @@ static lrt_status upload_tables(const lrt_ctx* c, const std::vector<int>& qs,
     D.np = c->np;
     D.ldr = P.ldr;
     D.gpad = c->rho_gpad;
-    D.n_st2 = P.n_st2;
+    D.half_all = half_all ? 1 : 0;
+    D.n_ru = half_all ? P.n_st : (P.n_st + 1) / 2;
+    D.half_last = (!half_all && P.n_st % 2) ? 1 : 0;
     D.n_n = P.n_n;
     split_q(c, P, stages, &D.n_split, &D.k_per_split);
-    // super-tile pair, then pair range, then column tile: the clusters running at the same
-    // time share one super-tile pair, so the column tiles of a pair range read the same
-    // pair-density blocks (through L2) and only n_n tiles of FP64 sums (1 MB each) are being
-    // reduced into at once; ordering by pair range alone keeps all n_st2 n_n of them live,
-    // which with the staging areas overflows L2
-    for (int st2 = 0; st2 < D.n_st2; ++st2)
+    // row unit, then pair range, then column tile: the clusters running at the same time
+    // share one row unit, so the column tiles of a pair range read the same pair-density
+    // blocks (through L2) and only n_n tiles of FP64 sums (1 MB each) are being reduced into
+    // at once; ordering by pair range alone keeps all n_ru n_n of them live, which with the
+    // staging areas overflows L2
+    for (int ru = 0; ru < D.n_ru; ++ru)
       for (int ks = 0; ks < D.n_split; ++ks)
         for (int nt = 0; nt < D.n_n; ++nt)
-          units.push_back(make_int2((int)i, (st2 * D.n_n + nt) * D.n_split + ks));
+          units.push_back(make_int2((int)i, (ru * D.n_n + nt) * D.n_split + ks));
   }
   if (limit_units > 0 && (int)units.size() > limit_units) units.resize(limit_units);
   *nunits = (int)units.size();
@@ -989,18 +1020,20 @@ static lrt_status launch_tables(const lrt_ctx* c, bool bf, int v, int nunits, cu
   return LRT_OK;
 }
 
-// Variant and unit size for a launch: forced by the caller, tuned once per shape (each
-// candidate timed on the first units of the launch), or the defaults.
+// Variant, unit size and row-unit shape for a launch: forced by the caller, tuned once per
+// shape (each candidate timed on the first units of the launch), or the defaults.
 static lrt_status choose(const lrt_ctx* c, const std::vector<int>& qs,
                          const std::vector<const void*>& rhos, bool bf, cudaStream_t s, int* v,
-                         int* ui) {
+                         int* ui, bool* half) {
   *v = c->tune_variant >= 0 ? c->tune_variant : 0;
   *ui = 0;
+  *half = c->half_tiles;
   if (c->tune_unit_stages > 0) {
     // forced unit size: use it directly (index -1 means "the forced value")
     *ui = -1;
   }
-  if (!c->autotune || c->tune_variant >= 0 || c->tune_unit_stages > 0) return LRT_OK;
+  if (!c->autotune || c->tune_variant >= 0 || c->tune_unit_stages > 0 || c->half_tiles)
+    return LRT_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   LRT_CUDA(cudaStreamIsCapturing(s, &cs));
   if (cs != cudaStreamCaptureStatusNone) return LRT_OK;   // no timing inside a capture
@@ -1009,46 +1042,50 @@ static lrt_status choose(const lrt_ctx* c, const std::vector<int>& qs,
   for (int qi : qs) key.push_back(c->qd[qi].nG);
   auto it = T->tuned.find(key);
   if (it != T->tuned.end()) {
-    *v = it->second.first;
-    *ui = it->second.second;
+    *v = it->second.v;
+    *ui = it->second.ui;
+    *half = it->second.half != 0;
     return LRT_OK;
   }
   cudaEvent_t e0, e1;
   LRT_CUDA(cudaEventCreate(&e0));
   LRT_CUDA(cudaEventCreate(&e1));
   double best = 1e300;
-  for (int cv = 0; cv < kNumVariants; ++cv) {
-    int ncl = 0;
-    LRT_TRY(cluster_capacity(c, bf, cv, &ncl));
-    for (int cu = 0; cu < kNumUnitStages; ++cu) {
-      int nunits = 0;
-      LRT_TRY(upload_tables(c, qs, rhos, kUnitStages[cu], 2 * ncl, &nunits, s));
-      // time per stage of the first 2 rounds of units (a warm-up launch first)
-      LRT_TRY(launch_tables(c, bf, cv, nunits, s, false));
-      LRT_CUDA(cudaEventRecord(e0, s));
-      LRT_TRY(launch_tables(c, bf, cv, nunits, s, false));
-      LRT_CUDA(cudaEventRecord(e1, s));
-      LRT_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      LRT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      long long stages = 0;
-      TcState* TT = tc_of(c);
-      for (int u = 0; u < nunits; ++u) {
-        const QDesc& D = TT->qdesc_h[TT->units_h[u].x];
-        const long long kb = (long long)(TT->units_h[u].y % D.n_split) * D.k_per_split;
-        stages += (std::min(D.np, kb + D.k_per_split) - kb + KS - 1) / KS;
-      }
-      const double per = ms / (double)std::max(1LL, stages);
-      if (per < best) {
-        best = per;
-        *v = cv;
-        *ui = cu;
+  for (int hm = 0; hm < 2; ++hm)
+    for (int cv = 0; cv < kNumVariants; ++cv) {
+      int ncl = 0;
+      LRT_TRY(cluster_capacity(c, bf, cv, &ncl));
+      for (int cu = 0; cu < kNumUnitStages; ++cu) {
+        int nunits = 0;
+        LRT_TRY(upload_tables(c, qs, rhos, kUnitStages[cu], hm == 1, 2 * ncl, &nunits, s));
+        // time per super-tile stage (a 32-pair stage of 256 rows per CTA) of the first 2
+        // rounds of units, after a warm-up launch
+        LRT_TRY(launch_tables(c, bf, cv, nunits, s, false));
+        LRT_CUDA(cudaEventRecord(e0, s));
+        LRT_TRY(launch_tables(c, bf, cv, nunits, s, false));
+        LRT_CUDA(cudaEventRecord(e1, s));
+        LRT_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        LRT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        long long work = 0;
+        TcState* TT = tc_of(c);
+        for (int u = 0; u < nunits; ++u) {
+          const QDesc& D = TT->qdesc_h[TT->units_h[u].x];
+          const Unit U = unit_of(D, TT->units_h[u].y);
+          work += (U.ke - U.kb + KS - 1) / KS * (U.half ? 1 : 2);
+        }
+        const double per = ms / (double)std::max(1LL, work);
+        if (per < best) {
+          best = per;
+          *v = cv;
+          *ui = cu;
+          *half = hm == 1;
+        }
       }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  T->tuned[key] = std::make_pair(*v, *ui);
+  T->tuned[key] = TcState::Choice{*v, *ui, *half ? 1 : 0};
   // the trial launches added into the sums: clear them
   for (int qi : qs) {
     const SplitPlan& P = c->qd[qi].sp;
@@ -1062,10 +1099,11 @@ static lrt_status launch_group(const lrt_ctx* c, const std::vector<int>& qs,
                                const std::vector<const void*>& rhos, cudaStream_t s) {
   const bool bf = c->precision == LRT_PREC_BF16X3;
   int v = 0, ui = 0;
-  LRT_TRY(choose(c, qs, rhos, bf, s, &v, &ui));
+  bool half = false;
+  LRT_TRY(choose(c, qs, rhos, bf, s, &v, &ui, &half));
   const int stages = ui < 0 ? c->tune_unit_stages : kUnitStages[ui];
   int nunits = 0;
-  LRT_TRY(upload_tables(c, qs, rhos, stages, 0, &nunits, s));
+  LRT_TRY(upload_tables(c, qs, rhos, stages, half, 0, &nunits, s));
   LRT_TRY(launch_tables(c, bf, v, nunits, s, true));
   count_launch(c);
   if (c->profiling)
@@ -1084,6 +1122,7 @@ static lrt_status launch_group(const lrt_ctx* c, const std::vector<int>& qs,
   }
   const_cast<lrt_ctx*>(c)->last_tc_variant = v;
   const_cast<lrt_ctx*>(c)->last_tc_unit_stages = stages;
+  const_cast<lrt_ctx*>(c)->last_tc_rows = half ? 2 * TM : 2 * NACC * TM;
   return LRT_OK;
 }
 
@@ -1125,6 +1164,25 @@ static lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho,
 // chi0 of q_begin .. q_end - 1 on the tensor path.  q's whose pair densities fit in their own
 // buffers next to the others' run in one launch; the rest run one at a time in the shared
 // pair-density buffer.
+// Split-form pair weights {Delta_hi, Delta_lo, df sB, 0} of q in q.sp.pw (allocated on first
+// use) for the engines that need them without the tensor plan; sB is returned.
+lrt_status split_pair_weights(const lrt_ctx* c, QData& q, float* sB, cudaStream_t s) {
+  *sB = scale_B(c);
+  SplitPlan& P = q.sp;
+  if (!P.pw) {
+    P.pw_n = (size_t)((c->np + KS - 1) / KS * KS);
+    LRT_CUDA(cudaMalloc(&P.pw, P.pw_n * sizeof(float4)));
+    LRT_CUDA(cudaMemsetAsync(P.pw, 0, P.pw_n * sizeof(float4), s));
+  }
+  int dev = 0, nsm = 0;
+  LRT_CUDA(cudaGetDevice(&dev));
+  LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  pair_weights_split<<<4 * nsm, 256, 0, s>>>(q.eps, q.occ, q.wgt, c->nk, c->nb, *sB, P.pw);
+  count_launch(c);
+  LRT_CUDA(cudaGetLastError());
+  return LRT_OK;
+}
+
 lrt_status launch_chi0_split_range(lrt_ctx* c, int q_begin, int q_end, cudaStream_t s) {
   if (c->np <= 0) {
     set_error("no pairs to contract");

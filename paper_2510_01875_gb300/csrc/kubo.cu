@@ -225,6 +225,7 @@ extern "C" lrt_status lrtddft_kubo_greenwood(lrt_ctx* c, int n_eta, const double
       return LRT_EINVAL;
     }
   LRT_CUDA(cudaSetDevice(c->device));
+  LRT_TRY(adopt_orbitals(c, 0, 0));
   LRT_CUDA(cudaDeviceSynchronize());
   const QData& Q = c->qd[0];
   const int nk = c->nk, nb = c->nb, npw = c->npw, nw = c->nw;

@@ -26,11 +26,11 @@ const char* last_error();
 // the geometry and the frequency list only; weights and sums are refilled per assemble).
 struct SplitPlan {
   bool built = false;
-  int nsub = 0, n_st2 = 0, n_n = 0, ldc = 0;
+  int nsub = 0, n_st = 0, n_n = 0, ldc = 0;   // sub-blocks, row super-tiles, column tiles
   long long ldr = 0;
   size_t pw_n = 0;
-  int2* rowtab = nullptr;         // [2 n_st2][8] ring rows of the G quads of each sub-block
-  int* blk = nullptr;             // [2 n_st2][6] G blocks per super-tile
+  int2* rowtab = nullptr;         // [n_st][8] ring rows of the G quads of each sub-block
+  int* blk = nullptr;             // [n_st][6] G blocks per super-tile
   int* rp_of = nullptr;           // [nG][nG] row pair of (G, G')
   float4* wtab = nullptr;         // [n_n][64] frequency pairs (hi, hi, lo, lo)
   float2* etab = nullptr;         // [n_n][64] eta of the two frequencies of each pair
@@ -65,6 +65,22 @@ struct QData {
   std::vector<double> ds0;        // [5] complex: d/d(T, eta, A, B, C) of d chi_00/d eta at w = 0
   bool have_dchi = false;
   SplitPlan sp;                   // tensor-path tables of this q
+  double sp_x0 = 0.0;             // spectral engine: grid of the last assembly (x_0, bins)
+  long long sp_nbins = 0;
+  // orbitals of the next assembly, uploaded by lrtddft_set_orbitals_async on the context's
+  // upload stream while earlier work runs; swapped with the fields above by adopt_orbitals
+  struct Pending {
+    bool pending = false;
+    double2* coeff = nullptr;     // device [2][nk][nb][npw]
+    double* eps = nullptr;        // device [2][nk][nb]
+    double* occ = nullptr;
+    double* wgt = nullptr;
+    std::vector<double> wgt_h;
+    double mu = 0.0;
+    double* stage = nullptr;      // pinned host [3][2 nk nb]: eps, occ, weights of the copy
+    cudaEvent_t ready = nullptr;  // the copies into these buffers have completed
+    cudaEvent_t free = nullptr;   // the work that read these buffers (before the swap) is done
+  } up;
 };
 
 struct DeviceWork {
@@ -144,12 +160,18 @@ struct lrt_ctx {
   bool multi_q = true;
   bool pair_simt = false;         // split-path pair densities on the FP32 SIMT kernel
   bool fine_accum = false;        // FP32 accumulation period of 32 stages instead of 64
+  bool half_tiles = false;        // forced half row units (256 rows per CTA pair)
+  int spectral_order = 0;         // chi0 engine: 0 the direct pair sum, 1 or 3 the spectral
+  double spectral_h = 0.0;        // function on a grid of this spacing (interpolation order)
+  void* sp = nullptr;             // spectral engine state (spectral.cu)
+  int last_tc_rows = 0;           // rows per CTA-pair unit of the last tensor launch (512, 256)
   int tune_variant = -1;          // forced kernel variant, -1: tuned or default
   int tune_unit_stages = 0;       // forced stages per unit, 0: tuned or default
   int last_tc_variant = -1, last_tc_unit_stages = 0;
   // Kubo-Greenwood scan (kubo.cu): S*_KG rows and the reference eta of the last scan
   void* kg = nullptr;
   // captured forward graph (lrtddft_graph_capture)
+  cudaStream_t upload = nullptr;    // lrtddft_set_orbitals_async copies (non-blocking stream)
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
 };
@@ -198,6 +220,13 @@ lrt_status build_geometry(lrt_ctx* c, const int* nG);
 lrt_status solve_ground_states(lrt_ctx* c, const double* occupations);
 lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host);
 lrt_status reset_band_weights(lrt_ctx* c, int iq, const double* eps_host);
+lrt_status fermi_occupations(const lrt_ctx* c, const double* eps_host, const double* wgt,
+                             double* f, double* mu);
+lrt_status band_weights_all(const lrt_ctx* c, const double* eps_host, double* out);
+lrt_status adopt_orbitals(lrt_ctx* c, int iq, cudaStream_t s);
+lrt_status launch_chi0_spectral(lrt_ctx* c, QData& q, const void* rho, cudaStream_t s);
+void free_spectral_state(lrt_ctx* c);
+lrt_status split_pair_weights(const lrt_ctx* c, QData& q, float* sB, cudaStream_t s);
 double fxc_alda(double n);
 double fxc_model(double qg, double n, double A, double B, double C);
 // K_GG = 4 pi/|q+G|^2 + f_xc for the context's kernel, from Q.qg2 (host vector only).

@@ -556,11 +556,11 @@ int band_weights(const double* e, int nfull, int nbands, double* w, bool complet
 }
 
 // mu by 200 halvings of [min eps - 60 T, max eps + 60 T] so that (2/N_k) sum w f = N_e over
-// the k mesh of q; f on both meshes uploaded.
-lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host) {
+// the k mesh of q (wgt: band weights of both meshes); f [2 nk nb] on both meshes.
+lrt_status fermi_occupations(const lrt_ctx* c, const double* eps_host, const double* wg,
+                             double* f, double* mu_out) {
   int nk = c->nk, nb = c->nb;
   size_t half = (size_t)nk * nb;
-  const double* wg = c->qd[iq].wgt_h.data();
   double cap = 0.0;
   for (size_t i = 0; i < half; ++i) cap += wg[i];
   if (2.0 * cap / nk < c->nelec) {
@@ -584,11 +584,18 @@ lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host) {
       hi = mid;
     if (hi - lo <= 0.0) break;
   }
-  double mu = 0.5 * (lo + hi);
-  c->qd[iq].mu = mu;
-  std::vector<double> f(2 * half);
+  const double mu = 0.5 * (lo + hi);
+  *mu_out = mu;
   for (size_t i = 0; i < 2 * half; ++i) f[i] = fermi(eps_host[i], mu, c->T);
-  LRT_CUDA(cudaMemcpy(c->qd[iq].occ, f.data(), 2 * half * sizeof(double), cudaMemcpyHostToDevice));
+  return LRT_OK;
+}
+
+// Fermi-Dirac occupations of q from host eigenvalues and the q's band weights, uploaded.
+lrt_status set_occupations_fd(lrt_ctx* c, int iq, const double* eps_host) {
+  QData& Q = c->qd[iq];
+  std::vector<double> f((size_t)2 * c->nk * c->nb);
+  LRT_TRY(fermi_occupations(c, eps_host, Q.wgt_h.data(), f.data(), &Q.mu));
+  LRT_CUDA(cudaMemcpy(Q.occ, f.data(), f.size() * sizeof(double), cudaMemcpyHostToDevice));
   return LRT_OK;
 }
 
@@ -806,20 +813,24 @@ lrt_status solve_ground_states(lrt_ctx* c, const double* occupations) {
   return LRT_OK;
 }
 
-// Band weights recomputed from eigenvalues supplied through the orbital hook.
-lrt_status reset_band_weights(lrt_ctx* c, int iq, const double* eps_host) {
-  QData& Q = c->qd[iq];
-  int nb = c->nb;
-  std::vector<double> w(nb);
+// Band weights of both meshes [2 nk nb] from eigenvalues supplied through the orbital hook.
+lrt_status band_weights_all(const lrt_ctx* c, const double* eps_host, double* out) {
+  const int nb = c->nb;
   for (int s = 0; s < 2 * c->nk; ++s) {
     // the context's nb already holds every member of a multiplet split at setup
-    int used = band_weights(eps_host + (size_t)s * nb, nb, c->nbands, w.data(), true);
+    int used = band_weights(eps_host + (size_t)s * nb, nb, c->nbands, out + (size_t)s * nb, true);
     if (used < 0) {
       set_error("a degenerate multiplet at the band cut extends past the supplied bands");
       return LRT_EINVAL;
     }
-    std::copy(w.begin(), w.end(), Q.wgt_h.begin() + (size_t)s * nb);
   }
+  return LRT_OK;
+}
+
+// Band weights recomputed from eigenvalues supplied through the orbital hook, uploaded.
+lrt_status reset_band_weights(lrt_ctx* c, int iq, const double* eps_host) {
+  QData& Q = c->qd[iq];
+  LRT_TRY(band_weights_all(c, eps_host, Q.wgt_h.data()));
   LRT_CUDA(cudaMemcpy(Q.wgt, Q.wgt_h.data(), Q.wgt_h.size() * sizeof(double), cudaMemcpyHostToDevice));
   return LRT_OK;
 }

@@ -161,10 +161,10 @@ def test_host_geometry_matches_oracle(lib, wl):
 def test_tuning_flags_and_hooks_on_host(lib):
     st, h = _host_ctx(W.tiny())
     assert st == 0
-    # LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q | LRT_TUNE_PAIR_SIMT | LRT_TUNE_FINE_ACCUM are the known flags
-    for flags in (0, 1, 2, 4, 7, 8, 15):
+    # LRT_TUNE_AUTO | SINGLE_Q | PAIR_SIMT | FINE_ACCUM | HALF_TILES are the known flags
+    for flags in (0, 1, 2, 4, 7, 8, 15, 16, 31):
         assert lib.lrtddft_set_tuning(h, flags, -1, 0) == 0, flags
-    for flags in (16, 32, -1):
+    for flags in (32, 64, -1):
         assert lib.lrtddft_set_tuning(h, flags, -1, 0) == binding.LRT_EINVAL, flags
     for v, u in ((2, 0), (-2, 0), (0, 100), (0, -64)):
         assert lib.lrtddft_set_tuning(h, 0, v, u) == binding.LRT_EINVAL, (v, u)
@@ -172,6 +172,17 @@ def test_tuning_flags_and_hooks_on_host(lib):
     v, u = C.c_int(), C.c_int()
     assert lib.lrtddft_get_tuning(h, C.byref(v), C.byref(u)) == 0
     assert (v.value, u.value) == (-1, 0)   # no tensor-core launch has run
+    r = C.c_int(-1)
+    assert lib.lrtddft_get_tile_rows(h, C.byref(r)) == 0 and r.value == 0
+    # the spectral chi0 engine: bin width >= 0, order 1 or 3
+    for hh, order in ((-1.0, 3), (0.01, 2), (float("inf"), 3)):
+        assert lib.lrtddft_set_spectral(h, hh, order) == binding.LRT_EINVAL, (hh, order)
+    assert lib.lrtddft_set_spectral(h, 0.01, 3) == 0
+    assert lib.lrtddft_set_spectral(h, 0.0, 0) == 0
+    x0, nb = C.c_double(-1.0), C.c_longlong(-1)
+    assert lib.lrtddft_get_spectral_grid(h, 0, C.byref(x0), C.byref(nb)) == 0
+    assert (x0.value, nb.value) == (0.0, 0)
+    assert lib.lrtddft_get_spectral_grid(h, 9, C.byref(x0), C.byref(nb)) == binding.LRT_EINVAL
     out = np.zeros(16)
     D = C.POINTER(C.c_double)
     assert lib.lrtddft_get_pair_densities(h, 0, out.ctypes.data_as(D)) == binding.LRT_ESTATE

@@ -5,8 +5,8 @@ and the torch.autograd wrapper.
  - FP64 path against the oracle's analytic forward-mode tangents (oracle/adjoint.py):
    1e-8 of each parameter's max |dF| (the oracle tangents are pinned to central
    differences of the oracle's forward path in tests/test_oracle_adjoint.py);
- - split-precision paths against central differences of the FP64 forward (Richardson-
-   extrapolated): FP16x3 within 1e-4 relative (the gradient bound), BF16x3 within 1e-3;
+ - split-precision paths (FP16x3 and BF16x3) against central differences of the FP64 forward
+   (Richardson-extrapolated), within the 1e-4 gradient bound (three readings of it below);
  - FP64 path against the same central differences within 1e-6;
  - vector-Jacobian products equal the contracted Jacobians; set_params reproduces a
    freshly created context; the autograd wrapper returns the library's vjp.

@@ -5,6 +5,7 @@ the captured CUDA graph of the forward path (through the C ABI).
    bounds (chi0 3e-5 of the per-q max norm, F 1e-5 pointwise);
  - one launch for all q equals one launch per q to FP64 rounding (each unit computes the same
    FP32 partial sums; only the order of the FP64 reductions differs);
+ - half row units (256 rows) equal the default 512-row units to FP64 rounding;
  - every (variant, unit size) and the autotuner agree with the defaults within 2e-6 on F and
    report the choice they made;
  - a graph replay reproduces the eager S and F and is refused after set_params.
@@ -38,7 +39,8 @@ def run(wl, prec="fp16x3", **tune):
     c.dyson_solve()
     tau = response.tau_grid(wl.T, wl.ntau)
     F, _ = c.itcf(tau)
-    out = {"S": c.dsf(), "F": F, "chi0": [c.get_chi0(i) for i in range(wl.nq)], "tuning": c.get_tuning()}
+    out = {"S": c.dsf(), "F": F, "chi0": [c.get_chi0(i) for i in range(wl.nq)], "tuning": c.get_tuning(),
+           "rows": c.get_tile_rows() if prec != "fp64" else None}
     c.close()
     return out
 
@@ -51,6 +53,20 @@ def test_ragged_q_in_one_launch_against_oracle():
         c0 = r["chi0"]
         assert np.abs(g["chi0"][iq] - c0).max() / np.abs(c0).max() < 3e-5, iq
         assert np.abs(g["F"][iq] / r["F"] - 1).max() < 1e-5, iq
+
+
+def test_half_row_units_equal_full_units():
+    """Every row unit a half (256 rows, one accumulator per CTA) against the default (512-row
+    units; an odd last one is a half): each row accumulates the same FP32 partial sums in the
+    same order, so only the order of the FP64 reductions differs."""
+    wl = ragged()
+    a = run(wl)
+    b = run(wl, half_tiles=True)
+    assert a["rows"] == 512 and b["rows"] == 256
+    for iq in range(wl.nq):
+        scale = np.abs(a["chi0"][iq]).max()
+        assert np.abs(a["chi0"][iq] - b["chi0"][iq]).max() <= 1e-12 * scale
+    np.testing.assert_allclose(a["F"], b["F"], rtol=1e-12)
 
 
 def test_one_launch_equals_one_launch_per_q():
@@ -77,7 +93,7 @@ def test_autotune_picks_a_candidate():
     ref = run(wl)
     g = run(wl, auto=True)
     v, u = g["tuning"]
-    assert v in (0, 1) and u in (1024, 4096, 16384)
+    assert v in (0, 1) and u in (1024, 4096, 16384) and g["rows"] in (256, 512)
     np.testing.assert_allclose(g["F"], ref["F"], rtol=2e-6)
 
 
