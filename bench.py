@@ -55,9 +55,12 @@ def parse():
     ap.add_argument("--unit-stages", type=int, default=0, help="force the stages per work unit")
     ap.add_argument("--fine-accum", action="store_true",
                     help="flush the FP32 tensor-core accumulators every 32 stages instead of 64")
-    ap.add_argument("--workload", default="al1", choices=["al1", "al4_adjoint", "al64_slice", "al32_k1"],
+    ap.add_argument("--workload", default="al1",
+                    choices=["al1", "al4_adjoint", "al64_slice", "al32_k1", "al1_q_fp64"],
                     help="al1: the timed 8-q workload (default); the others measure the other "
-                         "configurations once and print one JSON line each")
+                         "configurations once and print one JSON line each (al1_q_fp64: the "
+                         "largest |q| of the timed workload at full size in the FP64 and the "
+                         "split form)")
     return ap.parse_args()
 
 
@@ -239,8 +242,8 @@ def run_ours(args, world, rank, local, pg):
     if args.precision == "fp64":
         bound, unit = "fp64", "TFLOP/s"
         flops_per_cmac = 4.0
-        peak = binding.measure_fp64(local)
-        peak_note = "measured: FP64 FMA loop on every SM (lrtddft_measure_fp64)"
+        peak = max(binding.measure_fp64(local), fp64_peak()["tflops"])
+        peak_note = "measured: the larger of an FP64 FMA loop (lrtddft_measure_fp64) and cuBLAS DGEMM"
     else:
         bound, unit = "tensor", "TFLOP/s"
         flops_per_cmac = 12.0      # 2 real MACs per complex MAC (Hermitian split) x 3 products
@@ -297,6 +300,8 @@ def run_ours(args, world, rank, local, pg):
                            * (16 if args.precision == "fp64" else 8) / 1e9)},
             "q_spectra_per_s": sum_over_ranks(None, wl.nq * world) / (ms_max / 1e3),
             "setup_s": setup_s,
+            # setup = one dense eigensolve per k point of both meshes of every q (+ refinement)
+            "setup_ms_per_eigensolve": 1e3 * setup_s / (2 * ctx.nk * wl.nq),
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": prof["launches"],
@@ -410,12 +415,14 @@ def run_extras(args, ctx_main, wl, S_direct, F_direct):
     peak64 = fp64_peak()
     dfma = binding.measure_fp64(0)
     tf64 = 4.0 * fp["cmac"] / (fp["ms"] / 1e3) / 1e12
+    peak = max(dfma, peak64["tflops"])
     out["fp64_form"] = {"value": fp["cmac"] / (fp["ms"] / 1e3), "unit": UNIT,
                         "chi0_tflops": tf64,
-                        "roofline": {"bound": "fp64", "achieved": tf64, "peak": dfma,
-                                     "unit": "TFLOP/s", "frac": tf64 / dfma,
-                                     "peak_source": "measured: FP64 FMA loop on every SM (the pipe "
-                                                    "of the SIMT FP64 kernel), lrtddft_measure_fp64"},
+                        "roofline": {"bound": "fp64", "achieved": tf64, "peak": peak,
+                                     "unit": "TFLOP/s", "frac": tf64 / peak,
+                                     "peak_source": "measured: the larger of an FP64 FMA loop on "
+                                                    "every SM (lrtddft_measure_fp64, %.3f) and cuBLAS "
+                                                    "DGEMM (%.3f)" % (dfma, peak64["tflops"])},
                         "dgemm_peak": {"tflops": peak64["tflops"], "frac": tf64 / peak64["tflops"],
                                        "how": peak64["how"]},
                         "sample": f"1 q, 63 frequencies (15-25 eV) and w = 0, all {ctx_main.nk * ctx_main.nb ** 2:.3g} "
@@ -713,6 +720,7 @@ def run_workload(args):
     t0 = time.time()
     c = binding.Context(wl, prec)
     line["setup_s"] = time.time() - t0
+    line["setup_ms_per_eigensolve"] = 1e3 * line["setup_s"] / (2 * c.nk * wl.nq)
     line["workload"] = wl.name
     line.update({"nq": wl.nq, "nk": c.nk, "nbands": c.nb, "nG": [int(x) for x in wl.nG][:48],
                  "nw": wl.nw, "np_per_q": c.nk * c.nb * c.nb})
@@ -774,8 +782,64 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_full_q_fp64(args):
+    """The largest |q| of the timed workload at its full size (12^3 k, 121 bands, 59 G, 1024
+    frequencies) in the FP64 form and in the split form: the split form's error at exactly the
+    timed configuration, and the FP64 form's rate and roofline on a whole q."""
+    from paper_2510_01875_gb300 import binding, build
+    build.build()
+    binding.load()
+    full = workload(0, 0)
+    wl = full.replace(q=full.q[-1:], nG=full.nG[-1:], name=full.name.replace(f"q{full.nq}", "q1last"))
+    tau = np.linspace(0.0, 0.5 / wl.T, wl.ntau)
+    prec = args.precision if args.precision != "fp64" else "fp16x3"
+    res = {}
+    for p in ("fp64", prec):
+        t0 = time.time()
+        c = binding.Context(wl, p)
+        setup = time.time() - t0
+        c.profile(True)
+
+        def fwd():
+            c.chi0_assemble()
+            c.dyson_solve()
+            return c.dsf(), c.itcf(tau)[0]
+
+        ms, (S, F) = _timed(fwd)
+        pr = c.profile_read()
+        res[p] = {"S": S[0], "F": F[0], "chi0": c.get_chi0(0), "ms": ms, "chi0_ms": pr["chi0_ms"],
+                  "cmac": pr["chi0_cmac"], "setup_s": setup}
+        c.close()
+    a, b = res["fp64"], res[prec]
+    Sa, Sb = a["S"], b["S"]
+    peaks = [j for j in range(1, wl.nw - 1) if Sa[j] > Sa[j - 1] and Sa[j] >= Sa[j + 1] and Sa[j] > 0.1 * Sa.max()]
+    tf64 = 4.0 * a["cmac"] / (a["chi0_ms"] / 1e3) / 1e12
+    dfma = max(binding.measure_fp64(0), fp64_peak()["tflops"])
+    line = {"workload_kind": "al1_q_fp64", "workload": wl.name, "precision": prec,
+            "q_inv_bohr": float(np.linalg.norm(wl.q[0])),
+            "fp64_form": {"forward_ms": a["ms"], "chi0_ms": a["chi0_ms"],
+                          "cmac_per_s": a["cmac"] / (a["chi0_ms"] / 1e3), "chi0_tflops": tf64,
+                          "roofline": {"bound": "fp64", "achieved": tf64, "peak": dfma, "unit": "TFLOP/s",
+                                       "frac": tf64 / dfma,
+                                       "peak_source": "measured: the larger of an FP64 FMA loop "
+                                                      "(lrtddft_measure_fp64) and cuBLAS DGEMM"},
+                          "setup_s": a["setup_s"]},
+            "split_form": {"forward_ms": b["ms"], "chi0_ms": b["chi0_ms"],
+                           "cmac_per_s": b["cmac"] / (b["chi0_ms"] / 1e3), "setup_s": b["setup_s"]},
+            "split_vs_fp64": {
+                "chi0_maxnorm_rel": float(np.abs(b["chi0"] - a["chi0"]).max() / np.abs(a["chi0"]).max()),
+                "S_maxnorm_rel": float(np.abs(Sb - Sa).max() / np.abs(Sa).max()),
+                "S_peak_rel": float(max(abs(Sb[j] / Sa[j] - 1) for j in peaks)) if peaks else None,
+                "F_pointwise_rel": float(np.abs(b["F"] / a["F"] - 1).max()),
+                "bounds": {"F": 1e-5, "S_peaks": 1e-4}}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "al1_q_fp64":
+        run_full_q_fp64(args)
+        return
     if args.workload != "al1":
         run_workload(args)
         return

@@ -208,9 +208,11 @@ lrt_status lrtddft_get_tile_rows(lrt_ctx* ctx, int* rows);
  * frequency and every eta of a list is one GEMM over the bins.  The relative error is
  * O((h/eta)^(order+1)) (order 3, h = eta/16: about 1e-6 of max |chi0|); the cost of the pair
  * sum no longer grows with the number of frequencies.  Grid: over the pairs with df != 0,
- * x_0 = h (floor(min x_p / h) - 1), n_b = floor((max x_p - x_0)/h) + 3.  The FP64 context sums
- * in FP64 (cuBLAS DGEMM transform); the split contexts sum FP32 products with compensated FP32
- * sums (SGEMM transform).  S(q,0) keeps its exact limit.  h = 0 selects the direct engine
+ * x_0 = h (floor(min x_p / h) - 1), n_b = floor((max x_p - x_0)/h) + 3.  The FP64 context forms
+ * A in FP64 and transforms with cuBLAS DGEMM; the split contexts form A from FP32 products with
+ * compensated FP32 sums per bin and transform with FP32 products accumulated over 256 bins at
+ * a time (cuBLAS SGEMM, strided batches), the chunks summed in FP64.  S(q,0) keeps its exact
+ * limit.  h = 0 selects the direct engine
  * (the default).  Not with the adjoint or graph capture (LRT_EUNSUPPORTED there).  LRT_EINVAL
  * for h < 0 or an order other than 1, 3; chi0_assemble returns LRT_EINVAL when the grid would
  * exceed 2^26 bins. */

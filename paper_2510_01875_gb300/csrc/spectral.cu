@@ -14,9 +14,10 @@
 //     shared memory; FP64 for the FP64 form, FP32 products with compensated FP32 sums for the
 //     split forms (whose pair densities are FP32);
 //  4. A_b from the moments (L_c(f) is a polynomial in f: A_b = sum_c sum_k a_ck M_k(j(b, c)));
-//  5. the transform as one real GEMM: rows Re A, Im A of every G <= G' pair, columns Re, Im of
-//     1/(w - x_b + i eta) of every (eta, w) column, inner dimension the bins (cuBLAS: D for the
-//     FP64 form, S for the split forms);
+//  5. the transform as a real GEMM (cuBLAS): rows Re A, Im A of every G <= G' pair, columns
+//     Re, Im of 1/(w - x_b + i eta) of every (eta, w) column, inner dimension the bins; FP64
+//     (DGEMM) for the FP64 form, FP32 products summed over 256 bins at a time and the chunks in
+//     FP64 for the split forms;
 //  6. unpack with the Hermitian split of P (chi0(G',G) from conj A).
 #include <cublas_v2.h>
 
@@ -33,6 +34,7 @@ constexpr int SP_THREADS = 256;
 constexpr int SP_E = 4;                          // G <= G' pairs per thread
 constexpr int SP_TILE = SP_THREADS * SP_E;       // G <= G' pairs per block
 constexpr int SP_CHUNK = 32;                     // sorted pairs staged per step
+constexpr int SP_KCHUNK = 256;                   // bins per FP32 partial product of the transform
 
 // Lagrange basis of order m as polynomials in the fraction f: L_c(f) = sum_k a[c][k] f^k.
 // m = 1: nodes j, j + 1.  m = 3: nodes j - 1 .. j + 2.
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
     const int2* __restrict__ range, double2* __restrict__ Mom) {
   using T2 = typename V2<T>::type;
   extern __shared__ __align__(16) unsigned char sp_smem[];
-  T2* rs = reinterpret_cast<T2*>(sp_smem);                     // [nG][SP_CHUNK]
+  T2* rs = reinterpret_cast<T2*>(sp_smem);                     // [SP_CHUNK][nG]
   T* cs = reinterpret_cast<T*>(rs + (size_t)nG * SP_CHUNK);    // [SP_CHUNK][M + 1]
   int* bs = reinterpret_cast<int*>(cs + SP_CHUNK * (M + 1));   // [SP_CHUNK]
   const int tid = threadIdx.x;
@@ -229,8 +231,10 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
   for (int i0 = rg.x; i0 < rg.y; i0 += SP_CHUNK) {
     const int n = min(SP_CHUNK, rg.y - i0);
     __syncthreads();
+    // (pair-major in shared memory, so that the lanes of a warp, which hold consecutive G <= G'
+    // pairs, read consecutive G' without bank conflicts; every global read is a gather anyway)
     for (int e = tid; e < nG * SP_CHUNK; e += SP_THREADS) {
-      const int G = e / SP_CHUNK, i = e % SP_CHUNK;
+      const int i = e / nG, G = e % nG;
       T2 v;
       v.x = 0;
       v.y = 0;
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
 #pragma unroll
       for (int e = 0; e < SP_E; ++e) {
         if (ga[e] < 0) continue;
-        const T2 a = rs[ga[e] * SP_CHUNK + i], b = rs[gb[e] * SP_CHUNK + i];
+        const T2 a = rs[i * nG + ga[e]], b = rs[i * nG + gb[e]];
         const T Pr = a.x * b.x + a.y * b.y, Pi = a.y * b.x - a.x * b.y;
 #pragma unroll
         for (int k = 0; k <= M; ++k) {
@@ -273,11 +277,11 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
   flush();
 }
 
-// Re A and Im A per G <= G' pair and bin, as the GEMM's left operand: Am [2 ngg][nbins]
+// Re A and Im A per G <= G' pair and bin, as the GEMM's left operand: Am [2 ngg][ld]
 // (rows Re then Im), A_b = scale sum_c sum_k a[c][k] M_k(j), j = b - c (m = 1) or b + 1 - c (m = 3).
 template <typename T, int M>
-__global__ void sp_assemble_A(const double2* __restrict__ Mom, int ngg, int nbins, double scale,
-                              T* __restrict__ Am) {
+__global__ void sp_assemble_A(const double2* __restrict__ Mom, int ngg, int nbins, int ld,
+                              double scale, T* __restrict__ Am) {
   const long long total = (long long)ngg * nbins;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -297,8 +301,8 @@ __global__ void sp_assemble_A(const double2* __restrict__ Mom, int ngg, int nbin
         im += a * m.y;
       }
     }
-    Am[(size_t)g * nbins + b] = (T)(scale * re);
-    Am[(size_t)(ngg + g) * nbins + b] = (T)(scale * im);
+    Am[(size_t)g * ld + b] = (T)(scale * re);
+    Am[(size_t)(ngg + g) * ld + b] = (T)(scale * im);
   }
 }
 
@@ -340,6 +344,17 @@ __global__ void sp_unpack(const T* __restrict__ Cm, int ngg, int nG, int ncol, d
   }
 }
 
+// Cd = sum over the FP32 partial products of the bin chunks, in FP64.
+__global__ void sp_reduce(const float* __restrict__ parts, int nparts, long long n,
+                          double* __restrict__ Cd) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < nparts; ++c) acc += (double)parts[(size_t)c * n + i];
+    Cd[i] = acc;
+  }
+}
+
 struct SpState {
   cublasHandle_t blas = nullptr;
   void* buf = nullptr;            // per-pair arrays (x, df, bins, order, coefficients, range)
@@ -348,7 +363,8 @@ struct SpState {
   size_t bytes2 = 0;
   int2* ranges = nullptr;         // block ranges of whole bins
   int ranges_cap = 0;
-  std::vector<int2> ranges_h;
+  std::vector<int2> ranges_h;     // host sources of asynchronous copies, kept alive here
+  std::vector<int> start_h;
   double* freqs_etas = nullptr;   // [nwi + neta]
   size_t fe_n = 0;
 };
@@ -393,8 +409,8 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
       reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(coef) + al(np * (M + 1) * sizeof(T)));
   sp_pairs<<<grid, 256, 0, s>>>(q.eps, q.occ, q.wgt, nk, nb, x, df);
   count_launch(c);
-  const unsigned long long init[2] = {~0ull, 0ull};
-  LRT_CUDA(cudaMemcpyAsync(mm, init, sizeof init, cudaMemcpyHostToDevice, s));
+  LRT_CUDA(cudaMemsetAsync(mm, 0xff, sizeof(unsigned long long), s));   // min key: all ones
+  LRT_CUDA(cudaMemsetAsync(mm + 1, 0, sizeof(unsigned long long), s));  // max key: zero
   sp_range<<<grid, 256, 0, s>>>(x, df, np, mm);
   count_launch(c);
   LRT_CUDA(cudaGetLastError());
@@ -424,10 +440,17 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
   const size_t o_cur = o_cnt + n_cnt;
   const size_t o_mom = o_cur + n_cnt;
   const size_t n_mom = al((size_t)nbins * (M + 1) * ngg * sizeof(double2));
-  const size_t o_am = o_mom + n_mom, n_am = al((size_t)2 * ngg * nbins * sizeof(T));
-  const size_t o_km = o_am + n_am, n_km = al((size_t)2 * ncol * nbins * sizeof(T));
-  const size_t o_c = o_km + n_km, n_c = al((size_t)2 * ncol * 2 * ngg * sizeof(T));
-  const size_t need2 = o_c + n_c;
+  // GEMM operands in the moments' type; the split contexts' FP32 transform runs in chunks of
+  // SP_KCHUNK bins whose partial products are summed in FP64
+  const bool f32 = sizeof(T) == 4;
+  const int nbp = f32 ? (nbins + SP_KCHUNK - 1) / SP_KCHUNK * SP_KCHUNK : nbins;
+  const int nparts = f32 ? nbp / SP_KCHUNK : 0;
+  const long long nC = (long long)2 * ncol * 2 * ngg;
+  const size_t o_am = o_mom + n_mom, n_am = al((size_t)2 * ngg * nbp * sizeof(T));
+  const size_t o_km = o_am + n_am, n_km = al((size_t)2 * ncol * nbp * sizeof(T));
+  const size_t o_c = o_km + n_km, n_c = al((size_t)nC * sizeof(double));
+  const size_t o_p = o_c + n_c, n_p = al((size_t)nparts * nC * sizeof(float));
+  const size_t need2 = o_p + n_p;
   if (S->bytes2 < need2) {
     cudaFree(S->buf2);
     S->buf2 = nullptr;
@@ -441,7 +464,8 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
   double2* Mom = reinterpret_cast<double2*>(b2 + o_mom);
   T* Am = reinterpret_cast<T*>(b2 + o_am);
   T* Km = reinterpret_cast<T*>(b2 + o_km);
-  T* Cm = reinterpret_cast<T*>(b2 + o_c);
+  double* Cm = reinterpret_cast<double*>(b2 + o_c);
+  float* Cp = reinterpret_cast<float*>(b2 + o_p);
   // pass 2: bins, histogram, exclusive scan (on the host: the block ranges need it there too)
   LRT_CUDA(cudaMemsetAsync(count, 0, (size_t)(nbins + 1) * sizeof(int), s));
   sp_bins<<<grid, 256, 0, s>>>(x, df, np, x0, h, bin, count);
@@ -450,7 +474,8 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
   std::vector<int> cnt(nbins);
   LRT_CUDA(cudaMemcpyAsync(cnt.data(), count, nbins * sizeof(int), cudaMemcpyDeviceToHost, s));
   LRT_CUDA(cudaStreamSynchronize(s));
-  std::vector<int> start(nbins + 1, 0);
+  std::vector<int>& start = S->start_h;
+  start.assign(nbins + 1, 0);
   for (int j = 0; j < nbins; ++j) start[j + 1] = start[j] + cnt[j];
   const int npos = start[nbins];
   // block ranges of whole bins, about 2048 pairs each (a larger bin is one block)
@@ -490,7 +515,8 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
     LRT_CUDA(cudaGetLastError());
   }
   // pass 4: A; 5: the transform GEMM; 6: unpack
-  sp_assemble_A<T, M><<<grid, 256, 0, s>>>(Mom, ngg, nbins, 1.0, Am);
+  if (nbp > nbins) LRT_CUDA(cudaMemsetAsync(Am, 0, (size_t)2 * ngg * nbp * sizeof(T), s));
+  sp_assemble_A<T, M><<<grid, 256, 0, s>>>(Mom, ngg, nbins, nbp, 1.0, Am);
   count_launch(c);
   const size_t nfe = (size_t)c->nwi + c->neta;
   if (S->fe_n < nfe) {
@@ -505,7 +531,7 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
                            cudaMemcpyHostToDevice, s));
   LRT_CUDA(cudaStreamSynchronize(s));   // the eta list is read from a host vector
   sp_kernel_matrix<T><<<grid, 256, 0, s>>>(S->freqs_etas, S->freqs_etas + c->nwi, c->nwi, ncol, x0, h,
-                                           nbins, Km);
+                                           nbp, Km);
   count_launch(c);
   LRT_CUDA(cudaGetLastError());
   if (!S->blas && cublasCreate(&S->blas) != CUBLAS_STATUS_SUCCESS) {
@@ -513,20 +539,31 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
     return LRT_ECUDA;
   }
   cublasSetStream(S->blas, s);
-  const T one = 1, zero = 0;
+  // The sum over all bins cancels between the bins below and above each frequency: one FP32
+  // accumulation over ~10^4 bins loses ~1e-5 of the result to it, so the FP32 products are
+  // accumulated over SP_KCHUNK bins at a time and the chunks summed in FP64 (FP64 context:
+  // one DGEMM).
   cublasStatus_t st;
-  if constexpr (sizeof(T) == 8)
+  if constexpr (sizeof(T) == 4) {
+    const float one = 1.f, zero = 0.f;
+    st = cublasSgemmStridedBatched(S->blas, CUBLAS_OP_T, CUBLAS_OP_N, 2 * ngg, 2 * ncol, SP_KCHUNK,
+                                   &one, Am, nbp, SP_KCHUNK, Km, nbp, SP_KCHUNK, &zero, Cp, 2 * ngg,
+                                   nC, nparts);
+    if (st == CUBLAS_STATUS_SUCCESS) {
+      sp_reduce<<<grid, 256, 0, s>>>(Cp, nparts, nC, Cm);
+      count_launch(c);
+    }
+  } else {
+    const double one = 1, zero = 0;
     st = cublasDgemm(S->blas, CUBLAS_OP_T, CUBLAS_OP_N, 2 * ngg, 2 * ncol, nbins, &one, Am, nbins, Km,
                      nbins, &zero, Cm, 2 * ngg);
-  else
-    st = cublasSgemm(S->blas, CUBLAS_OP_T, CUBLAS_OP_N, 2 * ngg, 2 * ncol, nbins, &one, Am, nbins, Km,
-                     nbins, &zero, Cm, 2 * ngg);
+  }
   if (st != CUBLAS_STATUS_SUCCESS) {
     set_error("spectral transform GEMM failed");
     return LRT_ECUDA;
   }
   const double pref = 2.0 / (c->nk * c->volume) / (rho_scale * rho_scale);
-  sp_unpack<T><<<grid, 256, 0, s>>>(Cm, ngg, nG, ncol, pref, q.chi0);
+  sp_unpack<double><<<grid, 256, 0, s>>>(Cm, ngg, nG, ncol, pref, q.chi0);
   count_launch(c);
   LRT_CUDA(cudaGetLastError());
   return LRT_OK;
