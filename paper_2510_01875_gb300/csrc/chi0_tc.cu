@@ -535,53 +535,75 @@ __global__ void chi0_unpack(const double* __restrict__ C, long long ldr,
 // RI = sum Pr wi, IR = sum Pi wr, II = sum Pi wi give chi0(G,G') = (RR - II) + i(RI + IR) and
 // chi0(G',G) = (RR + II) + i(RI - IR).  FP32 products and per-thread FP32 partial sums over
 // 1024 pairs, flushed into FP64 (round-to-nearest, so unbiased), then FP64 atomics into chi0.
-// grid (G-tile pair I <= J of 16 x 16, pair range); block 64: each thread a 2 x 2 (G, G')
-// register tile (two 16-byte shared loads feed four entries); ZN etas per pass.
-constexpr int ZT = 16;   // G per tile side
+// Grid (pair range, tile of the G <= G' list); block 256, each thread E entries of the
+// row-major list of G <= G' pairs (no padding but in the last tile), the pair densities of
+// every G staged once per 32-pair chunk; ZN etas per pass.  8 FP32 FMAs per (entry, pair)
+// and eta: the work is that of the one frequency, so nothing is reused across columns.
 constexpr int ZE = 2;    // etas per pass of an eta list
+constexpr int ZL_THREADS = 256;
 struct ZEtas {
   float v[64];
 };
-template <int ZN>   // etas per pass: 1 (a single eta) or ZE
-__global__ void __launch_bounds__(64) chi0_zero_split_kernel(
+template <int ZN, int E>   // etas per pass (1, or ZE for an eta list); G <= G' pairs per thread
+__global__ void __launch_bounds__(ZL_THREADS, 1) chi0_zero_split_kernel(
     const float2* __restrict__ rho, int gpad, const float4* __restrict__ pw, long long np,
-    long long per, int nG, int nT, int neta, int e0, double scale, double2* __restrict__ chi0,
+    long long per, int nG, int ngg, int neta, int e0, double scale, double2* __restrict__ chi0,
     long long mat_stride, ZEtas etas) {
-  __shared__ __align__(16) float2 rI[32][ZT];
-  __shared__ __align__(16) float2 rJ[32][ZT];
-  __shared__ float2 ws[ZN][32];
-  int bp = blockIdx.x, I = 0;
-  while (bp >= nT - I) {
-    bp -= nT - I;
-    ++I;
-  }
-  const int J = I + bp;
-  const int ti = threadIdx.x >> 3, tj = threadIdx.x & 7;   // rows 2 ti, 2 ti + 1; cols 2 tj, 2 tj + 1
-  const int ne = min(ZN, neta - e0);
-  float acc[ZN][4][4];
-  double sum[ZN][4][4];
+  extern __shared__ __align__(16) float2 zs[];
+  float2* rs = zs;                        // [2][32 pairs][nG]: pair-major, so the lanes of a warp
+  float2* ws = zs + (size_t)64 * nG;      // (consecutive G') read without bank conflicts;
+                                          // [2][ZN][32] weights
+  const int tid = threadIdx.x;
+  int ga[E], gb[E];
 #pragma unroll
-  for (int e = 0; e < ZN; ++e)
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[e][k][c] = 0.f, sum[e][k][c] = 0.0;
-  const long long pb = (long long)blockIdx.y * per, pe = min(np, pb + per);
-  int nch = 0;
-  for (long long p0 = pb; p0 < pe; p0 += 32) {
-    __syncthreads();
-    for (int e2 = threadIdx.x; e2 < 2 * 32 * ZT; e2 += 64) {
-      const int half = e2 / (32 * ZT), r = e2 % (32 * ZT);
-      const int l = r % 32, g = r / 32;
-      const long long p = p0 + l;
-      const int GG = (half ? J : I) * ZT + g;
-      float2 v = make_float2(0.f, 0.f);
-      if (p < pe && GG < nG) v = rho[((size_t)((p >> 5) * gpad + GG) << 5) + (size_t)(p & 31)];
-      (half ? rJ : rI)[l][g] = v;
+  for (int k = 0; k < E; ++k) {
+    const int idx = blockIdx.y * (ZL_THREADS * E) + k * ZL_THREADS + tid;
+    ga[k] = -1;
+    gb[k] = 0;
+    if (idx < ngg) {   // entry idx of the row-major list of (G, G'), G <= G'
+      int G = 0, rem = idx;
+      while (rem >= nG - G) {
+        rem -= nG - G;
+        ++G;
+      }
+      ga[k] = G;
+      gb[k] = G + rem;
     }
-    if (threadIdx.x < 32) {
-      const int l = threadIdx.x;
-      const long long p = p0 + l;
+  }
+  const int ne = min(ZN, neta - e0);
+  float acc[E][ZN][4];
+  double sum[E][ZN][4];
+#pragma unroll
+  for (int k = 0; k < E; ++k)
+#pragma unroll
+    for (int e = 0; e < ZN; ++e)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[k][e][c] = 0.f, sum[k][e][c] = 0.0;
+  const long long pb = (long long)blockIdx.x * per, pe = min(np, pb + per);
+  // double-buffered chunks: the pair densities of chunk c + 1 arrive by asynchronous copies
+  // while chunk c is summed
+  const int nchunk = (int)((pe - pb + 31) / 32);
+  auto issue = [&](int c) {
+    const long long p0 = pb + 32LL * c;   // a multiple of 32: one 32-pair group of the layout
+    const float2* src = rho + ((size_t)(p0 >> 5) * gpad << 5);
+    const uint32_t dst = smem_u32(rs + (size_t)(c & 1) * 32 * nG);
+    for (int e = tid; e < 32 * nG; e += ZL_THREADS) {
+      const int G = e >> 5, i = e & 31;
+      const bool ok = p0 + i < pe;
+      cp_async8(dst + (uint32_t)(i * nG + G) * 8u, ok ? (const void*)(src + ((size_t)G << 5) + i) : (const void*)rho,
+                ok ? 8u : 0u);
+    }
+    cp_async_commit();
+  };
+  if (nchunk > 0) issue(0);
+  int nch = 0;
+  for (int ck = 0; ck < nchunk; ++ck) {
+    const long long p0 = pb + 32LL * ck;
+    float2* rb = rs + (size_t)(ck & 1) * 32 * nG;
+    float2* wb = ws + (size_t)(ck & 1) * ZN * 32;
+    cp_async_wait_all();
+    if (tid < 32) {
+      const long long p = p0 + tid;
       const float4 q = p < pe ? pw[p] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float x = q.x + q.y;
 #pragma unroll
@@ -592,49 +614,49 @@ __global__ void __launch_bounds__(64) chi0_zero_split_kernel(
           const float r = 1.0f / (x * x + eta * eta);
           w = make_float2(q.z * x * r, -q.z * eta * r);   // df sB / (x + i eta)
         }
-        ws[e][l] = w;
+        wb[e * 32 + tid] = w;
       }
     }
+    // chunk ck is complete for every thread, and the other buffer's readers (chunk ck - 1) are
+    // done
     __syncthreads();
+    if (ck + 1 < nchunk) issue(ck + 1);
 #pragma unroll 2
-    for (int l = 0; l < 32; ++l) {
-      const float4 A = *reinterpret_cast<const float4*>(&rI[l][2 * ti]);
-      const float4 B = *reinterpret_cast<const float4*>(&rJ[l][2 * tj]);
-      // a conj(b) for the four (row, col) pairs: k = 2 r + c
-      float pr[4], pi[4];
-      pr[0] = A.x * B.x + A.y * B.y, pi[0] = A.y * B.x - A.x * B.y;
-      pr[1] = A.x * B.z + A.y * B.w, pi[1] = A.y * B.z - A.x * B.w;
-      pr[2] = A.z * B.x + A.w * B.y, pi[2] = A.w * B.x - A.z * B.y;
-      pr[3] = A.z * B.z + A.w * B.w, pi[3] = A.w * B.z - A.z * B.w;
+    for (int i = 0; i < 32; ++i) {
+      float2 w[ZN];
 #pragma unroll
-      for (int e = 0; e < ZN; ++e) {
-        const float2 w = ws[e][l];
+      for (int e = 0; e < ZN; ++e) w[e] = wb[e * 32 + i];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          acc[e][k][0] = fmaf(pr[k], w.x, acc[e][k][0]);
-          acc[e][k][1] = fmaf(pr[k], w.y, acc[e][k][1]);
-          acc[e][k][2] = fmaf(pi[k], w.x, acc[e][k][2]);
-          acc[e][k][3] = fmaf(pi[k], w.y, acc[e][k][3]);
+      for (int k = 0; k < E; ++k) {
+        if (ga[k] < 0) continue;
+        const float2 a = rb[i * nG + ga[k]], b = rb[i * nG + gb[k]];
+        const float pr = a.x * b.x + a.y * b.y, pi = a.y * b.x - a.x * b.y;   // a conj(b)
+#pragma unroll
+        for (int e = 0; e < ZN; ++e) {
+          acc[k][e][0] = fmaf(pr, w[e].x, acc[k][e][0]);
+          acc[k][e][1] = fmaf(pr, w[e].y, acc[k][e][1]);
+          acc[k][e][2] = fmaf(pi, w[e].x, acc[k][e][2]);
+          acc[k][e][3] = fmaf(pi, w[e].y, acc[k][e][3]);
         }
       }
     }
-    if (++nch == 32) {
+    if (++nch == 32) {   // FP32 partial sums over 1024 pairs, then into FP64
       nch = 0;
 #pragma unroll
-      for (int e = 0; e < ZN; ++e)
+      for (int k = 0; k < E; ++k)
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int e = 0; e < ZN; ++e)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) sum[e][k][c] += (double)acc[e][k][c], acc[e][k][c] = 0.f;
+          for (int c = 0; c < 4; ++c) sum[k][e][c] += (double)acc[k][e][c], acc[k][e][c] = 0.f;
     }
   }
-  for (int k = 0; k < 4; ++k) {
-    const int gi = 2 * ti + (k >> 1), gj = 2 * tj + (k & 1);
-    const int G = I * ZT + gi, Gp = J * ZT + gj;
-    if (G >= nG || Gp >= nG || (I == J && gi > gj)) continue;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    if (ga[k] < 0) continue;
+    const int G = ga[k], Gp = gb[k];
     for (int e = 0; e < ne; ++e) {
-      const double RR = sum[e][k][0] + acc[e][k][0], RI = sum[e][k][1] + acc[e][k][1];
-      const double IR = sum[e][k][2] + acc[e][k][2], II = sum[e][k][3] + acc[e][k][3];
+      const double RR = sum[k][e][0] + acc[k][e][0], RI = sum[k][e][1] + acc[k][e][1];
+      const double IR = sum[k][e][2] + acc[k][e][2], II = sum[k][e][3] + acc[k][e][3];
       double2* m = chi0 + (size_t)(e0 + e) * mat_stride;
       atomicAdd(&m[(size_t)G * nG + Gp].x, scale * (RR - II));
       atomicAdd(&m[(size_t)G * nG + Gp].y, scale * (RI + IR));
@@ -1137,8 +1159,12 @@ static lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho,
   int dev = 0, nsm = 0;
   LRT_CUDA(cudaGetDevice(&dev));
   LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int nT = (nG + ZT - 1) / ZT, nTP = nT * (nT + 1) / 2;
-  long long nsplit = std::max<long long>(1, (32LL * nsm + nTP - 1) / nTP);
+  const int ngg = nG * (nG + 1) / 2;
+  const bool list = c->neta > 1;
+  const int per_block = ZL_THREADS * (list ? 4 : 7);
+  const int ntile = (ngg + per_block - 1) / per_block;
+  // about four blocks per SM in all, each over one range of pairs (a multiple of 32)
+  long long nsplit = std::max<long long>(1, (4LL * nsm + ntile - 1) / ntile);
   long long per = (c->np + nsplit - 1) / nsplit;
   per = (per + 31) / 32 * 32;
   nsplit = (c->np + per - 1) / per;
@@ -1146,24 +1172,21 @@ static lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho,
   const double scale = 2.0 / (c->nk * c->volume) / (rs * rs * (double)sB);
   ZEtas E{};   // the etas travel as a kernel argument (at most 64)
   for (int j = 0; j < c->neta; ++j) E.v[j] = (float)c->etas[j];
+  const size_t smem = ((size_t)64 * nG + (size_t)(list ? ZE : 1) * 64) * sizeof(float2);
+  auto k1 = chi0_zero_split_kernel<1, 7>;
+  auto k2 = chi0_zero_split_kernel<ZE, 4>;
+  LRT_CUDA(cudaFuncSetAttribute(list ? k2 : k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int e0 = 0; e0 < c->neta; e0 += ZE) {
-    if (c->neta == 1)
-      chi0_zero_split_kernel<1><<<dim3(nTP, (unsigned)nsplit), 64, 0, s>>>(
-          (const float2*)rho, c->rho_gpad, q.sp.pw, c->np, per, nG, nT, c->neta, e0, scale, base,
-          (long long)c->nwi * mat, E);
-    else
-      chi0_zero_split_kernel<ZE><<<dim3(nTP, (unsigned)nsplit), 64, 0, s>>>(
-          (const float2*)rho, c->rho_gpad, q.sp.pw, c->np, per, nG, nT, c->neta, e0, scale, base,
-          (long long)c->nwi * mat, E);
+    (list ? k2 : k1)<<<dim3((unsigned)nsplit, (unsigned)ntile), ZL_THREADS, smem, s>>>(
+        (const float2*)rho, c->rho_gpad, q.sp.pw, c->np, per, nG, ngg, c->neta, e0, scale, base,
+        (long long)c->nwi * mat, E);
     count_launch(c);
     LRT_CUDA(cudaGetLastError());
+    if (!list) break;
   }
   return LRT_OK;
 }
 
-// chi0 of q_begin .. q_end - 1 on the tensor path.  q's whose pair densities fit in their own
-// buffers next to the others' run in one launch; the rest run one at a time in the shared
-// pair-density buffer.
 // Split-form pair weights {Delta_hi, Delta_lo, df sB, 0} of q in q.sp.pw (allocated on first
 // use) for the engines that need them without the tensor plan; sB is returned.
 lrt_status split_pair_weights(const lrt_ctx* c, QData& q, float* sB, cudaStream_t s) {
@@ -1183,6 +1206,9 @@ lrt_status split_pair_weights(const lrt_ctx* c, QData& q, float* sB, cudaStream_
   return LRT_OK;
 }
 
+// chi0 of q_begin .. q_end - 1 on the tensor path.  q's whose pair densities fit in their own
+// buffers next to the others' run in one launch; the rest run one at a time in the shared
+// pair-density buffer.
 lrt_status launch_chi0_split_range(lrt_ctx* c, int q_begin, int q_end, cudaStream_t s) {
   if (c->np <= 0) {
     set_error("no pairs to contract");

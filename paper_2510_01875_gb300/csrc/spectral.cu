@@ -26,14 +26,16 @@
 #include <cstring>
 
 #include "lrt_internal.h"
+#include "tc_ptx.cuh"
 
 namespace lrt {
 namespace {
 
+using namespace tcx;
+
 constexpr int SP_THREADS = 256;
 constexpr int SP_E = 4;                          // G <= G' pairs per thread
 constexpr int SP_TILE = SP_THREADS * SP_E;       // G <= G' pairs per block
-constexpr int SP_CHUNK = 32;                     // sorted pairs staged per step
 constexpr int SP_KCHUNK = 256;                   // bins per FP32 partial product of the transform
 
 // Lagrange basis of order m as polynomials in the fraction f: L_c(f) = sum_k a[c][k] f^k.
@@ -135,6 +137,12 @@ __global__ void sp_scatter(const double* __restrict__ x, const double* __restric
   }
 }
 
+// sorted pairs per staged chunk: two chunks of N_G <= 300 complex values fit in shared memory
+template <typename T>
+struct SpChunk {
+  static constexpr int value = sizeof(T) == 8 ? 16 : 32;
+};
+
 template <typename T>
 struct V2;
 template <>
@@ -169,10 +177,13 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
     const int* __restrict__ perm, const int* __restrict__ sbin, const T* __restrict__ coef,
     const int2* __restrict__ range, double2* __restrict__ Mom) {
   using T2 = typename V2<T>::type;
+  constexpr int CH = SpChunk<T>::value;
   extern __shared__ __align__(16) unsigned char sp_smem[];
-  T2* rs = reinterpret_cast<T2*>(sp_smem);                     // [SP_CHUNK][nG]
-  T* cs = reinterpret_cast<T*>(rs + (size_t)nG * SP_CHUNK);    // [SP_CHUNK][M + 1]
-  int* bs = reinterpret_cast<int*>(cs + SP_CHUNK * (M + 1));   // [SP_CHUNK]
+  // two buffers of [CH pairs][nG] pair densities (pair-major, so the lanes of a warp, which
+  // hold consecutive G <= G' pairs, read consecutive G' without bank conflicts), [CH][M + 1]
+  // moment coefficients and [CH] bins: chunk c + 1 arrives by asynchronous copies while chunk
+  // c is summed
+  const size_t bufsz = (size_t)CH * nG * sizeof(T2) + CH * (M + 1) * sizeof(T) + CH * sizeof(int);
   const int tid = threadIdx.x;
   const int2 rg = range[blockIdx.x];
   // this thread's G <= G' pairs (row-major upper triangle)
@@ -228,29 +239,56 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
 #pragma unroll
       for (int k = 0; k <= M; ++k) sr[e][k] = si[e][k] = cr[e][k] = ci[e][k] = 0;
   };
-  for (int i0 = rg.x; i0 < rg.y; i0 += SP_CHUNK) {
-    const int n = min(SP_CHUNK, rg.y - i0);
-    __syncthreads();
-    // (pair-major in shared memory, so that the lanes of a warp, which hold consecutive G <= G'
-    // pairs, read consecutive G' without bank conflicts; every global read is a gather anyway)
-    for (int e = tid; e < nG * SP_CHUNK; e += SP_THREADS) {
+  const int nchunk = (rg.y - rg.x + CH - 1) / CH;
+  auto issue = [&](int ck) {
+    const int i0 = rg.x + ck * CH, n = min(CH, rg.y - i0);
+    unsigned char* bufp = sp_smem + (size_t)(ck & 1) * bufsz;
+    const uint32_t rdst = smem_u32(bufp);
+    const uint32_t cdst = rdst + (uint32_t)(CH * nG * sizeof(T2));
+    const uint32_t bdst = cdst + (uint32_t)(CH * (M + 1) * sizeof(T));
+    for (int e = tid; e < nG * CH; e += SP_THREADS) {
       const int i = e / nG, G = e % nG;
-      T2 v;
-      v.x = 0;
-      v.y = 0;
-      if (i < n) {
+      const bool ok = i < n;
+      const void* src = rho_v;   // (a valid address for the zero-filling copies)
+      if (ok) {
         const long long p = perm[i0 + i];
-        if constexpr (sizeof(T) == 8) {
-          v = reinterpret_cast<const double2*>(rho_v)[(size_t)G * ld + p];
-        } else {
-          v = reinterpret_cast<const float2*>(rho_v)[((size_t)(p >> 5) * gpad + G) * 32 + (p & 31)];
-        }
+        if constexpr (sizeof(T) == 8)
+          src = reinterpret_cast<const double2*>(rho_v) + (size_t)G * ld + p;
+        else
+          src = reinterpret_cast<const float2*>(rho_v) + ((size_t)(p >> 5) * gpad + G) * 32 + (p & 31);
       }
-      rs[e] = v;
+      if constexpr (sizeof(T) == 8)
+        cp_async16(rdst + (uint32_t)e * 16u, src, ok ? 16u : 0u);
+      else
+        cp_async8(rdst + (uint32_t)e * 8u, src, ok ? 8u : 0u);
     }
-    for (int e = tid; e < n * (M + 1); e += SP_THREADS) cs[e] = coef[(size_t)i0 * (M + 1) + e];
-    if (tid < n) bs[tid] = sbin[i0 + tid];
+    for (int e = tid; e < CH * (M + 1); e += SP_THREADS) {
+      const bool ok = e < n * (M + 1);
+      const void* src = ok ? (const void*)(coef + (size_t)i0 * (M + 1) + e) : (const void*)coef;
+      if constexpr (sizeof(T) == 8)
+        cp_async8(cdst + (uint32_t)e * 8u, src, ok ? 8u : 0u);
+      else
+        cp_async4(cdst + (uint32_t)e * 4u, src, ok ? 4u : 0u);
+    }
+    if (tid < CH) {
+      const bool ok = tid < n;
+      cp_async4(bdst + (uint32_t)tid * 4u, ok ? (const void*)(sbin + i0 + tid) : (const void*)sbin,
+                ok ? 4u : 0u);
+    }
+    cp_async_commit();
+  };
+  if (nchunk > 0) issue(0);
+  for (int ck = 0; ck < nchunk; ++ck) {
+    const int n = min(CH, rg.y - (rg.x + ck * CH));
+    const unsigned char* bufp = sp_smem + (size_t)(ck & 1) * bufsz;
+    const T2* rs = reinterpret_cast<const T2*>(bufp);
+    const T* cs = reinterpret_cast<const T*>(rs + (size_t)CH * nG);
+    const int* bs = reinterpret_cast<const int*>(cs + CH * (M + 1));
+    cp_async_wait_all();
+    // chunk ck is complete for every thread, and the other buffer's readers (chunk ck - 1) are
+    // done
     __syncthreads();
+    if (ck + 1 < nchunk) issue(ck + 1);
     for (int i = 0; i < n; ++i) {
       const int j = bs[i];   // the same for every thread
       if (j != cur) {
@@ -503,8 +541,9 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
   // pass 3: moments per bin (bins without pairs stay zero)
   LRT_CUDA(cudaMemsetAsync(Mom, 0, (size_t)nbins * (M + 1) * ngg * sizeof(double2), s));
   if (npos > 0) {
-    const size_t smem = (size_t)nG * SP_CHUNK * sizeof(typename V2<T>::type) + SP_CHUNK * (M + 1) * sizeof(T) +
-                        SP_CHUNK * sizeof(int);
+    constexpr int CH = SpChunk<T>::value;
+    const size_t smem = 2 * ((size_t)nG * CH * sizeof(typename V2<T>::type) + CH * (M + 1) * sizeof(T) +
+                             CH * sizeof(int));
     auto kern = sp_moments<T, M>;
     LRT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 g((unsigned)ranges.size(), (unsigned)((ngg + SP_TILE - 1) / SP_TILE));

@@ -1,5 +1,5 @@
 // Device-side building blocks shared by the tcgen05 kernels: mbarriers with bounded waits,
-// bulk copies, proxy and tensor-memory fences, cluster addressing, shared-memory matrix
+// bulk and 8-byte asynchronous copies, proxy and tensor-memory fences, cluster addressing, shared-memory matrix
 // descriptors and MMA issue (CTA pairs and single CTAs), the 128-byte-swizzled MN-major tile
 // addressing, the 16-bit hi/lo split, and shared-memory loads and stores by address.
 #pragma once
@@ -16,6 +16,24 @@ constexpr unsigned long long kTimeoutNs = 2000000000ull;   // bound of every mba
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
+// Asynchronous 4-, 8- or 16-byte copy global -> shared (cp.async, L1-allocating); src_bytes = 0 writes
+// zeros and reads nothing (src must still be a valid address).  Completion per thread by
+// cp_async_wait_all; other threads see the data after a barrier.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long gtime() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
