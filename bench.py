@@ -311,18 +311,26 @@ def run_ours(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def chi0_kernel_digest(path):
+    """sha256 of the contraction kernel's source (the text from its template header to the unpack
+    kernel that follows it), so that host-side edits of the file keep a capture valid."""
+    import hashlib
+    text = open(path, "rb").read()
+    a = text.find(b"template <bool BF, int NS, int NSR, bool ME>")
+    b = text.find(b"// chi0[i][G][G'] from the FP64 sums", a)
+    return hashlib.sha256(text[a:b] if a >= 0 and b > a else text).hexdigest()
+
+
 def profiled_traffic(precision, np_per_q):
     """DRAM bytes per contraction launch from the committed ncu summary of the kernel
     (dram__bytes_read.sum + dram__bytes_write.sum on a 4^3-k case, per pair, scaled by this
     launch's pair count), or None when the kernel source has changed since the capture or the
     precision was not the profiled one."""
     import glob
-    import hashlib
     if precision != "fp16x3":
         return None
     here = os.path.dirname(os.path.abspath(__file__))
-    src = os.path.join(here, "paper_2510_01875_gb300", "csrc", "chi0_tc.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    digest = chi0_kernel_digest(os.path.join(here, "paper_2510_01875_gb300", "csrc", "chi0_tc.cu"))
     for path in sorted(glob.glob(os.path.join(here, "profiles", "chi0_tc_kernel_*.md"))):
         text = open(path).read()
         m = re.search(r"sha256 prefix `([0-9a-f]+)`", text)

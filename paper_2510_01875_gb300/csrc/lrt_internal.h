@@ -227,6 +227,7 @@ lrt_status adopt_orbitals(lrt_ctx* c, int iq, cudaStream_t s);
 lrt_status launch_chi0_spectral(lrt_ctx* c, QData& q, const void* rho, cudaStream_t s);
 void free_spectral_state(lrt_ctx* c);
 lrt_status split_pair_weights(const lrt_ctx* c, QData& q, float* sB, cudaStream_t s);
+lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho, float sB, cudaStream_t s);
 double fxc_alda(double n);
 double fxc_model(double qg, double n, double A, double B, double C);
 // K_GG = 4 pi/|q+G|^2 + f_xc for the context's kernel, from Q.qg2 (host vector only).
