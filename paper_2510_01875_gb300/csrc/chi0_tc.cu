@@ -70,8 +70,7 @@ constexpr int PW_OFF = RROWS * KS * 8;               // pair weights after the r
 constexpr int R_STAGE = PW_OFF + KS * 16;            // rho rows, 32 float4 pair weights
 constexpr int NSUB = NACC * 64 / 16;                 // 4 x 4 (G, G') sub-blocks per super-tile
 constexpr int kFlushStages = 64;   // FP32 accumulation period: 64 stages = 2048 pairs
-constexpr int CW = 32;                  // accumulator columns per tensor-memory load
-constexpr int NCHUNK = NACC * TN / CW;  // CW-column pieces of the accumulators per lane
+constexpr int NCHUNK = NACC * TN / 16;  // 16-column pieces of the accumulators per lane
 
 // One q of a launch: its pair densities, weights, tables and FP64 sums.
 struct QDesc {
@@ -99,7 +98,7 @@ struct Params {
   const QDesc* qd;            // [nq of the launch]
   const int2* units;          // [nunits] (q of the launch, unit within the q), q-major
   int nunits;
-  float4* stage;              // [gridDim.x][4 warps][NCHUNK][CW / 4][32 lanes] accumulator staging
+  float4* stage;              // [gridDim.x][4 warps][NCHUNK][4][32 lanes] accumulator staging
   int* status;
   int flush;                  // stages per accumulator period
   float eta;
@@ -341,69 +340,46 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
     } else if (warp == WMMA) {
       // ---------------- MMA issuer (even CTA) ----------------
       if (leader) {
-        // both accumulators take every stage; at the start of a period accumulator 0 (handed
-        // back first by the epilogues) runs up to NS - 1 stages ahead while accumulator 1 is
-        // still being read out, and accumulator 1 then catches up on the same stages
-        auto wait_full = [&](uint32_t idx) -> bool {
-          bool w = true;
-          if (lane == 0) w = mbar_wait(&full[idx % NS], (idx / NS) & 1, &abort_s, P.status);
-          w = __shfl_sync(0xffffffffu, w, 0);
-          if (w) tc_fence_after();
-          return w;
-        };
-        auto wait_acc = [&](int a) -> bool {
-          // first use of accumulator a in this period: both epilogues must have read it
-          bool w = true;
-          if (lane == 0) w = mbar_wait(&acc_empty[a], (pc & 1) ^ 1, &abort_s, P.status);
-          w = __shfl_sync(0xffffffffu, w, 0);
-          if (w) tc_fence_after();
-          return w;
-        };
-        auto issue = [&](int a, uint32_t idx, bool first) {
-          if (lane == 0 && a < nacc) {
-            const uint32_t sst = base + (idx % NS) * STAGE_BYTES;
+        bool ok = true;
+        for (int per = 0; per < nper && ok; ++per, ++pc) {
+          const int s0 = per * P.flush, s1 = min(nstage, s0 + P.flush);
+          for (int st_ = s0; st_ < s1; ++st_, ++it) {
+            const int s = it % NS;
+            if (lane == 0) ok = mbar_wait(&full[s], (it / NS) & 1, &abort_s, P.status);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t sst = base + s * STAGE_BYTES;
             const uint32_t bH = sst + NACC * 2 * A_BYTES, bL = bH + B_BYTES;
-            const uint32_t aH = sst + a * 2 * A_BYTES, aL = aH + A_BYTES;
-            const uint32_t d = tmem + a * TN;
 #pragma unroll
             for (int kk = 0; kk < KS / 16; ++kk) {
               const uint64_t dBh = sdesc(bH + kk * 2 * B_SBO, 1024, B_SBO);
               const uint64_t dBl = sdesc(bL + kk * 2 * B_SBO, 1024, B_SBO);
-              const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
-              const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
-              mma2(d, dAh, dBh, idesc, (first && kk == 0) ? 0u : 1u);
-              mma2(d, dAh, dBl, idesc, 1u);
-              mma2(d, dAl, dBh, idesc, 1u);
+#pragma unroll
+              for (int a = 0; a < NACC; ++a) {
+                if (st_ == s0 && kk == 0) {
+                  // first use of accumulator a in this period: both epilogues must have read it
+                  if (lane == 0) ok = mbar_wait(&acc_empty[a], (pc & 1) ^ 1, &abort_s, P.status);
+                  ok = __shfl_sync(0xffffffffu, ok, 0);
+                  if (!ok) break;
+                  tc_fence_after();
+                }
+                if (lane == 0 && a < nacc) {
+                  const uint32_t aH = sst + a * 2 * A_BYTES, aL = aH + A_BYTES;
+                  const uint64_t dAh = sdesc(aH + kk * 2 * A_SBO, 1024, A_SBO);
+                  const uint64_t dAl = sdesc(aL + kk * 2 * A_SBO, 1024, A_SBO);
+                  const uint32_t d = tmem + a * TN;
+                  mma2(d, dAh, dBh, idesc, (st_ > s0 || kk > 0) ? 1u : 0u);
+                  mma2(d, dAh, dBl, idesc, 1u);
+                  mma2(d, dAl, dBh, idesc, 1u);
+                }
+                __syncwarp();
+              }
+              if (!ok) break;
             }
-          }
-          __syncwarp();
-        };
-        auto release = [&](uint32_t idx) {
-          if (lane == 0) mma_commit_pair(&empty[idx % NS]);
-          __syncwarp();
-        };
-        bool ok = true;
-        for (int per = 0; per < nper && ok; ++per, ++pc) {
-          const int s0 = per * P.flush, s1 = min(nstage, s0 + P.flush);
-          const int L = min(s1 - s0, NS - 1);
-          ok = wait_acc(0);
-          for (int j = 0; j < L && ok; ++j) {
-            ok = wait_full(it + j);
-            if (ok) issue(0, it + j, j == 0);
-          }
-          if (ok) ok = wait_acc(1);
-          if (!ok) break;
-          for (int j = 0; j < L; ++j) {
-            issue(1, it + j, j == 0);
-            release(it + j);
-          }
-          it += L;
-          for (int st_ = s0 + L; st_ < s1; ++st_, ++it) {
-            ok = wait_full(it);
             if (!ok) break;
-            issue(0, it, false);
-            issue(1, it, false);
-            release(it);
+            if (lane == 0) mma_commit_pair(&empty[s]);
+            __syncwarp();
           }
           if (!ok) break;
           if (lane == 0) mma_commit_pair(&acc_full);
@@ -434,7 +410,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       // rows and n_n * TN columns, so no bounds checks are needed (padding rows and columns
       // collect values that are never read).
       const int q = warp & 3;            // tensor-memory lane quadrant of this warp
-      float4* stg = P.stage + ((size_t)blockIdx.x * 4 + q) * (NCHUNK * (CW / 4) * 32) + lane;
+      float4* stg = P.stage + ((size_t)blockIdx.x * 4 + q) * (NCHUNK * 4 * 32) + lane;
       const long long grow0 = (long long)st * (NACC * TM) + sub0 * 32 + q * 32 + lane;
       const size_t ldr = (size_t)D.ldr;
       double* cbase = D.C + (size_t)(U.nt * TN) * ldr;
@@ -447,29 +423,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
         tc_fence_after();
 #pragma unroll 1
         for (int ch = 0; ch < NCHUNK; ++ch) {
-          const int a = ch / (TN / CW), c = ch % (TN / CW);
+          const int a = ch / (TN / 16), c = ch % (TN / 16);
           if (a >= nacc) {
             // accumulator 1 of a half unit holds nothing: hand it back unread
-            if (c == TN / CW - 1) {
+            if (c == TN / 16 - 1) {
               tc_fence_before();
               __syncwarp();
               if (lane == 0) mbar_arrive_cluster(acc_empty0 + a * 8);
             }
             continue;
           }
-          uint32_t r[CW];
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + c * CW;
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * TN + c * 16;
           asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          float4* d = stg + (size_t)ch * (CW / 4) * 32;
+          float4* d = stg + (size_t)ch * 128;
 #pragma unroll
-          for (int k = 0; k < CW / 4; ++k)
+          for (int k = 0; k < 4; ++k)
             d[32 * k] = make_float4(__uint_as_float(r[4 * k]), __uint_as_float(r[4 * k + 1]),
                                     __uint_as_float(r[4 * k + 2]), __uint_as_float(r[4 * k + 3]));
-          if (c == TN / CW - 1) {
+          if (c == TN / 16 - 1) {
             // accumulator a has been read: hand it back
             tc_fence_before();
             __syncwarp();
@@ -478,17 +457,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
         }
 #pragma unroll 1
         for (int ch = 0; ch < NCHUNK; ++ch) {
-          const int a = ch / (TN / CW), c = ch % (TN / CW);
+          const int a = ch / (TN / 16), c = ch % (TN / 16);
           if (a >= nacc) break;
-          const float4* sp = stg + (size_t)ch * (CW / 4) * 32;
-          double* cp = cbase + (size_t)(c * CW) * ldr + grow0 + a * TM;
-#pragma unroll 2
-          for (int k = 0; k < CW / 4; ++k) {
-            const float4 v = sp[32 * k];
-            red_add_f64(cp, (double)v.x);
-            red_add_f64(cp + ldr, (double)v.y);
-            red_add_f64(cp + 2 * ldr, (double)v.z);
-            red_add_f64(cp + 3 * ldr, (double)v.w);
+          const float4* sp = stg + (size_t)ch * 128;
+          float4 v[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[k] = sp[32 * k];
+          double* cp = cbase + (size_t)(c * 16) * ldr + grow0 + a * TM;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            red_add_f64(cp, (double)v[k].x);
+            red_add_f64(cp + ldr, (double)v[k].y);
+            red_add_f64(cp + 2 * ldr, (double)v[k].z);
+            red_add_f64(cp + 3 * ldr, (double)v[k].w);
             cp += 4 * ldr;
           }
         }
@@ -884,7 +865,7 @@ static lrt_status launch_tables(const lrt_ctx* c, bool bf, int v, int nunits, cu
   int ncl = 0;
   LRT_TRY(cluster_capacity(c, bf, v, &ncl));
   const int grid = 2 * std::min(ncl, std::max(1, nunits));
-  const size_t need = (size_t)grid * 4 * NCHUNK * (CW / 4) * 32 * sizeof(float4);
+  const size_t need = (size_t)grid * 4 * NCHUNK * 4 * 32 * sizeof(float4);
   if (T->stage_bytes < need) {
     cudaFree(T->stage);
     T->stage = nullptr;

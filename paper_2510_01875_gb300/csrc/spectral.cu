@@ -33,9 +33,19 @@ namespace {
 
 using namespace tcx;
 
-constexpr int SP_THREADS = 256;
-constexpr int SP_E = 4;                          // G <= G' pairs per thread
-constexpr int SP_TILE = SP_THREADS * SP_E;       // G <= G' pairs per block
+// Block shape of the moments kernel: the FP32 form (split contexts) keeps its compensated bin
+// totals in shared memory and runs 32 warps of 2 G <= G' pairs each; the FP64 form keeps them
+// in registers, 8 warps of 4 pairs each.  Either way a block covers 2048 or 1024 of the pairs.
+template <typename T>
+struct SpCfg;
+template <>
+struct SpCfg<float> {
+  static constexpr int threads = 1024, E = 2;
+};
+template <>
+struct SpCfg<double> {
+  static constexpr int threads = 256, E = 4;
+};
 constexpr int SP_KCHUNK = 256;                   // bins per FP32 partial product of the transform
 
 // Lagrange basis of order m as polynomials in the fraction f: L_c(f) = sum_k a[c][k] f^k.
@@ -137,12 +147,6 @@ __global__ void sp_scatter(const double* __restrict__ x, const double* __restric
   }
 }
 
-// sorted pairs per staged chunk: two chunks of N_G <= 300 complex values fit in shared memory
-template <typename T>
-struct SpChunk {
-  static constexpr int value = sizeof(T) == 8 ? 16 : 32;
-};
-
 template <typename T>
 struct V2;
 template <>
@@ -168,29 +172,33 @@ __device__ __forceinline__ void kadd(T& s, T& c, T v) {
 }
 
 // Moments of whole bins: block b takes the sorted positions [range[b].x, range[b].y) (whole
-// bins) and SP_TILE of the G <= G' pairs (blockIdx.y).  rho: FP64 [G][ld] (T = double) or the
+// bins) and threads x E of the G <= G' pairs (blockIdx.y).  rho: FP64 [G][ld] (T = double) or the
 // split form's blocked FP32 [p/32][gpad][32] (T = float, values scaled by a power of two that
 // the caller removes).  Mom [nbins][M + 1][ngg] complex FP64.
-template <typename T, int M>
-__global__ void __launch_bounds__(SP_THREADS) sp_moments(
+template <typename T, int M, int CH>   // CH: sorted pairs per staged chunk
+__global__ void __launch_bounds__(SpCfg<T>::threads, 1) sp_moments(
     const void* __restrict__ rho_v, long long ld, int gpad, int nG, int ngg,
     const int* __restrict__ perm, const int* __restrict__ sbin, const T* __restrict__ coef,
     const int2* __restrict__ range, double2* __restrict__ Mom) {
   using T2 = typename V2<T>::type;
-  constexpr int CH = SpChunk<T>::value;
+  constexpr int NT = SpCfg<T>::threads, SP_E = SpCfg<T>::E, SP_TILE = NT * SP_E;
+  constexpr bool F32 = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char sp_smem[];
   // two buffers of [CH pairs][nG] pair densities (pair-major, so the lanes of a warp, which
   // hold consecutive G <= G' pairs, read consecutive G' without bank conflicts), [CH][M + 1]
   // moment coefficients and [CH] bins: chunk c + 1 arrives by asynchronous copies while chunk
   // c is summed
   const size_t bufsz = (size_t)CH * nG * sizeof(T2) + CH * (M + 1) * sizeof(T) + CH * sizeof(int);
+  // FP32 form: the compensated bin totals (sum re, sum im, compensation re, im) of every
+  // (pair, k) of this thread, [SP_E (M + 1) 4][NT], after the two chunk buffers
+  float* tot = reinterpret_cast<float*>(sp_smem + 2 * bufsz);
   const int tid = threadIdx.x;
   const int2 rg = range[blockIdx.x];
   // this thread's G <= G' pairs (row-major upper triangle)
   int ga[SP_E], gb[SP_E];
 #pragma unroll
   for (int e = 0; e < SP_E; ++e) {
-    const int idx = blockIdx.y * SP_TILE + e * SP_THREADS + tid;
+    const int idx = blockIdx.y * SP_TILE + e * NT + tid;
     ga[e] = -1;
     gb[e] = 0;
     if (idx < ngg) {
@@ -203,21 +211,45 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
       gb[e] = G + rem;
     }
   }
-  T sr[SP_E][M + 1], si[SP_E][M + 1];   // bin totals (compensated)
-  T cr[SP_E][M + 1], ci[SP_E][M + 1];
   T pr[SP_E][M + 1], pi[SP_E][M + 1];   // this chunk's partial sums
+  T sr[SP_E][M + 1], si[SP_E][M + 1];   // FP64 form: the bin totals
+  auto tref = [&](int e, int k, int j) -> float& { return tot[((e * (M + 1) + k) * 4 + j) * NT + tid]; };
+  auto zero_totals = [&]() {
+#pragma unroll
+    for (int e = 0; e < SP_E; ++e)
+#pragma unroll
+      for (int k = 0; k <= M; ++k) {
+        if constexpr (F32) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tref(e, k, j) = 0.f;
+        } else {
+          sr[e][k] = si[e][k] = 0;
+        }
+      }
+  };
 #pragma unroll
   for (int e = 0; e < SP_E; ++e)
 #pragma unroll
-    for (int k = 0; k <= M; ++k) sr[e][k] = si[e][k] = cr[e][k] = ci[e][k] = pr[e][k] = pi[e][k] = 0;
+    for (int k = 0; k <= M; ++k) pr[e][k] = pi[e][k] = 0;
+  zero_totals();
   int cur = -1;
   auto fold = [&]() {
 #pragma unroll
     for (int e = 0; e < SP_E; ++e)
 #pragma unroll
       for (int k = 0; k <= M; ++k) {
-        kadd(sr[e][k], cr[e][k], pr[e][k]);
-        kadd(si[e][k], ci[e][k], pi[e][k]);
+        if constexpr (F32) {
+          float s0 = tref(e, k, 0), s1 = tref(e, k, 1), c0 = tref(e, k, 2), c1 = tref(e, k, 3);
+          kadd(s0, c0, (float)pr[e][k]);
+          kadd(s1, c1, (float)pi[e][k]);
+          tref(e, k, 0) = s0;
+          tref(e, k, 1) = s1;
+          tref(e, k, 2) = c0;
+          tref(e, k, 3) = c1;
+        } else {
+          sr[e][k] += pr[e][k];
+          si[e][k] += pi[e][k];
+        }
         pr[e][k] = pi[e][k] = 0;
       }
   };
@@ -227,17 +259,20 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
 #pragma unroll
       for (int e = 0; e < SP_E; ++e) {
         if (ga[e] < 0) continue;
-        const int idx = blockIdx.y * SP_TILE + e * SP_THREADS + tid;
+        const int idx = blockIdx.y * SP_TILE + e * NT + tid;
 #pragma unroll
-        for (int k = 0; k <= M; ++k)
-          Mom[((size_t)cur * (M + 1) + k) * ngg + idx] =
-              make_double2((double)sr[e][k] - (double)cr[e][k], (double)si[e][k] - (double)ci[e][k]);
+        for (int k = 0; k <= M; ++k) {
+          double2 v;
+          if constexpr (F32)
+            v = make_double2((double)tref(e, k, 0) - (double)tref(e, k, 2),
+                             (double)tref(e, k, 1) - (double)tref(e, k, 3));
+          else
+            v = make_double2((double)sr[e][k], (double)si[e][k]);
+          Mom[((size_t)cur * (M + 1) + k) * ngg + idx] = v;
+        }
       }
     }
-#pragma unroll
-    for (int e = 0; e < SP_E; ++e)
-#pragma unroll
-      for (int k = 0; k <= M; ++k) sr[e][k] = si[e][k] = cr[e][k] = ci[e][k] = 0;
+    zero_totals();
   };
   const int nchunk = (rg.y - rg.x + CH - 1) / CH;
   auto issue = [&](int ck) {
@@ -246,7 +281,7 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
     const uint32_t rdst = smem_u32(bufp);
     const uint32_t cdst = rdst + (uint32_t)(CH * nG * sizeof(T2));
     const uint32_t bdst = cdst + (uint32_t)(CH * (M + 1) * sizeof(T));
-    for (int e = tid; e < nG * CH; e += SP_THREADS) {
+    for (int e = tid; e < nG * CH; e += NT) {
       const int i = e / nG, G = e % nG;
       const bool ok = i < n;
       const void* src = rho_v;   // (a valid address for the zero-filling copies)
@@ -262,7 +297,7 @@ __global__ void __launch_bounds__(SP_THREADS) sp_moments(
       else
         cp_async8(rdst + (uint32_t)e * 8u, src, ok ? 8u : 0u);
     }
-    for (int e = tid; e < CH * (M + 1); e += SP_THREADS) {
+    for (int e = tid; e < CH * (M + 1); e += NT) {
       const bool ok = e < n * (M + 1);
       const void* src = ok ? (const void*)(coef + (size_t)i0 * (M + 1) + e) : (const void*)coef;
       if constexpr (sizeof(T) == 8)
@@ -541,14 +576,25 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
   // pass 3: moments per bin (bins without pairs stay zero)
   LRT_CUDA(cudaMemsetAsync(Mom, 0, (size_t)nbins * (M + 1) * ngg * sizeof(double2), s));
   if (npos > 0) {
-    constexpr int CH = SpChunk<T>::value;
-    const size_t smem = 2 * ((size_t)nG * CH * sizeof(typename V2<T>::type) + CH * (M + 1) * sizeof(T) +
-                             CH * sizeof(int));
-    auto kern = sp_moments<T, M>;
+    // the largest chunk (32, 16 or 8 sorted pairs) whose two buffers fit next to the totals
+    constexpr int NT = SpCfg<T>::threads, E = SpCfg<T>::E;
+    auto smem_of = [&](int ch) {
+      return 2 * ((size_t)nG * ch * sizeof(typename V2<T>::type) + ch * (M + 1) * sizeof(T) +
+                  ch * sizeof(int)) +
+             (sizeof(T) == 4 ? (size_t)E * (M + 1) * 4 * NT * sizeof(float) : 0);
+    };
+    const size_t limit = 227 * 1024;
+    const int ch = smem_of(32) <= limit ? 32 : (smem_of(16) <= limit ? 16 : 8);
+    const size_t smem = smem_of(ch);
+    if (smem > limit) {
+      set_error("spectral engine: too many G vectors for the moments kernel's shared memory");
+      return LRT_EUNSUPPORTED;
+    }
+    auto kern = ch == 32 ? sp_moments<T, M, 32> : (ch == 16 ? sp_moments<T, M, 16> : sp_moments<T, M, 8>);
     LRT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 g((unsigned)ranges.size(), (unsigned)((ngg + SP_TILE - 1) / SP_TILE));
+    dim3 g((unsigned)ranges.size(), (unsigned)((ngg + NT * E - 1) / (NT * E)));
     TimedLaunch tl(c, &c->ev_chi0, s);
-    kern<<<g, SP_THREADS, smem, s>>>(rho, c->rho_ld, c->rho_gpad, nG, ngg, perm, sbin, coef,
+    kern<<<g, NT, smem, s>>>(rho, c->rho_ld, c->rho_gpad, nG, ngg, perm, sbin, coef,
                                      S->ranges, Mom);
     count_launch(c);
     LRT_CUDA(cudaGetLastError());

@@ -19,19 +19,23 @@ using namespace tcx;
 // every G staged once per 32-pair chunk; ZN etas per pass.  8 FP32 FMAs per (entry, pair)
 // and eta: the work is that of the one frequency, so nothing is reused across columns.
 constexpr int ZE = 2;    // etas per pass of an eta list
-constexpr int ZL_THREADS = 256;
+constexpr int ZL_THREADS = 1024;
 struct ZEtas {
   float v[64];
 };
+// Shared memory: two 32-pair chunks of the pair densities of every G, [32 pairs][nG] (pair-major,
+// so the lanes of a warp, which hold consecutive G', read without bank conflicts), their
+// weights [2][ZN][32], and the FP64 sums [E ZN 4][ZL_THREADS] (in shared memory rather than
+// registers, so that 32 warps fit on an SM to hide the shared-memory and FMA latencies).
 template <int ZN, int E>   // etas per pass (1, or ZE for an eta list); G <= G' pairs per thread
 __global__ void __launch_bounds__(ZL_THREADS, 1) chi0_zero_split_kernel(
     const float2* __restrict__ rho, int gpad, const float4* __restrict__ pw, long long np,
     long long per, int nG, int ngg, int neta, int e0, double scale, double2* __restrict__ chi0,
     long long mat_stride, ZEtas etas) {
   extern __shared__ __align__(16) float2 zs[];
-  float2* rs = zs;                        // [2][32 pairs][nG]: pair-major, so the lanes of a warp
-  float2* ws = zs + (size_t)64 * nG;      // (consecutive G') read without bank conflicts;
-                                          // [2][ZN][32] weights
+  float2* rs = zs;
+  float2* ws = zs + (size_t)64 * nG;
+  double* sums = reinterpret_cast<double*>(ws + 2 * ZN * 32);
   const int tid = threadIdx.x;
   int ga[E], gb[E];
 #pragma unroll
@@ -51,13 +55,26 @@ __global__ void __launch_bounds__(ZL_THREADS, 1) chi0_zero_split_kernel(
   }
   const int ne = min(ZN, neta - e0);
   float acc[E][ZN][4];
-  double sum[E][ZN][4];
 #pragma unroll
   for (int k = 0; k < E; ++k)
 #pragma unroll
     for (int e = 0; e < ZN; ++e)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[k][e][c] = 0.f, sum[k][e][c] = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        acc[k][e][c] = 0.f;
+        sums[((k * ZN + e) * 4 + c) * ZL_THREADS + tid] = 0.0;
+      }
+  auto flush = [&]() {   // FP32 partial sums into the FP64 sums
+#pragma unroll
+    for (int k = 0; k < E; ++k)
+#pragma unroll
+      for (int e = 0; e < ZN; ++e)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          sums[((k * ZN + e) * 4 + c) * ZL_THREADS + tid] += (double)acc[k][e][c];
+          acc[k][e][c] = 0.f;
+        }
+  };
   const long long pb = (long long)blockIdx.x * per, pe = min(np, pb + per);
   // double-buffered chunks: the pair densities of chunk c + 1 arrive by asynchronous copies
   // while chunk c is summed
@@ -121,21 +138,17 @@ __global__ void __launch_bounds__(ZL_THREADS, 1) chi0_zero_split_kernel(
     }
     if (++nch == 32) {   // FP32 partial sums over 1024 pairs, then into FP64
       nch = 0;
-#pragma unroll
-      for (int k = 0; k < E; ++k)
-#pragma unroll
-        for (int e = 0; e < ZN; ++e)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) sum[k][e][c] += (double)acc[k][e][c], acc[k][e][c] = 0.f;
+      flush();
     }
   }
+  flush();
 #pragma unroll
   for (int k = 0; k < E; ++k) {
     if (ga[k] < 0) continue;
     const int G = ga[k], Gp = gb[k];
     for (int e = 0; e < ne; ++e) {
-      const double RR = sum[k][e][0] + acc[k][e][0], RI = sum[k][e][1] + acc[k][e][1];
-      const double IR = sum[k][e][2] + acc[k][e][2], II = sum[k][e][3] + acc[k][e][3];
+      const double* sm = sums + (size_t)((k * ZN + e) * 4) * ZL_THREADS + tid;
+      const double RR = sm[0], RI = sm[ZL_THREADS], IR = sm[2 * ZL_THREADS], II = sm[3 * ZL_THREADS];
       double2* m = chi0 + (size_t)(e0 + e) * mat_stride;
       atomicAdd(&m[(size_t)G * nG + Gp].x, scale * (RR - II));
       atomicAdd(&m[(size_t)G * nG + Gp].y, scale * (RI + IR));
@@ -161,9 +174,11 @@ lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho, float 
   LRT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int ngg = nG * (nG + 1) / 2;
   const bool list = c->neta > 1;
-  const int per_block = ZL_THREADS * (list ? 4 : 7);
+  constexpr int NE = 2;   // entries per thread (both pass widths)
+  const int per_block = ZL_THREADS * NE;
   const int ntile = (ngg + per_block - 1) / per_block;
-  // about four blocks per SM in all, each over one range of pairs (a multiple of 32)
+  // about four blocks per SM in all (two resident at a time), each over one range of pairs
+  // (a multiple of 32)
   long long nsplit = std::max<long long>(1, (4LL * nsm + ntile - 1) / ntile);
   long long per = (c->np + nsplit - 1) / nsplit;
   per = (per + 31) / 32 * 32;
@@ -172,9 +187,11 @@ lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho, float 
   const double scale = 2.0 / (c->nk * c->volume) / (rs * rs * (double)sB);
   ZEtas E{};   // the etas travel as a kernel argument (at most 64)
   for (int j = 0; j < c->neta; ++j) E.v[j] = (float)c->etas[j];
-  const size_t smem = ((size_t)64 * nG + (size_t)(list ? ZE : 1) * 64) * sizeof(float2);
-  auto k1 = chi0_zero_split_kernel<1, 7>;
-  auto k2 = chi0_zero_split_kernel<ZE, 4>;
+  const int zn = list ? ZE : 1;
+  const size_t smem = ((size_t)64 * nG + (size_t)zn * 64) * sizeof(float2) +
+                      (size_t)NE * zn * 4 * ZL_THREADS * sizeof(double);
+  auto k1 = chi0_zero_split_kernel<1, NE>;
+  auto k2 = chi0_zero_split_kernel<ZE, NE>;
   LRT_CUDA(cudaFuncSetAttribute(list ? k2 : k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int e0 = 0; e0 < c->neta; e0 += ZE) {
     (list ? k2 : k1)<<<dim3((unsigned)nsplit, (unsigned)ntile), ZL_THREADS, smem, s>>>(
