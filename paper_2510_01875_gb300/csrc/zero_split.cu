@@ -54,26 +54,28 @@ __global__ void __launch_bounds__(ZL_THREADS, 1) chi0_zero_split_kernel(
     }
   }
   const int ne = min(ZN, neta - e0);
-  float acc[E][ZN][4];
+  // FP32 partial sums as packed pairs: rr_ri = (RR, RI), ir_ii = (IR, II)
+  float2 rr_ri[E][ZN], ir_ii[E][ZN];
 #pragma unroll
   for (int k = 0; k < E; ++k)
 #pragma unroll
-    for (int e = 0; e < ZN; ++e)
+    for (int e = 0; e < ZN; ++e) {
+      rr_ri[k][e] = ir_ii[k][e] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        acc[k][e][c] = 0.f;
-        sums[((k * ZN + e) * 4 + c) * ZL_THREADS + tid] = 0.0;
-      }
+      for (int c = 0; c < 4; ++c) sums[((k * ZN + e) * 4 + c) * ZL_THREADS + tid] = 0.0;
+    }
   auto flush = [&]() {   // FP32 partial sums into the FP64 sums
 #pragma unroll
     for (int k = 0; k < E; ++k)
 #pragma unroll
-      for (int e = 0; e < ZN; ++e)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          sums[((k * ZN + e) * 4 + c) * ZL_THREADS + tid] += (double)acc[k][e][c];
-          acc[k][e][c] = 0.f;
-        }
+      for (int e = 0; e < ZN; ++e) {
+        double* sm = sums + (size_t)((k * ZN + e) * 4) * ZL_THREADS + tid;
+        sm[0] += (double)rr_ri[k][e].x;
+        sm[ZL_THREADS] += (double)rr_ri[k][e].y;
+        sm[2 * ZL_THREADS] += (double)ir_ii[k][e].x;
+        sm[3 * ZL_THREADS] += (double)ir_ii[k][e].y;
+        rr_ri[k][e] = ir_ii[k][e] = make_float2(0.f, 0.f);
+      }
   };
   const long long pb = (long long)blockIdx.x * per, pe = min(np, pb + per);
   // double-buffered chunks: the pair densities of chunk c + 1 arrive by asynchronous copies
@@ -126,13 +128,13 @@ __global__ void __launch_bounds__(ZL_THREADS, 1) chi0_zero_split_kernel(
       for (int k = 0; k < E; ++k) {
         if (ga[k] < 0) continue;
         const float2 a = rb[i * nG + ga[k]], b = rb[i * nG + gb[k]];
-        const float pr = a.x * b.x + a.y * b.y, pi = a.y * b.x - a.x * b.y;   // a conj(b)
+        // a conj(b) = b.x (a.x, a.y) + b.y (a.y, -a.x), in packed FP32x2
+        const float2 P = __ffma2_rn(make_float2(b.x, b.x), a,
+                                    __fmul2_rn(make_float2(b.y, b.y), make_float2(a.y, -a.x)));
 #pragma unroll
         for (int e = 0; e < ZN; ++e) {
-          acc[k][e][0] = fmaf(pr, w[e].x, acc[k][e][0]);
-          acc[k][e][1] = fmaf(pr, w[e].y, acc[k][e][1]);
-          acc[k][e][2] = fmaf(pi, w[e].x, acc[k][e][2]);
-          acc[k][e][3] = fmaf(pi, w[e].y, acc[k][e][3]);
+          rr_ri[k][e] = __ffma2_rn(make_float2(P.x, P.x), w[e], rr_ri[k][e]);
+          ir_ii[k][e] = __ffma2_rn(make_float2(P.y, P.y), w[e], ir_ii[k][e]);
         }
       }
     }
