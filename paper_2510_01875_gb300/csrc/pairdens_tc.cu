@@ -251,42 +251,27 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
       const int part = T.part;
       const int32_t* tab = P.gather + ((size_t)T.k * P.nG + T.G) * P.npw;
       const uint4* Bk = P.B + ((size_t)T.k * P.nbt + T.tm) * (P.npw + 1) * (NPB * PROW / 8);
-      // gather-table entry of this thread's row for a stage (the zero row for padding K)
-      auto row_of = [&](int s) {
-        const int K = s * PK + kk;
-        const int g = K >= P.npwp ? K - P.npwp : K;
-        const int j = g < P.npw ? tab[g] : -1;
-        return j < 0 ? P.npw : j;
-      };
-      // the 4 chunks x NPB parts of this thread's row of a stage (Re tile: Re c' in the first K
-      // half, Im c' in the second; Im tile: Im c', then -Re c')
-      auto load_row = [&](int s, int j, uint4 (&v)[NPB][4]) {
-        const bool im = s * PK + kk >= P.npwp;
-        const int off = (part ^ (im ? 1 : 0)) ? PN / 8 : 0;
-        const uint4* row = Bk + (size_t)j * (NPB * PROW / 8);
-#pragma unroll
-        for (int p = 0; p < NPB; ++p)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) v[p][i] = row[p * (PROW / 8) + off + c0 + i];
-      };
-      // this group's stages are s0, s0 + 2, ...: the rows of a stage are loaded one of the
-      // group's stages ahead and the gather-table entry two ahead, so a stage waits on no
-      // dependent load of its own
-      const int s0 = ((int)(it & 1) == grp) ? 0 : 1;
-      uint4 v[NPB][4], vn[NPB][4];
-      int jn = P.npw;
-      if (s0 < nst) load_row(s0, row_of(s0), v);
-      if (s0 + 2 < nst) jn = row_of(s0 + 2);
       for (int s = 0; s < nst; ++s, ++it) {
         if ((int)(it & 1) != grp) continue;
         const int slot = it % PNS;
-        if (s + 2 < nst) load_row(s + 2, jn, vn);
-        if (s + 4 < nst) jn = row_of(s + 4);
         if (!__all_sync(0xffffffffu, mbar_wait(&empty[slot], ((it / PNS) & 1) ^ 1, &abort_s, P.status))) {
           ok = false;
           break;
         }
-        const bool neg = part && (s * PK + kk >= P.npwp);
+        const int K = s * PK + kk;
+        const bool im = K >= P.npwp;
+        const int g = im ? K - P.npwp : K;
+        int j = g < P.npw ? tab[g] : -1;
+        if (j < 0) j = P.npw;                    // the zero row
+        const uint4* row = Bk + (size_t)j * (NPB * PROW / 8);
+        // Re tile: Re c' (first K half), Im c' (second); Im tile: Im c', then -Re c'
+        const int off = (part ^ (im ? 1 : 0)) ? PN / 8 : 0;
+        const bool neg = part && im;
+        uint4 v[NPB][4];
+#pragma unroll
+        for (int p = 0; p < NPB; ++p)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[p][i] = row[p * (PROW / 8) + off + c0 + i];
         const uint32_t bt = base + slot * PSTAGE + NPA * PA_BYTES;
 #pragma unroll
         for (int p = 0; p < NPB; ++p)
@@ -296,10 +281,6 @@ __global__ void __launch_bounds__(PTHREADS, 1) pair_density_tc_kernel(PParams P)
         fence_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[slot]);
-#pragma unroll
-        for (int p = 0; p < NPB; ++p)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) v[p][i] = vn[p][i];
       }
     }
   } else if (warp == PW_MMA) {

@@ -5,7 +5,8 @@ form (oracle/spectral.py, pinned to the direct sum) and against the direct engin
    within 1e-10 of the oracle's spectral chi0 (orders 1 and 3), and S(q, w) (with its exact
    w -> 0 limit) within 1e-10 of the oracle's S built from that chi0;
  - an eta list: every eta's chi0 from the one spectral function, against the oracle per eta;
- - split context: FP32 pair sums with compensated accumulation, within 1e-5 of the oracle;
+ - split context: FP32 pair sums with compensated accumulation, within 1e-5 of the oracle,
+   also at N_G = 200 (a smaller staged chunk);
  - against the direct engine at h = eta/16, order 3: within the interpolation bound;
  - the adjoint and graph capture are refused, and bad arguments are rejected.
 """
@@ -94,6 +95,19 @@ def test_split_spectral_against_oracle(prec):
         ref, _, _ = spectral.chi0_spectral(rho, delta, df, freqs, wl.eta, wl.nk, om, h, 3)
         got = c.get_chi0(iq)
         assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), iq
+    c.close()
+
+
+def test_split_spectral_large_g_set():
+    """N_G = 200: the moments kernel stages 16 sorted pairs per chunk instead of 32 (two chunks
+    of 200 pair densities next to the FP32 bin totals fill the shared memory)."""
+    wl = W.tiny(seed=73, nq=1, nw=24, kmesh=(2, 2, 2), nbands=8, nG=200)
+    h = wl.eta / 8
+    c = _ctx(wl, "fp16x3", h, 3)
+    _, rho, delta, df, freqs, _, om = _oracle_parts(wl, 0)
+    ref, _, _ = spectral.chi0_spectral(rho, delta, df, freqs, wl.eta, wl.nk, om, h, 3)
+    got = c.get_chi0(0)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
     c.close()
 
 
