@@ -124,10 +124,10 @@ __global__ void sp_bins(const double* __restrict__ x, const double* __restrict__
 }
 
 // pairs in bin order: perm[pos] = p, and per sorted position the moment coefficients
-// df f^k (k = 0..m) and the bin; bin[p] becomes the sorted position of p
+// df f^k (k = 0..m) and the bin
 template <typename T, int M>
 __global__ void sp_scatter(const double* __restrict__ x, const double* __restrict__ df,
-                           int* __restrict__ bin, long long np, double x0, double h,
+                           const int* __restrict__ bin, long long np, double x0, double h,
                            int* __restrict__ cursor, int* __restrict__ perm, int* __restrict__ sbin,
                            T* __restrict__ coef) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
@@ -137,7 +137,6 @@ __global__ void sp_scatter(const double* __restrict__ x, const double* __restric
     const int pos = atomicAdd(&cursor[j], 1);
     perm[pos] = (int)p;
     sbin[pos] = j;
-    bin[p] = pos;   // from here on the sorted position of p (the inverse permutation)
     const double f = (x[p] - x0) / h - (double)j;
     double fk = df[p];
 #pragma unroll
@@ -172,35 +171,15 @@ __device__ __forceinline__ void kadd(T& s, T& c, T v) {
   }
 }
 
-// The pair densities in bin order, pair-major: out[pos][G] = rho_p(G) with pos the sorted
-// position of p (pos[p] < 0: not sorted, df = 0).  A warp takes 32 consecutive pairs, so the
-// reads of the pair-density layout are coalesced; each thread writes its own row.
-template <typename T>
-__global__ void sp_permute(const void* __restrict__ rho_v, long long ld, int gpad, int nG, long long np,
-                           const int* __restrict__ pos, typename V2<T>::type* __restrict__ out) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int q = pos[p];
-    if (q < 0) continue;
-    typename V2<T>::type* o = out + (size_t)q * nG;
-    for (int G = 0; G < nG; ++G) {
-      if constexpr (sizeof(T) == 8)
-        o[G] = reinterpret_cast<const double2*>(rho_v)[(size_t)G * ld + p];
-      else
-        o[G] = reinterpret_cast<const float2*>(rho_v)[((size_t)(p >> 5) * gpad + G) * 32 + (p & 31)];
-    }
-  }
-}
-
 // Moments of whole bins: block b takes the sorted positions [range[b].x, range[b].y) (whole
-// bins) and threads x E of the G <= G' pairs (blockIdx.y).  rs_sorted: the pair densities in
-// bin order, [pos][nG] (FP64, or the split form's FP32 scaled by a power of two that the
-// caller removes).  Mom [nbins][M + 1][ngg] complex FP64.
+// bins) and threads x E of the G <= G' pairs (blockIdx.y).  rho: FP64 [G][ld] (T = double) or the
+// split form's blocked FP32 [p/32][gpad][32] (T = float, values scaled by a power of two that
+// the caller removes).  Mom [nbins][M + 1][ngg] complex FP64.
 template <typename T, int M, int CH>   // CH: sorted pairs per staged chunk
 __global__ void __launch_bounds__(SpCfg<T>::threads, 1) sp_moments(
-    const typename V2<T>::type* __restrict__ rsorted, int nG, int ngg,
-    const int* __restrict__ sbin, const T* __restrict__ coef, const int2* __restrict__ range,
-    double2* __restrict__ Mom) {
+    const void* __restrict__ rho_v, long long ld, int gpad, int nG, int ngg,
+    const int* __restrict__ perm, const int* __restrict__ sbin, const T* __restrict__ coef,
+    const int2* __restrict__ range, double2* __restrict__ Mom) {
   using T2 = typename V2<T>::type;
   constexpr int NT = SpCfg<T>::threads, SP_E = SpCfg<T>::E, SP_TILE = NT * SP_E;
   constexpr bool F32 = sizeof(T) == 4;
@@ -302,11 +281,17 @@ __global__ void __launch_bounds__(SpCfg<T>::threads, 1) sp_moments(
     const uint32_t rdst = smem_u32(bufp);
     const uint32_t cdst = rdst + (uint32_t)(CH * nG * sizeof(T2));
     const uint32_t bdst = cdst + (uint32_t)(CH * (M + 1) * sizeof(T));
-    // the chunk's rows are contiguous in the sorted copy
-    const T2* src0 = rsorted + (size_t)i0 * nG;
     for (int e = tid; e < nG * CH; e += NT) {
-      const bool ok = e < n * nG;
-      const void* src = ok ? (const void*)(src0 + e) : (const void*)rsorted;
+      const int i = e / nG, G = e % nG;
+      const bool ok = i < n;
+      const void* src = rho_v;   // (a valid address for the zero-filling copies)
+      if (ok) {
+        const long long p = perm[i0 + i];
+        if constexpr (sizeof(T) == 8)
+          src = reinterpret_cast<const double2*>(rho_v) + (size_t)G * ld + p;
+        else
+          src = reinterpret_cast<const float2*>(rho_v) + ((size_t)(p >> 5) * gpad + G) * 32 + (p & 31);
+      }
       if constexpr (sizeof(T) == 8)
         cp_async16(rdst + (uint32_t)e * 16u, src, ok ? 16u : 0u);
       else
@@ -463,8 +448,6 @@ struct SpState {
   std::vector<int> start_h;
   double* freqs_etas = nullptr;   // [nwi + neta]
   size_t fe_n = 0;
-  void* sorted = nullptr;         // the pair densities in bin order
-  size_t sorted_bytes = 0;
 };
 
 SpState* sp_of(lrt_ctx* c) {
@@ -598,20 +581,6 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
   sp_scatter<T, M><<<grid, 256, 0, s>>>(x, df, bin, np, x0, h, cursor, perm, sbin, coef);
   count_launch(c);
   LRT_CUDA(cudaGetLastError());
-  // the pair densities in bin order (one pass: coalesced reads, each pair's row written once)
-  using T2 = typename V2<T>::type;
-  const size_t sorted_bytes = std::max<size_t>(1, (size_t)npos) * nG * sizeof(T2);
-  if (S->sorted_bytes < sorted_bytes) {
-    cudaFree(S->sorted);
-    S->sorted = nullptr;
-    S->sorted_bytes = 0;
-    LRT_CUDA(cudaMalloc(&S->sorted, sorted_bytes));
-    S->sorted_bytes = sorted_bytes;
-  }
-  T2* rsorted = static_cast<T2*>(S->sorted);
-  sp_permute<T><<<grid, 256, 0, s>>>(rho, c->rho_ld, c->rho_gpad, nG, np, bin, rsorted);
-  count_launch(c);
-  LRT_CUDA(cudaGetLastError());
   // pass 3: moments per bin (bins without pairs stay zero)
   LRT_CUDA(cudaMemsetAsync(Mom, 0, (size_t)nbins * (M + 1) * ngg * sizeof(double2), s));
   if (npos > 0) {
@@ -633,7 +602,8 @@ lrt_status run_spectral(lrt_ctx* c, QData& q, const void* rho, double rho_scale,
     LRT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 g((unsigned)ranges.size(), (unsigned)((ngg + NT * E - 1) / (NT * E)));
     TimedLaunch tl(c, &c->ev_chi0, s);
-    kern<<<g, NT, smem, s>>>(rsorted, nG, ngg, sbin, coef, S->ranges, Mom);
+    kern<<<g, NT, smem, s>>>(rho, c->rho_ld, c->rho_gpad, nG, ngg, perm, sbin, coef,
+                                     S->ranges, Mom);
     count_launch(c);
     LRT_CUDA(cudaGetLastError());
   }
@@ -712,7 +682,6 @@ void free_spectral_state(lrt_ctx* c) {
   cudaFree(S->buf2);
   cudaFree(S->ranges);
   cudaFree(S->freqs_etas);
-  cudaFree(S->sorted);
   delete S;
   c->sp = nullptr;
 }
