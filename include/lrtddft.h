@@ -188,11 +188,16 @@ lrt_status lrtddft_itcf_laplace_device(lrt_ctx* ctx, int ntau, const double* tau
  *          LRT_TUNE_FINE_ACCUM flush the FP32 tensor-core accumulators into the FP64 sums every
  *                             32 stages (1024 pairs) instead of 64: the FP32 accumulation
  *                             error, which grows with the period, halves;
- *          LRT_TUNE_HALF_TILES every row unit a half (256 rows; more, smaller units).
+ *          LRT_TUNE_HALF_TILES every row unit a half (256 rows; more, smaller units);
+ *          LRT_TUNE_ZERO_SIMT  the split forms' w = 0 column (when 0 is not on the grid) on
+ *                             the CUDA cores instead of the tensor cores (the tensor-core
+ *                             kernel takes 64 x 64 G tiles, at least one SM each: with more
+ *                             tiles than SMs, N_G > 768 on 152 SMs, the CUDA-core kernel runs
+ *                             in any case).
  *   variant: -1 (tuned or default 0), 0 or 1;  unit_stages: 0 (tuned or default 4096) or a
  *   positive multiple of 64.  LRT_EINVAL otherwise.  Invalidates a captured graph. */
 enum { LRT_TUNE_AUTO = 1, LRT_TUNE_SINGLE_Q = 2, LRT_TUNE_PAIR_SIMT = 4, LRT_TUNE_FINE_ACCUM = 8,
-       LRT_TUNE_HALF_TILES = 16 };
+       LRT_TUNE_HALF_TILES = 16, LRT_TUNE_ZERO_SIMT = 32 };
 lrt_status lrtddft_set_tuning(lrt_ctx* ctx, int flags, int variant, int unit_stages);
 /* The variant and unit size used by the last tensor-core launch (-1 and 0 before any). */
 lrt_status lrtddft_get_tuning(lrt_ctx* ctx, int* variant, int* unit_stages);
@@ -445,6 +450,15 @@ lrt_status lrtddft_get_pair_densities(lrt_ctx* ctx, int iq, double* rho);
 lrt_status lrtddft_get_chi_col0(const lrt_ctx* ctx, int iq, double* chi);
 /* Internal frequencies [nw_int] and the index of the w = 0 column. */
 lrt_status lrtddft_get_frequencies(const lrt_ctx* ctx, double* freqs, int* hcol);
+/* The row plan of the split-precision contraction for nG response G vectors (1..4096; host
+ * only, no device work).  The Hermitian-split rows (Re and Im of rho(G) rho*(G') for G <= G')
+ * are cut into sub-blocks of 16 row pairs, 8 per 256-row super-tile: a 4 x 4 block of G quads,
+ * or a list of 16 pairs where a quad block would hold padding.  n_st: super-tiles (the least
+ * any covering has, ceil(nG (nG + 1) / 256)); n_list: list sub-blocks; max_blocks: the most
+ * 8-G blocks of pair densities one super-tile reads (at most 6); rp [nG][nG] (int32, or NULL):
+ * the row pair (rows 2 rp, 2 rp + 1) of (min(G, G'), max(G, G')).  LRT_EINVAL on a NULL
+ * output or nG out of range. */
+lrt_status lrtddft_row_plan(int nG, int* n_st, int* n_list, int* max_blocks, int32_t* rp);
 
 #ifdef __cplusplus
 }

@@ -117,6 +117,7 @@ SIGNATURES = {
     "lrtddft_eta_scan": (C.c_int, [_P, C.c_int, _D, C.c_double, _D, _D, C.POINTER(C.c_int)]),
     "lrtddft_dielectric": (C.c_int, [_P, _D, _D]),
     "lrtddft_measure_fp64": (C.c_int, [C.c_int, _D]),
+    "lrtddft_row_plan": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _I32]),
     "lrtddft_kubo_greenwood": (C.c_int, [_P, C.c_int, _D, C.c_int, _D, C.c_double, _D, _D, _D, _D,
                                          C.POINTER(C.c_int)]),
     "lrtddft_kubo_greenwood_attenuate": (C.c_int, [_P, C.POINTER(lrt_atten_params), _D,
@@ -158,6 +159,17 @@ def measure_fp64(device: int = 0) -> float:
     v = C.c_double()
     _check("lrtddft_measure_fp64", lib.lrtddft_measure_fp64(device, C.byref(v)))
     return v.value
+
+
+def row_plan(nG: int):
+    """Row plan of the split contraction for nG G vectors (host only):
+    (super-tiles, list sub-blocks, most G blocks per super-tile, row pair of (G, G') [nG, nG])."""
+    lib = load()
+    n_st, n_list, mb = C.c_int(), C.c_int(), C.c_int()
+    rp = np.zeros((nG, nG), dtype=np.int32)
+    _check("lrtddft_row_plan", lib.lrtddft_row_plan(nG, C.byref(n_st), C.byref(n_list), C.byref(mb),
+                                                    rp.ctypes.data_as(_I32)))
+    return n_st.value, n_list.value, mb.value, rp
 
 
 def atten_params(**kw) -> lrt_atten_params:
@@ -253,15 +265,17 @@ class Context:
             self.h, ntau, _P(tau_ptr), ITCF[mode], _P(F_ptr), _P(metrics_ptr), _P(stream)))
 
     def set_tuning(self, auto: bool = False, single_q: bool = False, variant: int = -1, unit_stages: int = 0,
-                   pair_simt: bool = False, fine_accum: bool = False, half_tiles: bool = False):
+                   pair_simt: bool = False, fine_accum: bool = False, half_tiles: bool = False,
+                   zero_simt: bool = False):
         """lrtddft_set_tuning: auto times the contraction's row-unit shapes, variants and unit
         sizes on the first launch of each shape; single_q launches the contraction once per q;
         pair_simt computes the split path's pair densities on the FP32 SIMT kernel instead of
         the tensor cores; fine_accum halves the FP32 accumulation period (32 stages);
-        half_tiles makes every row unit 256 rows; variant (-1, 0, 1) and unit_stages (0 or a
+        half_tiles makes every row unit 256 rows; zero_simt computes the w = 0 column on the
+        CUDA cores instead of the tensor cores; variant (-1, 0, 1) and unit_stages (0 or a
         multiple of 64) force a choice."""
         flags = ((1 if auto else 0) | (2 if single_q else 0) | (4 if pair_simt else 0)
-                 | (8 if fine_accum else 0) | (16 if half_tiles else 0))
+                 | (8 if fine_accum else 0) | (16 if half_tiles else 0) | (32 if zero_simt else 0))
         _check("lrtddft_set_tuning", self.lib.lrtddft_set_tuning(self.h, flags, variant, unit_stages))
 
     def get_tuning(self):

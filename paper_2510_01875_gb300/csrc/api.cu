@@ -76,6 +76,7 @@ void free_ctx(lrt_ctx* c) {
   cudaFree(c->dw.status);
   cudaFree(c->dw.scratch);
   cudaFree(c->dw.pd_work);
+  cudaFree(c->dw.zt_part);
   cudaFree(c->dw.dyson_ws);
   cudaFree(c->dw.s0);
   cudaFree(c->dw.zf);
@@ -945,7 +946,7 @@ extern "C" lrt_status lrtddft_dsf_vjp(lrt_ctx* c, const double* dL_dS, double gr
 extern "C" lrt_status lrtddft_set_tuning(lrt_ctx* c, int flags, int variant, int unit_stages) {
   if (!c) return bad("NULL context");
   if (flags & ~(LRT_TUNE_AUTO | LRT_TUNE_SINGLE_Q | LRT_TUNE_PAIR_SIMT | LRT_TUNE_FINE_ACCUM |
-                LRT_TUNE_HALF_TILES))
+                LRT_TUNE_HALF_TILES | LRT_TUNE_ZERO_SIMT))
     return bad("unknown tuning flags");
   if (variant < -1 || variant > 1) return bad("variant must be -1, 0 or 1");
   if (unit_stages != 0 && (unit_stages < 64 || unit_stages % 64 != 0))
@@ -955,6 +956,7 @@ extern "C" lrt_status lrtddft_set_tuning(lrt_ctx* c, int flags, int variant, int
   c->pair_simt = (flags & LRT_TUNE_PAIR_SIMT) != 0;
   c->fine_accum = (flags & LRT_TUNE_FINE_ACCUM) != 0;
   c->half_tiles = (flags & LRT_TUNE_HALF_TILES) != 0;
+  c->zero_simt = (flags & LRT_TUNE_ZERO_SIMT) != 0;
   c->tune_variant = variant;
   c->tune_unit_stages = unit_stages;
   c->graph_valid = false;

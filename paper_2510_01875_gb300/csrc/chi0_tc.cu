@@ -68,7 +68,7 @@ constexpr int B_SBO = (TNH / 64) * 1024;
 constexpr int RBLK_BYTES = GBLK * KS * 8;            // one G block of one stage: 2 KB
 constexpr int PW_OFF = RROWS * KS * 8;               // pair weights after the rows
 constexpr int R_STAGE = PW_OFF + KS * 16;            // rho rows, 32 float4 pair weights
-constexpr int NSUB = NACC * 64 / 16;                 // 4 x 4 (G, G') sub-blocks per super-tile
+constexpr int NSUB = NACC * 64 / 16;                 // sub-blocks of 16 (G, G') pairs per super-tile
 constexpr int kFlushStages = 64;   // FP32 accumulation period: 64 stages = 2048 pairs
 constexpr int NCHUNK = NACC * TN / 16;  // 16-column pieces of the accumulators per lane
 
@@ -76,7 +76,8 @@ constexpr int NCHUNK = NACC * TN / 16;  // 16-column pieces of the accumulators 
 struct QDesc {
   const float2* rho;          // blocked [ld/32][gpad][32]
   const float4* pw;           // [np rounded up to 32] {Delta_hi, Delta_lo, df sB, 0}
-  const int2* rowtab;         // [n_st * NSUB] ring rows of the G quads of each sub-block
+  const int2* rowtab;         // [n_st * NSUB] ring rows of a sub-block's G quads, or (-1, list)
+  const int2* lsttab;         // [n_st * NSUB * 16] ring rows of the (G, G') of list slots
   const int* blk;             // [n_st * MAXBLK] G blocks of the super-tile, -1 padding
   const float4* wtab;         // [n_n * 64] per frequency pair {hi_f, hi_f+1, lo_f, lo_f+1}
                               // (CTA r of a pair builds the columns of pairs 32 r .. 32 r + 31)
@@ -134,6 +135,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
   __shared__ __align__(8) uint64_t rfull[NSR], rempty[NSR];
   __shared__ uint32_t tmem_base_s;
   __shared__ int2 rowtab_s[NSUB];   // byte offsets of the two G quads of each A warp's sub-block
+                                    // (x < 0: the sub-block is a list)
+  __shared__ int4 lst_s[NSUB][8];   // a list's 16 (G, G') byte offsets, two pairs per int4
   __shared__ int blk_s[MAXBLK];
   __shared__ int nblk_s;
   __shared__ float4 wtab_s[TNH / 4];
@@ -196,6 +199,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
       const int2 g = w < NSUB ? D.rowtab[st * NSUB + w] : make_int2(0, 0);
       rowtab_s[threadIdx.x] = make_int2(g.x * KS * 8, g.y * KS * 8);
     }
+    if (threadIdx.x < NSUB * 16) {
+      const int w = sub0 + (int)threadIdx.x / 16;
+      const int2 g = w < NSUB ? D.lsttab[(st * NSUB + w) * 16 + threadIdx.x % 16] : make_int2(0, 0);
+      reinterpret_cast<int2*>(&lst_s[0][0])[threadIdx.x] = make_int2(g.x * KS * 8, g.y * KS * 8);
+    }
     if (threadIdx.x < TNH / 4) wtab_s[threadIdx.x] = D.wtab[U.nt * 64 + rank * (TNH / 4) + threadIdx.x];
     if (ME && threadIdx.x < TNH / 4)
       etab_s[threadIdx.x] = D.etab[U.nt * 64 + rank * (TNH / 4) + threadIdx.x];
@@ -212,8 +220,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
 
     if (warp < NPROD) {
       // ---------------- producers ----------------
-      // Lane = pair.  A warp w (0..7) owns the 4 x 4 sub-block (G quad a, G quad b) of rows
-      // 32 w .. 32 w + 31: chunk i holds the row pairs (4 a + i, 4 b + j), j = 0..3.  B warp w
+      // Lane = pair.  A warp w (0..7) owns the sub-block of rows 32 w .. 32 w + 31: for a quad
+      // block (G quad a, G quad b) chunk i holds the row pairs (4 a + i, 4 b + j), j = 0..3;
+      // for a list chunk i holds its pairs 4 i .. 4 i + 3 (ring rows from lst_s).  B warp w
       // (8..15) owns 8 frequencies (2 chunks of 8 columns) of this CTA's 64.  Padding pairs
       // (beyond the last one) and padding G rows have zero pair densities and weights, so no
       // masking is needed.
@@ -228,6 +237,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
         }
       }
       const int2 ro = rowtab_s[warp & 7];                      // A warps
+      const bool is_list = ro.x < 0;
       const float4* wt = wtab_s + CHUNKS_B * 2 * (warp & 7);   // B warps: 4 frequency pairs
       const float2* et = etab_s + CHUNKS_B * 2 * (warp & 7);
       const float eta2 = P.eta * P.eta;
@@ -240,6 +250,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) chi0_tc_kernel(Params P) {
         const uint32_t sst = base + s * STAGE_BYTES;
         if (warp < 8 && warp >= 4 * nacc) {
           // a half unit: accumulator 1 is not used, its rows are not built
+        } else if (warp < 8 && is_list) {
+          // 16 listed (G, G'): two loads per product, the same x conj(y) arithmetic
+          const uint32_t rl = ring + lane * 8;
+          const int4* lt = lst_s[warp];
+#pragma unroll
+          for (int cc = 0; cc < CHUNKS_A; ++cc) {
+            float v[8];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int4 o = lt[2 * cc + h];
+              const float2 x0 = lds_f2(rl + o.x), y0 = lds_f2(rl + o.y);
+              const float2 x1 = lds_f2(rl + o.z), y1 = lds_f2(rl + o.w);
+              const float2 p0 = __ffma2_rn(make_float2(y0.x, y0.x), x0,
+                                           __fmul2_rn(make_float2(y0.y, y0.y), make_float2(x0.y, -x0.x)));
+              const float2 p1 = __ffma2_rn(make_float2(y1.x, y1.x), x1,
+                                           __fmul2_rn(make_float2(y1.y, y1.y), make_float2(x1.y, -x1.x)));
+              v[4 * h] = p0.x;
+              v[4 * h + 1] = p0.y;
+              v[4 * h + 2] = p1.x;
+              v[4 * h + 3] = p1.y;
+            }
+            uint4 hi, lo;
+            Pack<BF>::split(v, hi, lo);
+            st_shared_v4(sst + sto[cc], hi);
+            st_shared_v4(sst + sto[cc] + A_BYTES, lo);
+          }
         } else if (warp < 8) {
           // rho(4a + i) and rho(4b + j) of this lane's pair; x conj(y) as
           // y.re (x.re, x.im) + y.im (x.im, -x.re) in packed FP32x2
@@ -645,6 +681,7 @@ void free_tc_state(lrt_ctx* c) {
 
 void free_split_plan(SplitPlan& sp) {
   cudaFree(sp.rowtab);
+  cudaFree(sp.lsttab);
   cudaFree(sp.blk);
   cudaFree(sp.rp_of);
   cudaFree(sp.wtab);
@@ -660,7 +697,184 @@ void free_split_plan(SplitPlan& sp) {
 static int nw_tc(const lrt_ctx* c) { return c->hcol == c->nw ? c->nwi - 1 : c->nwi; }
 static int ncol_tc(const lrt_ctx* c) { return c->neta * nw_tc(c); }
 
-// Tables of one q, built once: row super-tiles (4 x 4 sub-blocks of G quads), G blocks,
+// A list costs its A warp about twice a quad block's shared-memory loads and instructions.
+// Inside each super-tile the lists take the A warp positions 2, 7, 3, 6, 1, 5, 0, 4 in that
+// order: warp w runs on SM sub-partition w % 4, and sub-partition 0 also runs the MMA issuer
+// (warp 16), whose issue slots a busy list warp delays; a half unit gives positions 0-3 and
+// 4-7 to different CTAs, so its first two lists go one to each.  (Spreading the lists over
+// more super-tiles measured slower: a row unit pays for its lists about once, however many.)
+// sub is padded to n_st * NSUB entries, (-2, 0) marking a padding slot.
+static void seat_lists(int n_st, std::vector<int2>& sub) {
+  sub.resize((size_t)n_st * NSUB, make_int2(-2, 0));
+  static const int kPos[NSUB] = {2, 7, 3, 6, 1, 5, 0, 4};
+  for (int t = 0; t < n_st; ++t) {
+    int2* e = &sub[(size_t)t * NSUB];
+    std::vector<int2> ls, rest;
+    for (int w = 0; w < NSUB; ++w) (e[w].x == -1 ? ls : rest).push_back(e[w]);
+    std::vector<char> taken(NSUB, 0);
+    for (size_t k = 0; k < ls.size(); ++k) {
+      e[kPos[k]] = ls[k];
+      taken[kPos[k]] = 1;
+    }
+    size_t r = 0;
+    for (int w = 0; w < NSUB; ++w)
+      if (!taken[w]) e[w] = rest[r++];
+  }
+}
+
+// Row pairs of the Hermitian split in sub-blocks of 16 (G <= G') pairs, in super-tile order
+// (NSUB consecutive sub-blocks per super-tile).  A sub-block is either a 4 x 4 block of G
+// quads (qa, qb), its pairs (4 qa + i, 4 qb + j), or a list of 16 arbitrary pairs.  A quad
+// block costs 8 pair-density loads per lane for its 16 products, a list 32, so quads are used
+// wherever they lose nothing: every block of two different full quads is one; the pairs that a
+// quad block would cover with padding (the diagonal blocks, whose i > j slots repeat pairs,
+// and the blocks of the partial last quad) go into lists, except as many of those blocks as
+// fit without raising the super-tile count above ceil(N_G (N_G + 1) / 256), the least any
+// covering has.  Sub-blocks are ordered by 8-G block pairs (lists filled in the same order),
+// so that a super-tile touches at most MAXBLK G blocks (checked by the caller).
+static int plan_subblocks(int nG, std::vector<int2>& sub, std::vector<int2>& lists) {
+  sub.clear();
+  lists.clear();
+  const int nQf = nG / 4, r = nG % 4, nblk = (nG + GBLK - 1) / GBLK;
+  const long long npairs = (long long)nG * (nG + 1) / 2;
+  const int n_st = (int)((npairs + NSUB * 16 - 1) / (NSUB * 16));
+  // quad blocks a list could take instead: diagonal (kind 0), full x partial (1), partial
+  // diagonal (2); kept as quads, largest first, while the sub-block count allows
+  struct Cand {
+    int kind, qa, pairs;
+  };
+  std::vector<Cand> cands;
+  if (r)
+    for (int qa = 0; qa < nQf; ++qa) cands.push_back({1, qa, 4 * r});
+  for (int qa = 0; qa < nQf; ++qa) cands.push_back({0, qa, 10});
+  if (r) cands.push_back({2, nQf, r * (r + 1) / 2});
+  std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.pairs > b.pairs; });
+  const long long nreg = (long long)nQf * (nQf - 1) / 2;
+  long long left = npairs - 16 * nreg, nsub = nreg + (left + 15) / 16;
+  std::vector<char> keep_diag(nQf + 1, 0), keep_part(nQf + 1, 0);
+  for (const Cand& cd : cands) {
+    const long long n2 = nsub + 1 - (left + 15) / 16 + (left - cd.pairs + 15) / 16;
+    if (n2 > (long long)NSUB * n_st) continue;
+    nsub = n2;
+    left -= cd.pairs;
+    (cd.kind == 1 ? keep_part : keep_diag)[cd.qa] = 1;
+  }
+  std::vector<int2> pend;
+  auto emit = [&](bool all) {
+    while (pend.size() >= 16 || (all && !pend.empty())) {
+      const int n = std::min<int>(16, (int)pend.size());
+      sub.push_back(make_int2(-1, (int)(lists.size() / 16)));
+      for (int t = 0; t < 16; ++t) lists.push_back(t < n ? pend[t] : make_int2(-1, -1));
+      pend.erase(pend.begin(), pend.begin() + n);
+    }
+  };
+  for (int I = 0; I < nblk; ++I) {
+    for (int qa = 2 * I; qa < std::min(nQf, 2 * I + 2); ++qa) {
+      if (keep_diag[qa]) {
+        sub.push_back(make_int2(qa, qa));
+      } else {
+        for (int i = 0; i < 4; ++i)
+          for (int j = i; j < 4; ++j) pend.push_back(make_int2(4 * qa + i, 4 * qa + j));
+      }
+    }
+    emit(false);
+    for (int J = I; J < nblk; ++J)
+      for (int qa = 2 * I; qa < 2 * I + 2; ++qa)
+        for (int qb = 2 * J; qb < 2 * J + 2; ++qb)
+          if (qa < qb && qb < nQf) sub.push_back(make_int2(qa, qb));
+    if (r) {
+      for (int qa = 2 * I; qa < std::min(nQf, 2 * I + 2); ++qa) {
+        if (keep_part[qa]) {
+          sub.push_back(make_int2(qa, nQf));
+        } else {
+          for (int i = 0; i < 4; ++i)
+            for (int Gp = 4 * nQf; Gp < nG; ++Gp) pend.push_back(make_int2(4 * qa + i, Gp));
+        }
+      }
+      if (I == (4 * nQf) / GBLK) {
+        if (keep_diag[nQf]) {
+          sub.push_back(make_int2(nQf, nQf));
+        } else {
+          for (int G = 4 * nQf; G < nG; ++G)
+            for (int Gp = G; Gp < nG; ++Gp) pend.push_back(make_int2(G, Gp));
+        }
+      }
+      emit(false);
+    }
+  }
+  emit(true);
+  seat_lists(n_st, sub);
+  return n_st;
+}
+
+// The row tables of N_G response G vectors: super-tiles, per sub-block its quads' ring rows or
+// its list, the list slots' ring rows, the G blocks of each super-tile and the row pair of
+// every (G, G').  Host only.
+static lrt_status row_tables(int nG, int& n_st, int& n_list, std::vector<int2>& rowtab,
+                             std::vector<int2>& lsttab, std::vector<int>& blk, std::vector<int>& rp_of) {
+  // Sub-blocks of 16 row pairs (quad blocks and pair lists); sub-block s, slot t holds row
+  // pair 16 s + t: a quad block's slot 4 i + j is (4 qa + i, 4 qb + j).  In a diagonal quad
+  // block the six slots with i > j repeat pairs held by slots with i < j; like padding G and
+  // the padding slots of the last list, their rows are computed and never read.
+  std::vector<int2> sub, lists;
+  n_st = plan_subblocks(nG, sub, lists);
+  const int nsub = (int)sub.size();
+  // rowtab: a quad block's ring rows of its two quads, or (-1, list) for a list;
+  // lsttab: the ring rows of every list slot's (G, G') (zero for quad blocks)
+  rowtab.assign((size_t)n_st * NSUB, make_int2(0, 0));
+  lsttab.assign((size_t)n_st * NSUB * 16, make_int2(0, 0));
+  blk.assign((size_t)n_st * MAXBLK, -1);
+  rp_of.assign((size_t)nG * nG, 0);
+  n_list = (int)(lists.size() / 16);
+  for (int t = 0; t < n_st; ++t) {
+    int* bl = &blk[(size_t)t * MAXBLK];
+    int n = 0;
+    auto slot = [&](int G) {   // ring row of G (its G block taken into the super-tile)
+      const int b = G / GBLK;
+      for (int i = 0; i < n; ++i)
+        if (bl[i] == b) return i * GBLK + G % GBLK;
+      if (n == MAXBLK) return -1;
+      bl[n] = b;
+      return (n++) * GBLK + G % GBLK;
+    };
+    for (int w = 0; w < NSUB && t * NSUB + w < nsub; ++w) {
+      const int s = t * NSUB + w;
+      const int2 qq = sub[s];
+      if (qq.x == -2) continue;   // padding slot: quad rows (0, 0), computed and never read
+      if (qq.x >= 0) {
+        const int la = slot(4 * qq.x), lb = slot(4 * qq.y);
+        if (la < 0 || lb < 0) {
+          set_error("a row super-tile touches more than 6 G blocks");
+          return LRT_EUNSUPPORTED;
+        }
+        rowtab[s] = make_int2(la, lb);
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) {
+            const int G = 4 * qq.x + i, Gp = 4 * qq.y + j;
+            if (G >= nG || Gp >= nG || G > Gp) continue;
+            rp_of[G * nG + Gp] = rp_of[Gp * nG + G] = s * 16 + 4 * i + j;
+          }
+      } else {
+        rowtab[s] = make_int2(-1, qq.y);
+        for (int k = 0; k < 16; ++k) {
+          const int2 pr = lists[(size_t)qq.y * 16 + k];
+          if (pr.x < 0) continue;   // padding slot: ring row 0 (computed, never read)
+          const int la = slot(pr.x), lb = slot(pr.y);
+          if (la < 0 || lb < 0) {
+            set_error("a row super-tile touches more than 6 G blocks");
+            return LRT_EUNSUPPORTED;
+          }
+          lsttab[(size_t)s * 16 + k] = make_int2(la, lb);
+          rp_of[pr.x * nG + pr.y] = rp_of[pr.y * nG + pr.x] = s * 16 + k;
+        }
+      }
+    }
+    if (n == 0) bl[0] = 0;
+  }
+  return LRT_OK;
+}
+
+// Tables of one q, built once: row super-tiles (sub-blocks of 16 G pairs), G blocks,
 // frequency pairs, the unpack map, and the weight and FP64-sum buffers.
 static lrt_status build_plan(const lrt_ctx* c, QData& q) {
   SplitPlan& P = q.sp;
@@ -670,57 +884,11 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
     set_error("pair densities are not in the blocked layout");
     return LRT_ESTATE;
   }
-  // Row pairs in 4 x 4 sub-blocks of G quads (Qa <= Qb): sub-block row pair 4 i + j is
-  // (4 Qa + i, 4 Qb + j).  Sub-blocks are ordered by 8-G block pairs so that a super-tile of
-  // NSUB sub-blocks touches few G blocks.  In a diagonal sub-block (Qa == Qb) the six slots
-  // with i > j repeat pairs held by slots with i < j; like padding G, their rows are computed
-  // and never read.
-  const int nQ = (nG + 3) / 4;
-  const int nblk = (nG + GBLK - 1) / GBLK;
-  std::vector<int2> sub;
-  for (int I = 0; I < nblk; ++I)
-    for (int J = I; J < nblk; ++J)
-      for (int qa = 2 * I; qa < std::min(nQ, 2 * I + 2); ++qa)
-        for (int qb = 2 * J; qb < std::min(nQ, 2 * J + 2); ++qb)
-          if (qa <= qb) sub.push_back(make_int2(qa, qb));
-  const int nsub = (int)sub.size();
-  // a row unit is a pair of super-tiles, one per CTA, or a single super-tile shared by the
-  // pair (one accumulator per CTA): an odd last super-tile is such a half, so no super-tile
-  // is padding
-  const int n_st = (nsub + NSUB - 1) / NSUB;
-  std::vector<int2> rowtab((size_t)n_st * NSUB, make_int2(0, 0));
-  std::vector<int> blk((size_t)n_st * MAXBLK, -1);
-  std::vector<int> rp_of((size_t)nG * nG, 0);
-  for (int t = 0; t < n_st; ++t) {
-    int* bl = &blk[(size_t)t * MAXBLK];
-    int n = 0;
-    if (t * NSUB >= nsub) bl[0] = 0;
-    auto slot = [&](int qq) {   // ring row of the first G of quad qq
-      const int b = qq / 2;
-      for (int i = 0; i < n; ++i)
-        if (bl[i] == b) return i * GBLK + 4 * (qq % 2);
-      if (n == MAXBLK) return -1;
-      bl[n] = b;
-      return (n++) * GBLK + 4 * (qq % 2);
-    };
-    for (int w = 0; w < NSUB && t * NSUB + w < nsub; ++w) {
-      const int2 qq = sub[t * NSUB + w];
-      const int la = slot(qq.x), lb = slot(qq.y);
-      if (la < 0 || lb < 0) {
-        set_error("a row super-tile touches more than 6 G blocks");
-        return LRT_EUNSUPPORTED;
-      }
-      rowtab[(size_t)t * NSUB + w] = make_int2(la, lb);
-      for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) {
-          const int G = 4 * qq.x + i, Gp = 4 * qq.y + j;
-          if (G >= nG || Gp >= nG || G > Gp) continue;
-          const int r = (t * NSUB + w) * 16 + 4 * i + j;
-          rp_of[G * nG + Gp] = r;
-          rp_of[Gp * nG + G] = r;
-        }
-    }
-  }
+  int n_st = 0, n_list = 0;
+  std::vector<int2> rowtab, lsttab;
+  std::vector<int> blk, rp_of;
+  if (lrt_status st = row_tables(nG, n_st, n_list, rowtab, lsttab, blk, rp_of)) return st;
+  const int nsub = n_st * NSUB;
   // columns (eta, w), eta-major: column j has the frequency freqs[j % nw_tc] and eta j / nw_tc
   const int nc = ncol_tc(c), nwt = nw_tc(c);
   const int n_n = (2 * nc + TN - 1) / TN;
@@ -748,6 +916,7 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
   };
   cudaError_t e;
   if ((e = cudaMalloc(&P.rowtab, rowtab.size() * sizeof(int2))) != cudaSuccess ||
+      (e = cudaMalloc(&P.lsttab, lsttab.size() * sizeof(int2))) != cudaSuccess ||
       (e = cudaMalloc(&P.blk, blk.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&P.rp_of, rp_of.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&P.wtab, wtab.size() * sizeof(float4))) != cudaSuccess ||
@@ -756,6 +925,8 @@ static lrt_status build_plan(const lrt_ctx* c, QData& q) {
       (e = cudaMalloc(&P.C, (size_t)P.ldr * P.ldc * sizeof(double))) != cudaSuccess)
     return fail(e);
   if ((e = cudaMemcpy(P.rowtab, rowtab.data(), rowtab.size() * sizeof(int2), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(P.lsttab, lsttab.data(), lsttab.size() * sizeof(int2), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMemcpy(P.blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(P.rp_of, rp_of.data(), rp_of.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
@@ -807,6 +978,7 @@ static lrt_status upload_tables(const lrt_ctx* c, const std::vector<int>& qs,
     D.rho = (const float2*)rhos[i];
     D.pw = P.pw;
     D.rowtab = P.rowtab;
+    D.lsttab = P.lsttab;
     D.blk = P.blk;
     D.wtab = P.wtab;
     D.etab = P.etab;
@@ -1097,3 +1269,30 @@ lrt_status launch_chi0_split_range(lrt_ctx* c, int q_begin, int q_end, cudaStrea
 }
 
 }  // namespace lrt
+
+extern "C" lrt_status lrtddft_row_plan(int nG, int* n_st, int* n_list, int* max_blocks, int32_t* rp) {
+  using namespace lrt;
+  if (!n_st || !n_list || !max_blocks) {
+    set_error("NULL argument");
+    return LRT_EINVAL;
+  }
+  if (nG < 1 || nG > 4096) {
+    set_error("nG out of range");
+    return LRT_EINVAL;
+  }
+  int ns = 0, nl = 0;
+  std::vector<int2> rowtab, lsttab;
+  std::vector<int> blk, rp_of;
+  if (lrt_status st = row_tables(nG, ns, nl, rowtab, lsttab, blk, rp_of)) return st;
+  int mb = 0;
+  for (int t = 0; t < ns; ++t) {
+    int n = 0;
+    while (n < MAXBLK && blk[(size_t)t * MAXBLK + n] >= 0) ++n;
+    mb = std::max(mb, n);
+  }
+  *n_st = ns;
+  *n_list = nl;
+  *max_blocks = mb;
+  if (rp) std::memcpy(rp, rp_of.data(), rp_of.size() * sizeof(int32_t));
+  return LRT_OK;
+}

@@ -29,7 +29,8 @@ struct SplitPlan {
   int nsub = 0, n_st = 0, n_n = 0, ldc = 0;   // sub-blocks, row super-tiles, column tiles
   long long ldr = 0;
   size_t pw_n = 0;
-  int2* rowtab = nullptr;         // [n_st][8] ring rows of the G quads of each sub-block
+  int2* rowtab = nullptr;         // [n_st][8] ring rows of a sub-block's G quads, or (-1, list)
+  int2* lsttab = nullptr;         // [n_st][8][16] ring rows of the (G, G') of list slots
   int* blk = nullptr;             // [n_st][6] G blocks per super-tile
   int* rp_of = nullptr;           // [nG][nG] row pair of (G, G')
   float4* wtab = nullptr;         // [n_n][64] frequency pairs (hi, hi, lo, lo)
@@ -98,6 +99,8 @@ struct DeviceWork {
   size_t scratch_bytes = 0;
   void* pd_work = nullptr;        // tensor-core pair densities: prepared operands of one q
   size_t pd_bytes = 0;
+  double* zt_part = nullptr;      // tensor-core w = 0 column: per-CTA FP64 partial sums
+  size_t zt_bytes = 0;
   void* dyson_ws = nullptr;       // Dyson matrices of N_G too large for shared memory
   size_t dyson_bytes = 0;
   double2* s0 = nullptr;          // [nq][neta] d chi_00/d eta at w = 0 (S(q,0) = T Re s0/(pi n))
@@ -161,6 +164,7 @@ struct lrt_ctx {
   bool pair_simt = false;         // split-path pair densities on the FP32 SIMT kernel
   bool fine_accum = false;        // FP32 accumulation period of 32 stages instead of 64
   bool half_tiles = false;        // forced half row units (256 rows per CTA pair)
+  bool zero_simt = false;         // split w = 0 column on the CUDA cores, not the tensor cores
   int spectral_order = 0;         // chi0 engine: 0 the direct pair sum, 1 or 3 the spectral
   double spectral_h = 0.0;        // function on a grid of this spacing (interpolation order)
   void* sp = nullptr;             // spectral engine state (spectral.cu)
@@ -228,6 +232,9 @@ lrt_status launch_chi0_spectral(lrt_ctx* c, QData& q, const void* rho, cudaStrea
 void free_spectral_state(lrt_ctx* c);
 lrt_status split_pair_weights(const lrt_ctx* c, QData& q, float* sB, cudaStream_t s);
 lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho, float sB, cudaStream_t s);
+// zero_tc.cu: the same column on the tensor cores (*done false when it does not apply)
+lrt_status launch_zero_tc(const lrt_ctx* c, QData& q, const void* rho, float sB, cudaStream_t s,
+                          bool* done);
 double fxc_alda(double n);
 double fxc_model(double qg, double n, double A, double B, double C);
 // K_GG = 4 pi/|q+G|^2 + f_xc for the context's kernel, from Q.qg2 (host vector only).

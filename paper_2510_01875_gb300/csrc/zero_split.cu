@@ -175,6 +175,9 @@ __global__ void __launch_bounds__(ZL_THREADS, 3) chi0_zero_split_kernel(
 
 lrt_status launch_zero_split(const lrt_ctx* c, QData& q, const void* rho, float sB, cudaStream_t s) {
   if (c->hcol != c->nw) return LRT_OK;   // w = 0 is on the grid: a tensor column
+  bool done = false;
+  if (!c->zero_simt) LRT_TRY(launch_zero_tc(c, q, rho, sB, s, &done));
+  if (done) return LRT_OK;
   const int nG = q.nG;
   const long long mat = (long long)nG * nG;
   double2* base = q.chi0 + (size_t)c->hcol * mat;

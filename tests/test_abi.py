@@ -161,10 +161,10 @@ def test_host_geometry_matches_oracle(lib, wl):
 def test_tuning_flags_and_hooks_on_host(lib):
     st, h = _host_ctx(W.tiny())
     assert st == 0
-    # LRT_TUNE_AUTO | SINGLE_Q | PAIR_SIMT | FINE_ACCUM | HALF_TILES are the known flags
-    for flags in (0, 1, 2, 4, 7, 8, 15, 16, 31):
+    # LRT_TUNE_AUTO | SINGLE_Q | PAIR_SIMT | FINE_ACCUM | HALF_TILES | ZERO_SIMT are the known flags
+    for flags in (0, 1, 2, 4, 7, 8, 15, 16, 31, 32, 63):
         assert lib.lrtddft_set_tuning(h, flags, -1, 0) == 0, flags
-    for flags in (32, 64, -1):
+    for flags in (64, 128, -1):
         assert lib.lrtddft_set_tuning(h, flags, -1, 0) == binding.LRT_EINVAL, flags
     for v, u in ((2, 0), (-2, 0), (0, 100), (0, -64)):
         assert lib.lrtddft_set_tuning(h, 0, v, u) == binding.LRT_EINVAL, (v, u)
