@@ -1,6 +1,7 @@
 // chi0 at w = 0 on the CUDA cores for the split forms, when 0 is not on the caller's grid (the
-// column S(q,0) needs), for every eta, instead of a tensor tile of its own (one extra frequency
-// would cost a whole 128-frequency column tile of the contraction).
+// column S(q,0) needs), for every eta: the fallback of the tensor-core kernel of zero_tc.cu
+// (taken when that kernel's 64 x 64 G tiles outnumber the SMs, or under LRT_TUNE_ZERO_SIMT).
+// One extra frequency in the contraction would cost a whole 128-frequency column tile.
 //
 // Same Hermitian split as the contraction: with P_p = rho_p(G) rho_p*(G') and
 // w_p = df_p sB/(Delta_p + i eta), RR = sum Pr wr, RI = sum Pr wi, IR = sum Pi wr, II = sum Pi wi
